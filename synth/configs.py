@@ -1,0 +1,64 @@
+"""Named synthetic workloads (sizes, seeds, sampling and solver parameters).
+
+Each workload mirrors the shape and structure of one of the paper's
+experiments (multi-coil 2D brain k-space; multi-echo T2 data) with a seeded
+ellipse phantom in place of the in-vivo scans, which are not available.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, asdict, replace
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    model: str            # "SHLR", "SHLR_V", "SHLR_P", "SHLR_VP"
+    J: int
+    M: int
+    N: int
+    L: int = 1
+    window: int = 8
+    window_param: int = 4
+    weight: int = 1       # 0: W = I ; 1: circular finite-difference filter
+    mask: str = "random1d"
+    R: float = 4.0
+    n_acs: int = 24
+    sigma_n: float = 0.0
+    seed: int = 1
+    te_ms: float = 10.0
+    n_iter: int = 30
+    lam: float = 1.0e4    # data-term weight lambda (<= 0 : hard data consistency)
+    lam2: float = 2.0     # parameter-dimension weight lambda_2
+    beta: float = 1.0
+    tau: float = 1.0
+    d_init: float = 1.0
+
+    def to_dict(self):
+        return asdict(self)
+
+    def with_(self, **kw):
+        return replace(self, **kw)
+
+
+CONFIGS = {
+    # 4-coil 64x64, plain SHLR, 1D Gaussian-density Cartesian R=3 + 8 centre lines
+    "shlr_4c_64": Workload(name="shlr_4c_64", model="SHLR", J=4, M=64, N=64, window=8,
+                           mask="gauss1d", R=3.0, n_acs=8, sigma_n=0.0, seed=1,
+                           beta=20.0, tau=20.0),
+    # 12-coil 256x256 parallel imaging, 1D random R=4 + 24 ACS, noise 1e-3
+    "shlr_12c_256": Workload(name="shlr_12c_256", model="SHLR", J=12, M=256, N=256, window=16,
+                             mask="random1d", R=4.0, n_acs=24, sigma_n=1e-3, seed=2,
+                             beta=20.0, tau=20.0),
+    # same data, SHLR-V (conjugate-symmetric virtual coils), 2D Poisson-disc R=5
+    "shlrv_12c_256": Workload(name="shlrv_12c_256", model="SHLR_V", J=12, M=256, N=256, window=16,
+                              mask="poisson2d", R=5.0, n_acs=8, sigma_n=1e-3, seed=2,
+                              beta=20.0, tau=20.0),
+    # 8-coil 192x192 x 8 echoes T2 series, SHLR-VP, echo-varying 1D random R=6 + 8 ACS
+    "shlrvp_8c_192_8e": Workload(name="shlrvp_8c_192_8e", model="SHLR_VP", J=8, M=192, N=192, L=8,
+                                 window=12, window_param=4, mask="random1d", R=6.0, n_acs=8,
+                                 sigma_n=1e-3, seed=4, te_ms=10.0, beta=20.0, tau=20.0, lam2=2.0),
+}
+
+
+def get_config(name: str) -> Workload:
+    return CONFIGS[name]
