@@ -1,0 +1,208 @@
+/*
+ * selr.h - C ABI of libselr, a GB300 (sm_103a) implementation of the
+ * separable low-rank Hankel reconstruction of Zhang et al., "Accelerated MRI
+ * Reconstruction with Separable and Enhanced Low-Rank Hankel Regularization"
+ * (SHLR, SHLR-V, SHLR-P, SHLR-VP).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex data is complex64: interleaved (re, im) float pairs, C-contiguous.
+ * - 2D models (SHLR, SHLR-V) use arrays [J][M][N] (coil j, row m, column n).
+ *   Parameter models (SHLR-P, SHLR-VP) use [L][J][M][N] (echo l outermost,
+ *   m = frequency encoding (FE), n = phase encoding (PE)).  For 2D models
+ *   L = 1 and the two layouts coincide.
+ * - The Fourier transform is the centred unitary DFT
+ *   F x = fftshift(fft(ifftshift(x))) / sqrt(n), DC at index n/2; every
+ *   transformed length must be even and factor into 2, 3 and 5.
+ * - A lifted matrix ("A") has rows = nv - p + 1 window positions and
+ *   cols = C * p, channel-major (column c = channel * p + tap), where nv is
+ *   the lifted vector length, p the window, C = J or 2J (virtual coils).
+ *   Its entries are A[i][ch*p + q] = w[i+q] * v_ch[i+q] for the plain
+ *   channels and w[i+q] * conj(v_j[nv-1-(i+q)]) for virtual coil ch = J + j.
+ *   Lifted arrays passed across this ABI are [nmat][rows][cols] row-major.
+ * - All array pointers are DEVICE pointers owned by the caller unless a
+ *   comment says "host".  Nothing is freed or retained by the library.
+ * - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *   default stream).  Host-detectable errors (bad arguments, shapes, CUDA
+ *   launch failures) are returned immediately and nothing is launched.
+ *   Device-detected conditions (Jacobi non-convergence, non-finite values)
+ *   are recorded in the plan and reported by selr_sync_status().
+ * - No call prints, throws, or aborts.  A plan is not thread-safe; distinct
+ *   plans may be used concurrently from different host threads.
+ */
+#ifndef SELR_H
+#define SELR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *selr_stream;   /* == cudaStream_t */
+
+typedef enum {
+    SELR_OK = 0,
+    SELR_ERR_INVALID_ARG = 1,     /* null pointer, bad enum, non-positive size, bad parameter */
+    SELR_ERR_SHAPE = 2,           /* sizes inconsistent with the plan or unsupported length */
+    SELR_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+    SELR_ERR_NO_CONVERGENCE = 4,  /* a Jacobi SVD hit its sweep cap (device-detected) */
+    SELR_ERR_NONFINITE = 5,       /* NaN/Inf met in data or in the iterate (device-detected) */
+    SELR_ERR_TIMEOUT = 6,         /* reserved: a bounded device wait ran out */
+    SELR_ERR_UNSUPPORTED = 7,     /* feature not built */
+    SELR_ERR_ALLOC = 8            /* device allocation failed */
+} selr_status;
+
+typedef enum {
+    SELR_SHLR = 0,     /* Eq. 2: row + column lifts, H~ W~ F~                         */
+    SELR_SHLR_V = 1,   /* Eq. 5: as SHLR with virtual coils H~_vc (Eq. 4)               */
+    SELR_SHLR_P = 2,   /* Eq. 7: per FE position, PE lifts + parameter-dimension lifts  */
+    SELR_SHLR_VP = 3   /* Eq. 8: SHLR-P with virtual coils on the PE lifts              */
+} selr_model;
+
+/* Lift families.  Each names the vectors that are lifted and their source array. */
+typedef enum {
+    SELR_AXIS_ROW = 0,   /* 2D: row m, vectors over n, source = F^1D along n of the image   */
+    SELR_AXIS_COL = 1,   /* 2D: column n, vectors over m, source = F^1D along m             */
+    SELR_AXIS_PE = 2,    /* param: (m, l), vectors over PE n, source = PE k-space [L][J][M][N] */
+    SELR_AXIS_PARAM = 3  /* param: (m, n), vectors over echoes l, source = image [L][J][M][N] */
+} selr_axis;
+
+typedef enum {
+    SELR_EXEC_BATCHED = 0, /* every matrix of an iteration in one launch per step; the whole
+                              iteration captured once as a CUDA graph                      */
+    SELR_EXEC_PLAIN = 1    /* one launch per matrix for lift/SVT/adjoint, no graph           */
+} selr_exec;
+
+/* Problem description (Sec. III; Algorithms S1 and S2). */
+typedef struct {
+    int32_t model;            /* selr_model                                               */
+    int32_t J, M, N, L;       /* coils, rows (FE), columns (PE), echoes (1 for 2D models) */
+    int32_t window;           /* Hankel window p of row / column / PE lifts               */
+    int32_t window_param;     /* Hankel window of the parameter-dimension lift            */
+    int32_t weight;           /* W: 0 = identity, 1 = circular first-difference filter    */
+    float lambda;             /* data weight (Eq. 2); <= 0 selects hard data consistency  */
+    float lambda2;            /* parameter-lift weight (Eq. 7/8); SVT threshold lambda2/beta */
+    float beta;               /* ADMM penalty; SVT threshold of row/col/PE lifts is 1/beta */
+    float tau;                /* multiplier step (Eqs. 13-14)                             */
+    float d_init;             /* initial multiplier value (the paper uses 1)              */
+    int32_t max_iter;         /* iteration cap (paper: 50 for S1, 100 for S2)             */
+    float tol;                /* stop when ||X+ - X||^2/||X||^2 < tol; < 0 = run max_iter */
+    int32_t jacobi_max_sweeps;/* sweep cap of the one-sided Jacobi SVD                    */
+    float jacobi_tol;         /* rotate a pair while |x^H y| > tol * ||x|| ||y||          */
+    int32_t exec;             /* selr_exec                                                */
+} selr_desc;
+
+typedef struct selr_plan selr_plan;   /* opaque; owns its device workspace */
+
+/* Fill *desc with defaults (SHLR, weight 1, beta = tau = 20, lambda = 1e4,
+ * lambda2 = 2, d_init = 1, max_iter = 30, tol = -1, 30 sweeps, tol 2e-6). */
+void selr_desc_default(selr_desc *desc);
+
+/* Validate *desc and allocate the plan's device workspace on the current
+ * device (multipliers D, Jacobi work copies, FFT twiddles, weights).
+ * Errors: SELR_ERR_INVALID_ARG, SELR_ERR_SHAPE (odd or non-2/3/5 FFT length,
+ * window larger than the vector), SELR_ERR_ALLOC, SELR_ERR_CUDA.
+ * *out is set to NULL on failure. */
+selr_status selr_plan_create(const selr_desc *desc, selr_plan **out);
+
+/* Free the plan and its workspace.  NULL is accepted. */
+selr_status selr_plan_destroy(selr_plan *plan);
+
+/* Bytes of device workspace held by the plan (host value). */
+size_t selr_plan_workspace_bytes(const selr_plan *plan);
+
+/* Number of matrices, rows and columns of the plan's lift family `axis`
+ * (host outputs; any may be NULL).  SELR_ERR_INVALID_ARG if the model has no
+ * such family (rows/cols for 2D models, PE/PARAM for parameter models). */
+selr_status selr_lift_shape(const selr_plan *plan, int32_t axis, int32_t *nmat,
+                            int32_t *rows, int32_t *cols);
+
+/* Centred unitary 1D DFT of an array [L][J][M][N] along dim M (dim = 0) or
+ * dim N (dim = 1); inverse != 0 selects F*.  in and out may alias.
+ * (Sec. III-A, F^1D; hybrid transforms feeding the row / column lifts.) */
+selr_status selr_transform(selr_plan *plan, int32_t dim, int32_t inverse,
+                           const void *in, void *out, selr_stream stream);
+
+/* Hankel lift (Eq. 2, Eq. 4, Eq. 7/8): A_out[mat] = lift(x)[mat] + D[mat] / beta.
+ * x  : the family's source array (see selr_axis) [L][J][M][N] complex64.
+ * D  : [nmat][rows][cols] complex64 or NULL (treated as zero).
+ * A_out: [nmat][rows][cols] complex64, fully overwritten. */
+selr_status selr_lift(selr_plan *plan, int32_t axis, const void *x, const void *D,
+                      void *A_out, selr_stream stream);
+
+/* Singular value thresholding S_t (Eqs. 16-17, S8-S9) of nmat complex64
+ * matrices [nmat][rows][cols], in place: A <- U diag(max(sigma - t, 0)) V^H.
+ * Computed by one-sided Jacobi on the shorter dimension in FP32.
+ * rank_out: device int32[nmat] receiving #{sigma > t}, or NULL.
+ * Requires nmat*rows*cols within the plan's workspace capacity
+ * (SELR_ERR_SHAPE otherwise) and t >= 0. */
+selr_status selr_svt(selr_plan *plan, void *A, int32_t nmat, int32_t rows, int32_t cols,
+                     float thresh, int32_t *rank_out, selr_stream stream);
+
+/* Real adjoint of the lift (the transpose appearing in Eq. 15 / S7):
+ * x_out = L^T E for the family `axis`.  Plain channel j contributes
+ * conj(w) * H*(E_j); virtual coil J+j contributes flip(w * conj(H*(E_{J+j}))),
+ * where H* sums anti-diagonals.  E: [nmat][rows][cols]; x_out: [L][J][M][N],
+ * fully overwritten, in the family's source domain. */
+selr_status selr_adjoint(selr_plan *plan, int32_t axis, const void *E, void *x_out,
+                         selr_stream stream);
+
+/* X-update of Eq. 15 (2D) / Eq. S7 (parameter models) without the SPIRiT term,
+ * as a pointwise divide in k-space:
+ *   K = (lambda U Y + beta (F a + F' b)) / (lambda U + beta (d_a + d_b)).
+ * 2D: adj_a = row-lift adjoint (F along M applied here), adj_b = column-lift
+ *     adjoint (F along N applied here).
+ * Parameter: adj_a = PE-lift adjoint (already in PE k-space), adj_b =
+ *     parameter-lift adjoint (F along N applied here).
+ * adj_a and adj_b are overwritten (transformed in place).  K is read as the
+ * previous iterate and overwritten.  Y: zero-filled data [L][J][M][N];
+ * mask: [L][M][N] uint8 0/1.  rel_out: device float receiving
+ * ||K_new - K||^2 / ||K||^2, or NULL. */
+selr_status selr_dc(selr_plan *plan, const void *Y, const uint8_t *mask, void *adj_a,
+                    void *adj_b, void *K, float *rel_out, selr_stream stream);
+
+/* Full reconstruction: Algorithm S1 (SHLR, SHLR-V) or S2 (SHLR-P, SHLR-VP,
+ * all FE positions batched, each stopping on its own criterion).
+ * Init: K = Y, Z = 0, D = d_init.  Per iteration: X-update (Eq. 15 / S7),
+ * Z = SVT (Eqs. 16-17 / S8-S9), D update (Eqs. 13-14 / S5-S6).
+ * Y: [L][J][M][N] zero-filled k-space (parameter models: after the inverse
+ * DFT along FE, i.e. hybrid (m, k_n) data).  mask: [L][M][N] uint8.
+ * X_out: [L][J][M][N] complex64 image.  iters_out (host, may be NULL):
+ * iterations run (max over FE positions for parameter models).
+ * rel_out (host, may be NULL): last relative change.
+ * With tol >= 0 the call synchronises `stream` once per iteration. */
+selr_status selr_solve(selr_plan *plan, const void *Y, const uint8_t *mask, void *X_out,
+                       int32_t *iters_out, float *rel_out, selr_stream stream);
+
+/* Change the iteration cap and stopping tolerance of an existing plan
+ * (same meaning as selr_desc.max_iter / tol).  SELR_ERR_INVALID_ARG if
+ * max_iter < 1. */
+selr_status selr_set_iterations(selr_plan *plan, int32_t max_iter, float tol);
+
+/* Stage timing of selr_solve (instrumentation, not part of the method).
+ * Stages: 0 lift adjoints, 1 data consistency (FFTs of the adjoints, the
+ * pointwise solve and its reduction), 2 hybrid transforms, 3 lifts,
+ * 4 Jacobi SVD, 5 SVT apply + multiplier update.
+ * selr_profile_enable(plan, on): when on, the following selr_solve calls
+ * record CUDA events around every stage of every iteration (in batched mode
+ * the whole solve, events included, is captured as one CUDA graph).
+ * selr_profile_read(plan, stage, total_ms, count): host outputs with the
+ * summed duration of `stage` over the last profiled solve and the number of
+ * iterations timed; synchronises on the recorded events. */
+selr_status selr_profile_enable(selr_plan *plan, int32_t on);
+selr_status selr_profile_read(selr_plan *plan, int32_t stage, float *total_ms, int32_t *count);
+
+/* Synchronise `stream` and return the first device-side condition recorded
+ * since the last call (SELR_ERR_NO_CONVERGENCE, SELR_ERR_NONFINITE), or
+ * SELR_ERR_CUDA if the stream reports an error; clears the record. */
+selr_status selr_sync_status(selr_plan *plan, selr_stream stream);
+
+/* Static, human-readable name of a status code. */
+const char *selr_status_string(selr_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SELR_H */

@@ -1,0 +1,188 @@
+"""Python binding of libselr with the C entry-point names.
+
+Argument marshalling only: each function checks that its torch tensors are
+contiguous CUDA tensors of the expected dtype and shape, then calls the C ABI
+with their device pointers and the current CUDA stream.  Every step of the
+reconstruction runs in libselr's kernels; if the library is missing the call
+raises (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import AXES, EXEC, MODELS, SelrDesc, check
+
+
+@dataclass
+class Desc:
+    """Mirror of ``selr_desc`` (include/selr.h)."""
+    model: str = "SHLR"
+    J: int = 4
+    M: int = 64
+    N: int = 64
+    L: int = 1
+    window: int = 8
+    window_param: int = 4
+    weight: int = 1
+    lam: float = 1.0e4
+    lam2: float = 2.0
+    beta: float = 20.0
+    tau: float = 20.0
+    d_init: float = 1.0
+    max_iter: int = 30
+    tol: float = -1.0
+    jacobi_max_sweeps: int = 30
+    jacobi_tol: float = 2.0e-6
+    exec: str = "batched"
+
+    @classmethod
+    def from_workload(cls, w, **over):
+        kw = dict(model=w.model, J=w.J, M=w.M, N=w.N, L=w.L, window=w.window, window_param=w.window_param,
+                  weight=w.weight, lam=w.lam, lam2=w.lam2, beta=w.beta, tau=w.tau, d_init=w.d_init,
+                  max_iter=w.n_iter)
+        kw.update(over)
+        return cls(**kw)
+
+    def to_c(self) -> SelrDesc:
+        d = SelrDesc()
+        d.model = MODELS[self.model]
+        d.J, d.M, d.N, d.L = self.J, self.M, self.N, self.L
+        d.window, d.window_param, d.weight = self.window, self.window_param, self.weight
+        d.lambda_, d.lambda2, d.beta, d.tau = self.lam, self.lam2, self.beta, self.tau
+        d.d_init, d.max_iter, d.tol = self.d_init, self.max_iter, self.tol
+        d.jacobi_max_sweeps, d.jacobi_tol = self.jacobi_max_sweeps, self.jacobi_tol
+        d.exec_ = EXEC[self.exec]
+        return d
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype, name, numel=None, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owns a ``selr_plan`` (device workspace on the current device)."""
+
+    def __init__(self, desc: Desc):
+        self.lib = _lib.load()
+        self.desc = desc
+        h = ctypes.c_void_p()
+        cd = desc.to_c()
+        check(self.lib.selr_plan_create(ctypes.byref(cd), ctypes.byref(h)), "selr_plan_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.selr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nK(self):
+        d = self.desc
+        return d.L * d.J * d.M * d.N
+
+    def workspace_bytes(self):
+        return int(self.lib.selr_plan_workspace_bytes(self.handle))
+
+    def set_iterations(self, max_iter, tol=-1.0):
+        check(self.lib.selr_set_iterations(self.handle, int(max_iter), float(tol)), "selr_set_iterations")
+        self.desc.max_iter, self.desc.tol = int(max_iter), float(tol)
+
+    STAGES = ("adjoint", "dc", "hybrid_fft", "lift", "jacobi", "apply")
+
+    def profile(self, on=True):
+        check(self.lib.selr_profile_enable(self.handle, 1 if on else 0), "selr_profile_enable")
+
+    def profile_read(self):
+        """{stage: (total_ms, iterations)} of the last profiled solve."""
+        out = {}
+        for k, name in enumerate(self.STAGES):
+            ms, n = ctypes.c_float(), ctypes.c_int32()
+            check(self.lib.selr_profile_read(self.handle, k, ctypes.byref(ms), ctypes.byref(n)), "selr_profile_read")
+            out[name] = (ms.value, n.value)
+        return out
+
+    def lift_shape(self, axis):
+        n, r, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(self.lib.selr_lift_shape(self.handle, AXES[axis], ctypes.byref(n), ctypes.byref(r), ctypes.byref(c)),
+              "selr_lift_shape")
+        return n.value, r.value, c.value
+
+
+def selr_transform(plan: Plan, dim: int, inverse: bool, x, out, stream=None):
+    check(plan.lib.selr_transform(plan.handle, dim, 1 if inverse else 0,
+                                  _ptr(x, torch.complex64, "x", plan.nK), _ptr(out, torch.complex64, "out", plan.nK),
+                                  _stream(stream)), "selr_transform")
+
+
+def selr_lift(plan: Plan, axis: str, x, D, A_out, stream=None):
+    n, r, c = plan.lift_shape(axis)
+    check(plan.lib.selr_lift(plan.handle, AXES[axis], _ptr(x, torch.complex64, "x", plan.nK),
+                             _ptr(D, torch.complex64, "D", n * r * c, allow_none=True),
+                             _ptr(A_out, torch.complex64, "A_out", n * r * c), _stream(stream)), "selr_lift")
+
+
+def selr_svt(plan: Plan, A, thresh: float, rank_out=None, stream=None):
+    if A.dim() != 3:
+        raise ValueError("A must be [nmat][rows][cols]")
+    nmat, rows, cols = A.shape
+    check(plan.lib.selr_svt(plan.handle, _ptr(A, torch.complex64, "A"), nmat, rows, cols, float(thresh),
+                            _ptr(rank_out, torch.int32, "rank_out", nmat, allow_none=True), _stream(stream)),
+          "selr_svt")
+
+
+def selr_adjoint(plan: Plan, axis: str, E, x_out, stream=None):
+    n, r, c = plan.lift_shape(axis)
+    check(plan.lib.selr_adjoint(plan.handle, AXES[axis], _ptr(E, torch.complex64, "E", n * r * c),
+                                _ptr(x_out, torch.complex64, "x_out", plan.nK), _stream(stream)), "selr_adjoint")
+
+
+def selr_dc(plan: Plan, Y, mask, adj_a, adj_b, K, rel_out=None, stream=None):
+    d = plan.desc
+    check(plan.lib.selr_dc(plan.handle, _ptr(Y, torch.complex64, "Y", plan.nK),
+                           _ptr(mask, torch.uint8, "mask", d.L * d.M * d.N),
+                           _ptr(adj_a, torch.complex64, "adj_a", plan.nK), _ptr(adj_b, torch.complex64, "adj_b", plan.nK),
+                           _ptr(K, torch.complex64, "K", plan.nK),
+                           _ptr(rel_out, torch.float32, "rel_out", 1, allow_none=True), _stream(stream)), "selr_dc")
+
+
+def selr_solve(plan: Plan, Y, mask, X_out, stream=None):
+    """Run the reconstruction; returns (iterations, last relative change)."""
+    d = plan.desc
+    it, rel = ctypes.c_int32(), ctypes.c_float()
+    check(plan.lib.selr_solve(plan.handle, _ptr(Y, torch.complex64, "Y", plan.nK),
+                              _ptr(mask, torch.uint8, "mask", d.L * d.M * d.N),
+                              _ptr(X_out, torch.complex64, "X_out", plan.nK), ctypes.byref(it), ctypes.byref(rel),
+                              _stream(stream)), "selr_solve")
+    return it.value, rel.value
+
+
+def selr_sync_status(plan: Plan, stream=None) -> int:
+    """Synchronise and return the device-side status code (0 = SELR_OK)."""
+    return int(plan.lib.selr_sync_status(plan.handle, _stream(stream)))

@@ -1,0 +1,704 @@
+// C ABI of libselr: plan management, the five operator entry points and the
+// ADMM driver (Algorithm S1 for SHLR / SHLR-V, Algorithm S2 for SHLR-P /
+// SHLR-VP with every FE position batched).
+#include "selr_internal.cuh"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <new>
+
+struct selr_plan {
+    selr_desc d;
+    int model2d, vc;
+    int L, J, M, N;
+    long long nK;
+    GroupSet gs;
+    long long lift_elems, vec_elems;
+    cf *K, *hybA, *hybB, *adjA, *adjB;
+    cf *D, *E, *W, *B0;
+    float *sigma;
+    int *mat_status;
+    double *partial;
+    float *rel;
+    int *active, *active_next;
+    unsigned *status;
+    cf *twM, *twN;
+    FftTable ftM, ftN;
+    cf *wM, *wN;
+    float *da, *db;
+    size_t bytes;
+    float *h_rel;          // pinned host mirror
+    int *h_active;         // pinned host mirror
+    cudaGraphExec_t graph;
+    const void *graph_Y;
+    const uint8_t *graph_mask;
+    cudaStream_t graph_stream;
+    int graph_iters;          // iterations captured in `graph` (1, or max_iter when profiling)
+    // stage profiling
+    int prof_on;
+    int prof_cap;             // iterations with events allocated
+    cudaEvent_t *ev;          // [prof_cap][NSTAGE][2]
+    int prof_count;           // iterations timed by the last solve
+};
+
+#define NSTAGE 6
+
+#define CK(x)                                          \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return SELR_ERR_CUDA;   \
+    } while (0)
+
+static bool smooth_even(int n) {
+    if (n < 2 || (n & 1)) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    while (n % 5 == 0) n /= 5;
+    return n == 1;
+}
+
+extern "C" void selr_desc_default(selr_desc *d) {
+    if (!d) return;
+    memset(d, 0, sizeof(*d));
+    d->model = SELR_SHLR;
+    d->J = 4; d->M = 64; d->N = 64; d->L = 1;
+    d->window = 8;
+    d->window_param = 4;
+    d->weight = 1;
+    d->lambda = 1.0e4f;
+    d->lambda2 = 2.0f;
+    d->beta = 20.0f;
+    d->tau = 20.0f;
+    d->d_init = 1.0f;
+    d->max_iter = 30;
+    d->tol = -1.0f;
+    d->jacobi_max_sweeps = 30;
+    d->jacobi_tol = 2.0e-6f;
+    d->exec = SELR_EXEC_BATCHED;
+}
+
+extern "C" const char *selr_status_string(selr_status s) {
+    switch (s) {
+        case SELR_OK: return "SELR_OK";
+        case SELR_ERR_INVALID_ARG: return "SELR_ERR_INVALID_ARG";
+        case SELR_ERR_SHAPE: return "SELR_ERR_SHAPE";
+        case SELR_ERR_CUDA: return "SELR_ERR_CUDA";
+        case SELR_ERR_NO_CONVERGENCE: return "SELR_ERR_NO_CONVERGENCE";
+        case SELR_ERR_NONFINITE: return "SELR_ERR_NONFINITE";
+        case SELR_ERR_TIMEOUT: return "SELR_ERR_TIMEOUT";
+        case SELR_ERR_UNSUPPORTED: return "SELR_ERR_UNSUPPORTED";
+        case SELR_ERR_ALLOC: return "SELR_ERR_ALLOC";
+    }
+    return "SELR_ERR_UNKNOWN";
+}
+
+// Host-side description of one lift family (see Group in selr_internal.cuh).
+static Group make_group(int kind, int nmat, int nv, int p, int J, int vc, int M, int N, int L, float thresh) {
+    Group g;
+    memset(&g, 0, sizeof(g));
+    g.kind = kind;
+    g.nmat = nmat;
+    g.nv = nv;
+    g.p = p;
+    g.J = J;
+    g.vc = vc;
+    g.C = vc ? 2 * J : J;
+    g.rows = nv - p + 1;
+    g.cols = g.C * p;
+    g.trans = g.cols > g.rows ? 1 : 0;
+    g.s = g.trans ? g.rows : g.cols;
+    g.len = g.trans ? g.cols : g.rows;
+    g.thresh = thresh;
+    g.M = M;
+    g.N = N;
+    g.L = L;
+    return g;
+}
+
+static void finish_set(GroupSet *gs) {
+    long long off = 0, soff = 0;
+    int moff = 0;
+    gs->start[0] = 0;
+    for (int k = 0; k < gs->n; ++k) {
+        gs->g[k].off = off;
+        gs->g[k].soff = soff;
+        gs->g[k].moff = moff;
+        off += (long long)gs->g[k].nmat * gs->g[k].rows * gs->g[k].cols;
+        soff += (long long)gs->g[k].nmat * gs->g[k].s;
+        moff += gs->g[k].nmat;
+        gs->start[k + 1] = moff;
+    }
+    gs->total = moff;
+}
+
+static selr_status validate(const selr_desc *d) {
+    if (!d) return SELR_ERR_INVALID_ARG;
+    if (d->model < SELR_SHLR || d->model > SELR_SHLR_VP) return SELR_ERR_INVALID_ARG;
+    if (d->J < 1 || d->M < 1 || d->N < 1 || d->L < 1 || d->window < 1) return SELR_ERR_INVALID_ARG;
+    if (!(d->beta > 0.f) || !(d->tau > 0.f) || d->max_iter < 1 || d->jacobi_max_sweeps < 1 ||
+        !(d->jacobi_tol > 0.f) || !isfinite(d->lambda) || !isfinite(d->beta) || !isfinite(d->tau) ||
+        !isfinite(d->d_init) || !(d->lambda2 >= 0.f))
+        return SELR_ERR_INVALID_ARG;
+    if (d->weight != 0 && d->weight != 1) return SELR_ERR_INVALID_ARG;
+    if (d->exec != SELR_EXEC_BATCHED && d->exec != SELR_EXEC_PLAIN) return SELR_ERR_INVALID_ARG;
+    const bool two_d = d->model <= SELR_SHLR_V;
+    if (two_d) {
+        if (d->L != 1) return SELR_ERR_SHAPE;
+        if (!smooth_even(d->M) || !smooth_even(d->N) || d->M > 1024 || d->N > 1024) return SELR_ERR_SHAPE;
+        if (d->window > d->M || d->window > d->N) return SELR_ERR_SHAPE;
+    } else {
+        if (d->window_param < 1 || d->window_param > d->L) return SELR_ERR_SHAPE;
+        if (!smooth_even(d->N) || d->N > 1024) return SELR_ERR_SHAPE;
+        if (d->window > d->N) return SELR_ERR_SHAPE;
+    }
+    return SELR_OK;
+}
+
+static selr_status alloc(selr_plan *p, void **ptr, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return SELR_ERR_ALLOC;
+    }
+    p->bytes += bytes;
+    return SELR_OK;
+}
+
+static void host_weights(int n, int kind, cf *out) {
+    for (int k = 0; k < n; ++k) {
+        if (kind == 0) { out[k] = mk(1.f, 0.f); continue; }
+        const double a = -2.0 * M_PI * ((double)k - n / 2.0) / (double)n;
+        out[k] = mk((float)(1.0 - cos(a)), (float)(-sin(a)));
+    }
+}
+
+// d(k) = c(k)|w(k)|^2 [+ c(n-1-k)|w(n-1-k)|^2], c = Hankel multiplicities.
+static void host_normal(int n, int p, int kind, int vc, float *out) {
+    cf *w = (cf *)malloc(sizeof(cf) * n);
+    for (int k = 0; k < n; ++k) out[k] = 0.f;
+    host_weights(n, kind, w);
+    const int l = n - p + 1;
+    double *acc = (double *)calloc(n, sizeof(double));
+    for (int k = 0; k < n; ++k) {
+        int c = k + 1;
+        if (p < c) c = p;
+        if (n - k < c) c = n - k;
+        if (l < c) c = l;
+        const double w2 = (double)w[k].x * w[k].x + (double)w[k].y * w[k].y;
+        acc[k] += c * w2;
+        if (vc) acc[n - 1 - k] += c * w2;
+    }
+    for (int k = 0; k < n; ++k) out[k] = (float)acc[k];
+    free(acc);
+    free(w);
+}
+
+static void host_multiplicity(int n, int p, float *out) {
+    const int l = n - p + 1;
+    for (int k = 0; k < n; ++k) {
+        int c = k + 1;
+        if (p < c) c = p;
+        if (n - k < c) c = n - k;
+        if (l < c) c = l;
+        out[k] = (float)c;
+    }
+}
+
+static selr_status upload(void *dst, const void *src, size_t bytes) {
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess ? SELR_OK : SELR_ERR_CUDA;
+}
+
+extern "C" selr_status selr_plan_destroy(selr_plan *p) {
+    if (!p) return SELR_OK;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->sigma,
+                    p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status,
+                    p->twM, p->twN, p->wM, p->wN, p->da, p->db};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (p->ev) {
+        for (size_t i = 0; i < (size_t)p->prof_cap * NSTAGE * 2; ++i) cudaEventDestroy(p->ev[i]);
+        free(p->ev);
+    }
+    if (p->h_rel) cudaFreeHost(p->h_rel);
+    if (p->h_active) cudaFreeHost(p->h_active);
+    delete p;
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_plan_create(const selr_desc *d, selr_plan **out) {
+    if (!out) return SELR_ERR_INVALID_ARG;
+    *out = nullptr;
+    selr_status s = validate(d);
+    if (s != SELR_OK) return s;
+    selr_plan *p = new (std::nothrow) selr_plan;
+    if (!p) return SELR_ERR_ALLOC;
+    memset(p, 0, sizeof(*p));
+    p->d = *d;
+    p->model2d = d->model <= SELR_SHLR_V;
+    p->vc = d->model == SELR_SHLR_V || d->model == SELR_SHLR_VP;
+    p->L = d->L; p->J = d->J; p->M = d->M; p->N = d->N;
+    p->nK = (long long)d->L * d->J * d->M * d->N;
+    const float t1 = 1.0f / d->beta;
+    GroupSet &gs = p->gs;
+    if (p->model2d) {
+        gs.n = 2;
+        gs.g[0] = make_group(G_ROW, d->M, d->N, d->window, d->J, p->vc, d->M, d->N, 1, t1);
+        gs.g[1] = make_group(G_COL, d->N, d->M, d->window, d->J, p->vc, d->M, d->N, 1, t1);
+    } else {
+        gs.n = 2;
+        gs.g[0] = make_group(G_PE, d->M * d->L, d->N, d->window, d->J, p->vc, d->M, d->N, d->L, t1);
+        gs.g[1] = make_group(G_PARAM, d->M * d->N, d->L, d->window_param, d->J, 0, d->M, d->N, d->L,
+                             d->lambda2 / d->beta);
+    }
+    for (int k = 0; k < gs.n; ++k) {
+        if (gs.g[k].len > 512 || gs.g[k].s > 1024) { delete p; return SELR_ERR_SHAPE; }
+    }
+    finish_set(&gs);
+    p->lift_elems = 0;
+    p->vec_elems = 0;
+    for (int k = 0; k < gs.n; ++k) {
+        p->lift_elems += (long long)gs.g[k].nmat * gs.g[k].rows * gs.g[k].cols;
+        p->vec_elems += (long long)gs.g[k].nmat * gs.g[k].s;
+    }
+    if (fft_init_attributes() != cudaSuccess || svt_init_attributes() != cudaSuccess) {
+        delete p;
+        return SELR_ERR_CUDA;
+    }
+#define AL(ptr, bytes)                                                      \
+    do {                                                                    \
+        selr_status s_ = alloc(p, (void **)&(ptr), (bytes));                \
+        if (s_ != SELR_OK) { selr_plan_destroy(p); return s_; }             \
+    } while (0)
+    const size_t kb = sizeof(cf) * (size_t)p->nK;
+    AL(p->K, kb); AL(p->hybA, kb); AL(p->hybB, kb); AL(p->adjA, kb); AL(p->adjB, kb);
+    const size_t lb = sizeof(cf) * (size_t)p->lift_elems;
+    AL(p->D, lb); AL(p->E, lb); AL(p->W, lb); AL(p->B0, lb);
+    AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
+    AL(p->mat_status, sizeof(int) * (size_t)gs.total);
+    AL(p->partial, sizeof(double) * 2 * (size_t)d->M);
+    AL(p->rel, sizeof(float) * (1 + (size_t)d->M));
+    AL(p->active, sizeof(int) * (size_t)d->M);
+    AL(p->active_next, sizeof(int) * (size_t)d->M);
+    AL(p->status, sizeof(unsigned));
+    AL(p->wN, sizeof(cf) * d->N);
+    AL(p->wM, sizeof(cf) * d->M);
+    AL(p->da, sizeof(float) * d->N);
+    AL(p->db, sizeof(float) * (p->model2d ? d->M : d->L));
+#undef AL
+    if (cudaMemset(p->status, 0, sizeof(unsigned)) != cudaSuccess) { selr_plan_destroy(p); return SELR_ERR_CUDA; }
+    // FFT tables (N always; M for the 2D models)
+    if (fft_table_build(d->N, &p->ftN, &p->twN) != cudaSuccess) { selr_plan_destroy(p); return SELR_ERR_SHAPE; }
+    if (p->model2d && fft_table_build(d->M, &p->ftM, &p->twM) != cudaSuccess) { selr_plan_destroy(p); return SELR_ERR_SHAPE; }
+    // weights and normal diagonals
+    {
+        const int nmax = d->M > d->N ? d->M : d->N;
+        cf *hw = (cf *)malloc(sizeof(cf) * nmax);
+        float *hd = (float *)malloc(sizeof(float) * (nmax > d->L ? nmax : d->L));
+        selr_status e = SELR_OK;
+        host_weights(d->N, d->weight, hw);
+        if (e == SELR_OK) e = upload(p->wN, hw, sizeof(cf) * d->N);
+        host_weights(d->M, d->weight, hw);
+        if (e == SELR_OK) e = upload(p->wM, hw, sizeof(cf) * d->M);
+        host_normal(d->N, d->window, d->weight, p->vc, hd);
+        if (e == SELR_OK) e = upload(p->da, hd, sizeof(float) * d->N);
+        if (p->model2d) {
+            host_normal(d->M, d->window, d->weight, p->vc, hd);
+            if (e == SELR_OK) e = upload(p->db, hd, sizeof(float) * d->M);
+        } else {
+            host_multiplicity(d->L, d->window_param, hd);
+            if (e == SELR_OK) e = upload(p->db, hd, sizeof(float) * d->L);
+        }
+        free(hw);
+        free(hd);
+        if (e != SELR_OK) { selr_plan_destroy(p); return e; }
+    }
+    const cf *wrow = d->weight ? p->wN : nullptr;
+    const cf *wcol = d->weight ? p->wM : nullptr;
+    if (p->model2d) {
+        gs.g[0].w = wrow; gs.g[0].src = p->hybA; gs.g[0].dst = p->adjA;
+        gs.g[1].w = wcol; gs.g[1].src = p->hybB; gs.g[1].dst = p->adjB;
+    } else {
+        gs.g[0].w = wrow; gs.g[0].src = p->K; gs.g[0].dst = p->adjA;
+        gs.g[1].w = nullptr; gs.g[1].src = p->hybB; gs.g[1].dst = p->adjB;
+    }
+    if (cudaMallocHost((void **)&p->h_rel, sizeof(float) * (1 + (size_t)d->M)) != cudaSuccess ||
+        cudaMallocHost((void **)&p->h_active, sizeof(int) * (size_t)d->M) != cudaSuccess) {
+        cudaGetLastError();
+        selr_plan_destroy(p);
+        return SELR_ERR_ALLOC;
+    }
+    *out = p;
+    return SELR_OK;
+}
+
+extern "C" size_t selr_plan_workspace_bytes(const selr_plan *p) { return p ? p->bytes : 0; }
+
+static int group_index(const selr_plan *p, int axis) {
+    if (p->model2d) {
+        if (axis == SELR_AXIS_ROW) return 0;
+        if (axis == SELR_AXIS_COL) return 1;
+    } else {
+        if (axis == SELR_AXIS_PE) return 0;
+        if (axis == SELR_AXIS_PARAM) return 1;
+    }
+    return -1;
+}
+
+extern "C" selr_status selr_lift_shape(const selr_plan *p, int32_t axis, int32_t *nmat, int32_t *rows,
+                                       int32_t *cols) {
+    if (!p) return SELR_ERR_INVALID_ARG;
+    const int gi = group_index(p, axis);
+    if (gi < 0) return SELR_ERR_INVALID_ARG;
+    if (nmat) *nmat = p->gs.g[gi].nmat;
+    if (rows) *rows = p->gs.g[gi].rows;
+    if (cols) *cols = p->gs.g[gi].cols;
+    return SELR_OK;
+}
+
+// Transform along M (dim 0) or N (dim 1) of an [L][J][M][N] array.
+static cudaError_t transform(selr_plan *p, int dim, int inverse, const cf *in, cf *out, cudaStream_t st) {
+    if (dim == 0) return launch_fft(in, out, p->ftM, (long long)p->L * p->J, p->N, inverse, st);
+    return launch_fft(in, out, p->ftN, (long long)p->L * p->J * p->M, 1, inverse, st);
+}
+
+extern "C" selr_status selr_transform(selr_plan *p, int32_t dim, int32_t inverse, const void *in, void *out,
+                                      selr_stream stream) {
+    if (!p || !in || !out || (dim != 0 && dim != 1)) return SELR_ERR_INVALID_ARG;
+    if (dim == 0 && !p->model2d) return SELR_ERR_SHAPE;
+    CK(transform(p, dim, inverse ? 1 : 0, (const cf *)in, (cf *)out, (cudaStream_t)stream));
+    return SELR_OK;
+}
+
+static GroupSet single_group(const selr_plan *p, int gi) {
+    GroupSet s;
+    memset(&s, 0, sizeof(s));
+    s.n = 1;
+    s.g[0] = p->gs.g[gi];
+    finish_set(&s);
+    return s;
+}
+
+extern "C" selr_status selr_lift(selr_plan *p, int32_t axis, const void *x, const void *D, void *A_out,
+                                 selr_stream stream) {
+    if (!p || !x || !A_out) return SELR_ERR_INVALID_ARG;
+    const int gi = group_index(p, axis);
+    if (gi < 0) return SELR_ERR_INVALID_ARG;
+    GroupSet s = single_group(p, gi);
+    s.g[0].src = (const cf *)x;
+    CK(launch_lift(s, 0, 0, s.total, (const cf *)D, 1, 1.0f / p->d.beta, (cf *)A_out, nullptr, 1, nullptr,
+                   (cudaStream_t)stream));
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_adjoint(selr_plan *p, int32_t axis, const void *E, void *x_out, selr_stream stream) {
+    if (!p || !E || !x_out) return SELR_ERR_INVALID_ARG;
+    const int gi = group_index(p, axis);
+    if (gi < 0) return SELR_ERR_INVALID_ARG;
+    GroupSet s = single_group(p, gi);
+    s.g[0].dst = (cf *)x_out;
+    CK(launch_adjoint(s, 0, 0, s.total, (const cf *)E, 1, (cudaStream_t)stream));
+    return SELR_OK;
+}
+
+static SvtArgs svt_args(selr_plan *p) {
+    SvtArgs a;
+    memset(&a, 0, sizeof(a));
+    a.W = p->W;
+    a.B0 = p->B0;
+    a.sigma = p->sigma;
+    a.mat_status = p->mat_status;
+    a.status = p->status;
+    a.max_sweeps = p->d.jacobi_max_sweeps;
+    a.tol = p->d.jacobi_tol;
+    a.beta = p->d.beta;
+    a.tau = p->d.tau;
+    return a;
+}
+
+extern "C" selr_status selr_svt(selr_plan *p, void *A, int32_t nmat, int32_t rows, int32_t cols, float thresh,
+                                int32_t *rank_out, selr_stream stream) {
+    if (!p || !A || nmat < 1 || rows < 1 || cols < 1 || !(thresh >= 0.f) || !isfinite(thresh))
+        return SELR_ERR_INVALID_ARG;
+    GroupSet s;
+    memset(&s, 0, sizeof(s));
+    s.n = 1;
+    Group &g = s.g[0];
+    g.kind = G_ROW;
+    g.nmat = nmat;
+    g.rows = rows;
+    g.cols = cols;
+    g.trans = cols > rows ? 1 : 0;
+    g.s = g.trans ? rows : cols;
+    g.len = g.trans ? cols : rows;
+    g.thresh = thresh;
+    finish_set(&s);
+    if (g.len > 512 || g.s > 1024) return SELR_ERR_SHAPE;
+    if ((long long)nmat * rows * cols > p->lift_elems || (long long)nmat * g.s > p->vec_elems || nmat > p->gs.total)
+        return SELR_ERR_SHAPE;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_natural_to_vm(s, (const cf *)A, p->W, p->B0, st));
+    SvtArgs a = svt_args(p);
+    a.mode = 0;
+    a.Zout = (cf *)A;
+    a.z_natural = 1;
+    a.rank_out = rank_out;
+    CK(launch_jacobi(s, 0, nmat, a, st));
+    CK(launch_svt_apply(s, 0, nmat, a, st));
+    return SELR_OK;
+}
+
+// FFTs of the adjoints to k-space, the pointwise solve and the reduction.
+static cudaError_t dc_step(selr_plan *p, const cf *Y, const uint8_t *mask, cf *adj_a, cf *adj_b, cf *K,
+                           const int *active, int *active_next, cudaStream_t st) {
+    cudaError_t e;
+    if (p->model2d) {
+        if ((e = transform(p, 0, 0, adj_a, adj_a, st)) != cudaSuccess) return e;
+        if ((e = transform(p, 1, 0, adj_b, adj_b, st)) != cudaSuccess) return e;
+    } else {
+        if ((e = transform(p, 1, 0, adj_b, adj_b, st)) != cudaSuccess) return e;
+    }
+    DcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.model2d = p->model2d;
+    a.L = p->L; a.J = p->J; a.M = p->M; a.N = p->N;
+    a.Y = Y; a.mask = mask; a.a = adj_a; a.b = adj_b; a.K = K;
+    a.da = p->da; a.db = p->db;
+    a.lambda = p->d.lambda;
+    a.beta = p->d.beta;
+    a.partial = p->partial;
+    a.active = active;
+    a.status = p->status;
+    if ((e = launch_dc(a, st)) != cudaSuccess) return e;
+    return launch_rel_finalize(p->partial, p->M, !p->model2d, p->d.tol, p->rel, active_next, st);
+}
+
+extern "C" selr_status selr_dc(selr_plan *p, const void *Y, const uint8_t *mask, void *adj_a, void *adj_b,
+                               void *K, float *rel_out, selr_stream stream) {
+    if (!p || !Y || !mask || !adj_a || !adj_b || !K) return SELR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(dc_step(p, (const cf *)Y, mask, (cf *)adj_a, (cf *)adj_b, (cf *)K, nullptr, nullptr, st));
+    if (rel_out) CK(cudaMemcpyAsync(rel_out, p->rel, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return SELR_OK;
+}
+
+static cudaError_t prof_mark(selr_plan *p, int it, int stage, int end, cudaStream_t st) {
+    if (!p->prof_on || it < 0 || it >= p->prof_cap) return cudaSuccess;
+    return cudaEventRecordWithFlags(p->ev[((size_t)it * NSTAGE + stage) * 2 + end], st, cudaEventRecordExternal);
+}
+
+static cudaError_t prof_reserve(selr_plan *p, int iters) {
+    if (iters <= p->prof_cap) return cudaSuccess;
+    cudaEvent_t *ev = (cudaEvent_t *)calloc((size_t)iters * NSTAGE * 2, sizeof(cudaEvent_t));
+    if (!ev) return cudaErrorMemoryAllocation;
+    for (size_t i = 0; i < (size_t)p->prof_cap * NSTAGE * 2; ++i) ev[i] = p->ev[i];
+    for (size_t i = (size_t)p->prof_cap * NSTAGE * 2; i < (size_t)iters * NSTAGE * 2; ++i) {
+        cudaError_t e = cudaEventCreate(&ev[i]);
+        if (e != cudaSuccess) {
+            for (size_t k = (size_t)p->prof_cap * NSTAGE * 2; k < i; ++k) cudaEventDestroy(ev[k]);
+            free(ev);
+            return e;
+        }
+    }
+    free(p->ev);
+    p->ev = ev;
+    p->prof_cap = iters;
+    return cudaSuccess;
+}
+
+#define PM(stage, end)                                                         \
+    do {                                                                       \
+        if ((e = prof_mark(p, it, stage, end, st)) != cudaSuccess) return e;   \
+    } while (0)
+
+// One ADMM iteration (X, then Z and D) on the plan's state.  `it` indexes the
+// profiling events (ignored unless profiling is on).
+static cudaError_t admm_iteration(selr_plan *p, const cf *Y, const uint8_t *mask, cudaStream_t st, int it) {
+    cudaError_t e;
+    const bool plain = p->d.exec == SELR_EXEC_PLAIN;
+    const int *act = p->model2d ? nullptr : p->active;
+    int *act_next = p->model2d ? nullptr : p->active_next;
+    const int total = p->gs.total;
+    // X-update: adjoint of (Z - D/beta), then Eq. 15 / S7
+    PM(0, 0);
+    if (plain) {
+        for (int m = 0; m < total; ++m)
+            if ((e = launch_adjoint(p->gs, 0, m, 1, p->E, 0, st)) != cudaSuccess) return e;
+    } else if ((e = launch_adjoint(p->gs, 0, 0, total, p->E, 0, st)) != cudaSuccess) return e;
+    PM(0, 1);
+    PM(1, 0);
+    if ((e = dc_step(p, Y, mask, p->adjA, p->adjB, p->K, act, act_next, st)) != cudaSuccess) return e;
+    PM(1, 1);
+    // lift sources
+    PM(2, 0);
+    if (p->model2d) {
+        if ((e = transform(p, 0, 1, p->K, p->hybA, st)) != cudaSuccess) return e;
+        if ((e = transform(p, 1, 1, p->K, p->hybB, st)) != cudaSuccess) return e;
+    } else {
+        if ((e = transform(p, 1, 1, p->K, p->hybB, st)) != cudaSuccess) return e;
+    }
+    PM(2, 1);
+    SvtArgs a = svt_args(p);
+    a.mode = 1;
+    a.D = p->D;
+    a.E = p->E;
+    a.active = act;
+    const float ib = 1.0f / p->d.beta;
+    if (plain) {
+        // per matrix: lift, SVD and apply launched one matrix at a time
+        PM(3, 0);
+        for (int m = 0; m < total; ++m) {
+            if ((e = launch_lift(p->gs, 0, m, 1, p->D, 0, ib, p->W, p->B0, 0, act, st)) != cudaSuccess) return e;
+            if ((e = launch_jacobi(p->gs, m, 1, a, st)) != cudaSuccess) return e;
+            if ((e = launch_svt_apply(p->gs, m, 1, a, st)) != cudaSuccess) return e;
+        }
+        PM(3, 1);
+    } else {
+        PM(3, 0);
+        if ((e = launch_lift(p->gs, 0, 0, total, p->D, 0, ib, p->W, p->B0, 0, act, st)) != cudaSuccess) return e;
+        PM(3, 1);
+        PM(4, 0);
+        if ((e = launch_jacobi(p->gs, 0, total, a, st)) != cudaSuccess) return e;
+        PM(4, 1);
+        PM(5, 0);
+        if ((e = launch_svt_apply(p->gs, 0, total, a, st)) != cudaSuccess) return e;
+        PM(5, 1);
+    }
+    if (!p->model2d) {
+        if ((e = launch_copy_active(p->active_next, p->active, p->M, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t admm_init(selr_plan *p, const cf *Y, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(p->K, Y, sizeof(cf) * p->nK, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = launch_fill(p->D, p->lift_elems, mk(p->d.d_init, 0.f), st)) != cudaSuccess) return e;
+    if ((e = launch_fill(p->E, p->lift_elems, mk(-p->d.d_init / p->d.beta, 0.f), st)) != cudaSuccess) return e;
+    if ((e = launch_fill_i(p->active, p->M, 1, st)) != cudaSuccess) return e;
+    return launch_fill_i(p->active_next, p->M, 1, st);
+}
+
+static cudaError_t output_image(selr_plan *p, cf *X, cudaStream_t st) {
+    cudaError_t e;
+    if (p->model2d) {
+        if ((e = transform(p, 1, 1, p->K, X, st)) != cudaSuccess) return e;
+        return transform(p, 0, 1, X, X, st);
+    }
+    return transform(p, 1, 1, p->K, X, st);
+}
+
+extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *mask, void *X_out,
+                                  int32_t *iters_out, float *rel_out, selr_stream stream) {
+    if (!p || !Yv || !mask || !X_out) return SELR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const cf *Y = (const cf *)Yv;
+    CK(admm_init(p, Y, st));
+    int iters = 0;
+    float last_rel = -1.f;
+    const bool fixed = p->d.tol < 0.f;
+    const bool use_graph = fixed && p->d.exec == SELR_EXEC_BATCHED && st != 0;
+    if (p->prof_on) CK(prof_reserve(p, p->d.max_iter));
+    const int giters = p->prof_on ? p->d.max_iter : 1;
+    if (use_graph) {
+        if (!p->graph || p->graph_Y != Yv || p->graph_mask != mask || p->graph_stream != st ||
+            p->graph_iters != giters) {
+            if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < giters && e == cudaSuccess; ++k) e = admm_iteration(p, Y, mask, st, k);
+            cudaError_t e2 = cudaStreamEndCapture(st, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (e2 == cudaSuccess) cudaGraphDestroy(g);
+                return SELR_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&p->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { p->graph = nullptr; return SELR_ERR_CUDA; }
+            p->graph_Y = Yv;
+            p->graph_mask = mask;
+            p->graph_stream = st;
+            p->graph_iters = giters;
+        }
+        for (int k = 0; k < p->d.max_iter; k += giters) CK(cudaGraphLaunch(p->graph, st));
+        iters = p->d.max_iter;
+    } else {
+        for (int k = 0; k < p->d.max_iter; ++k) {
+            CK(admm_iteration(p, Y, mask, st, k));
+            ++iters;
+            if (!fixed) {
+                CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float), cudaMemcpyDeviceToHost, st));
+                if (!p->model2d) CK(cudaMemcpyAsync(p->h_active, p->active, sizeof(int) * p->M, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                last_rel = p->h_rel[0];
+                if (p->model2d) {
+                    if (last_rel < p->d.tol) break;
+                } else {
+                    int any = 0;
+                    for (int m = 0; m < p->M; ++m) any |= p->h_active[m];
+                    if (!any) break;
+                }
+            }
+        }
+    }
+    p->prof_count = p->prof_on ? (iters < p->prof_cap ? iters : p->prof_cap) : 0;
+    CK(output_image(p, (cf *)X_out, st));
+    if (rel_out || iters_out) {
+        if (rel_out && fixed) {
+            CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            last_rel = p->h_rel[0];
+        }
+        if (rel_out) *rel_out = last_rel;
+        if (iters_out) *iters_out = iters;
+    }
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_set_iterations(selr_plan *p, int32_t max_iter, float tol) {
+    if (!p || max_iter < 1 || !isfinite(tol)) return SELR_ERR_INVALID_ARG;
+    p->d.max_iter = max_iter;
+    p->d.tol = tol;
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_profile_enable(selr_plan *p, int32_t on) {
+    if (!p) return SELR_ERR_INVALID_ARG;
+    p->prof_on = on ? 1 : 0;
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_profile_read(selr_plan *p, int32_t stage, float *total_ms, int32_t *count) {
+    if (!p || stage < 0 || stage >= NSTAGE || !total_ms) return SELR_ERR_INVALID_ARG;
+    float tot = 0.f;
+    const bool plain = p->d.exec == SELR_EXEC_PLAIN;
+    int n = 0;
+    for (int it = 0; it < p->prof_count; ++it) {
+        if (plain && (stage == 4 || stage == 5)) break;   // folded into stage 3 in plain mode
+        const cudaEvent_t a = p->ev[((size_t)it * NSTAGE + stage) * 2];
+        const cudaEvent_t b = p->ev[((size_t)it * NSTAGE + stage) * 2 + 1];
+        if (cudaEventSynchronize(b) != cudaSuccess) return SELR_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return SELR_ERR_CUDA;
+        tot += ms;
+        ++n;
+    }
+    *total_ms = tot;
+    if (count) *count = n;
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_sync_status(selr_plan *p, selr_stream stream) {
+    if (!p) return SELR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SELR_ERR_CUDA;
+    unsigned h = 0;
+    if (cudaMemcpy(&h, p->status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return SELR_ERR_CUDA;
+    if (cudaMemset(p->status, 0, sizeof(unsigned)) != cudaSuccess) return SELR_ERR_CUDA;
+    if (h & ST_NONFINITE) return SELR_ERR_NONFINITE;
+    if (h & ST_NOCONV) return SELR_ERR_NO_CONVERGENCE;
+    return SELR_OK;
+}

@@ -1,0 +1,165 @@
+// Internal declarations shared by the translation units of libselr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/selr.h"
+
+// ---------------------------------------------------------------- complex
+struct __align__(8) cf {
+    float x, y;
+};
+
+__host__ __device__ __forceinline__ cf mk(float a, float b) { cf r; r.x = a; r.y = b; return r; }
+__host__ __device__ __forceinline__ cf cadd(cf a, cf b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cf csub(cf a, cf b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cf cmul(cf a, cf b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// conj(a) * b
+__host__ __device__ __forceinline__ cf cmulc(cf a, cf b) { return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+__host__ __device__ __forceinline__ cf cconj(cf a) { return mk(a.x, -a.y); }
+__host__ __device__ __forceinline__ cf cscale(cf a, float s) { return mk(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float cabs2(cf a) { return a.x * a.x + a.y * a.y; }
+
+// --------------------------------------------------------------- lift groups
+enum { G_ROW = 0, G_COL = 1, G_PE = 2, G_PARAM = 3 };
+#define SELR_MAX_GROUPS 4
+
+// One family of lifted matrices (all rows, all columns, all PE or all
+// parameter lifts).  A matrix is rows x cols = (nv - p + 1) x (C * p).
+// Internal storage of lifted arrays is "vector-major": the s vectors of the
+// shorter side, each of length len, contiguous.  trans = 0: vectors are the
+// columns of A (cols <= rows); trans = 1: vectors are the rows of A.
+struct Group {
+    int kind;
+    int nmat;
+    int nv, p, J, C, vc;
+    int rows, cols;
+    int trans;
+    int s, len;
+    float thresh;          // SVT threshold of this family
+    int M, N, L;           // array dims of the source / adjoint arrays
+    long long off;         // element offset of matrix 0 in lifted workspaces
+    long long soff;        // offset of matrix 0 in per-vector arrays (sigma)
+    int moff;              // index of matrix 0 among all matrices (status words)
+    const cf *w;           // weights (length nv) or nullptr (identity)
+    const cf *src;         // lift source array
+    cf *dst;               // adjoint destination array
+};
+
+struct GroupSet {
+    int n;
+    int total;                       // total matrices
+    int start[SELR_MAX_GROUPS + 1];  // prefix sums of nmat
+    Group g[SELR_MAX_GROUPS];
+};
+
+__device__ __forceinline__ int find_group(const GroupSet &gs, int mat_global, int *local) {
+    int gi = 0;
+#pragma unroll
+    for (int k = 1; k < SELR_MAX_GROUPS; ++k)
+        if (k < gs.n && mat_global >= gs.start[k]) gi = k;
+    *local = mat_global - gs.start[gi];
+    return gi;
+}
+
+// Address of element `pos` of the vector of coil j belonging to matrix `mat`.
+__device__ __forceinline__ long long src_index(const Group &g, int mat, int j, int pos) {
+    const long long M = g.M, N = g.N;
+    switch (g.kind) {
+        case G_ROW:   return ((long long)j * M + mat) * N + pos;                 // [J][M][N], row m = mat
+        case G_COL:   return ((long long)j * M + pos) * N + mat;                 // column n = mat
+        case G_PE: {  int m = mat / g.L, l = mat % g.L;                          // (m, l), along n
+                      return (((long long)l * g.J + j) * M + m) * N + pos; }
+        default: {    int m = mat / g.N, n = mat % g.N;                          // (m, n), along l
+                      return (((long long)pos * g.J + j) * M + m) * N + n; }
+    }
+}
+
+// Element (r, c) of matrix `mat` in vector-major storage (relative to group).
+__device__ __forceinline__ long long vm_index(const Group &g, int mat, int r, int c) {
+    const long long base = (long long)mat * g.s * g.len;
+    return g.trans ? base + (long long)r * g.len + c : base + (long long)c * g.len + r;
+}
+
+// Lifted value lift(x)[mat][r][c] (Eq. 2 / Eq. 4 / Eq. 7).
+__device__ __forceinline__ cf lift_value(const Group &g, int mat, int r, int c) {
+    const int ch = c / g.p, q = c - ch * g.p, pos = r + q;
+    cf v;
+    if (ch < g.J) {
+        v = g.src[src_index(g, mat, ch, pos)];
+    } else {
+        v = cconj(g.src[src_index(g, mat, ch - g.J, g.nv - 1 - pos)]);
+    }
+    if (g.w) v = cmul(g.w[pos], v);
+    return v;
+}
+
+// ---------------------------------------------------------- status words
+enum { ST_NOCONV = 1, ST_NONFINITE = 2 };
+
+// --------------------------------------------------------------- launchers
+// fft.cu
+struct FftTable {
+    int n;
+    int nst;
+    int radix[24];
+    const cf *tw;   // tw[k] = exp(-2 pi i k / n), k < n
+};
+cudaError_t fft_table_build(int n, FftTable *t, cf **tw_dev);
+cudaError_t fft_init_attributes();
+// Transform along dim of [outer][n][inner] (element (o,k,i) at (o*n+k)*inner+i).
+cudaError_t launch_fft(const cf *in, cf *out, const FftTable &t, long long outer, long long inner,
+                       int inverse, cudaStream_t st);
+
+// lift.cu
+// mode 0: write natural layout [mat][rows][cols]; mode 1: vector-major (also copy to out2 if non-null)
+cudaError_t launch_lift(const GroupSet &gs, int gfirst, int mat_begin, int mat_count, const cf *D,
+                        int d_natural, float inv_beta, cf *out, cf *out2, int out_natural,
+                        const int *active, cudaStream_t st);
+cudaError_t launch_adjoint(const GroupSet &gs, int gfirst, int mat_begin, int mat_count,
+                           const cf *E, int e_natural, cudaStream_t st);
+cudaError_t launch_natural_to_vm(const GroupSet &gs, const cf *A, cf *out, cf *out2, cudaStream_t st);
+
+// svt.cu
+struct SvtArgs {
+    cf *W;               // vector-major working copy (orthogonalised in place)
+    const cf *B0;        // vector-major original matrices
+    float *sigma;        // per-vector singular values
+    int *mat_status;     // per-matrix sweeps used (negative = not converged)
+    unsigned *status;    // plan status word (ST_* bits)
+    int max_sweeps;
+    float tol;
+    // apply epilogue
+    int mode;            // 0: write Z (natural if z_natural, else vector-major) ; 1: ADMM D/E update
+    cf *Zout; int z_natural;
+    cf *D; cf *E;        // vector-major
+    float beta, tau;
+    int *rank_out;
+    const int *active;   // per-FE-position activity (parameter models) or nullptr
+};
+cudaError_t svt_init_attributes();
+cudaError_t launch_jacobi(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
+cudaError_t launch_svt_apply(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
+
+// dc.cu
+struct DcArgs {
+    int model2d;
+    int L, J, M, N;
+    const cf *Y; const uint8_t *mask;
+    const cf *a; const cf *b;     // already in k-space
+    cf *K;
+    const float *da;              // 2D: d_r(k_n) [N]; param: d_pe(k_n) [N]
+    const float *db;              // 2D: d_c(k_m) [M]; param: c_p(l) [L]
+    float lambda, beta;
+    double *partial;              // [M][2]
+    const int *active;            // per m or nullptr
+    unsigned *status;
+};
+cudaError_t launch_dc(const DcArgs &a, cudaStream_t st);
+cudaError_t launch_rel_finalize(const double *partial, int M, int per_m, float tol, float *rel,
+                                int *active_next, cudaStream_t st);
+cudaError_t launch_fill(cf *p, long long n, cf v, cudaStream_t st);
+cudaError_t launch_fill_i(int *p, long long n, int v, cudaStream_t st);
+cudaError_t launch_copy_active(const int *src, int *dst, int n, cudaStream_t st);

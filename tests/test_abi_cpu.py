@@ -1,0 +1,70 @@
+"""C-ABI checks that need no GPU.
+
+* libselr.so builds (nvcc cross-compiles for sm_103a) and loads.
+* It exports every function declared in include/selr.h.
+* Descriptor validation rejects bad arguments before any CUDA call.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2107_11650_gb300 import build
+from paper_2107_11650_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "selr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(selr_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(_lib.SIGNATURES), set(names) - set(_lib.SIGNATURES)
+
+
+def test_status_strings(lib):
+    for code, name in _lib.STATUS_NAMES.items():
+        assert lib.selr_status_string(code).decode() == name
+
+
+def _desc(lib, **kw):
+    d = _lib.SelrDesc()
+    lib.selr_desc_default(ctypes.byref(d))
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(model=7), 1), (dict(J=0), 1), (dict(beta=0.0), 1), (dict(tau=-1.0), 1), (dict(max_iter=0), 1),
+    (dict(weight=3), 1), (dict(exec_=5), 1), (dict(jacobi_tol=0.0), 1), (dict(lambda2=-1.0), 1),
+    (dict(M=63), 2), (dict(N=14 * 7), 2), (dict(window=65), 2), (dict(L=2), 2),
+    (dict(model=3, L=8, window_param=9, N=64), 2), (dict(model=2, L=8, window_param=4, N=66 * 7), 2),
+])
+def test_descriptor_validation(lib, kw, code):
+    d = _desc(lib, **kw)
+    h = ctypes.c_void_p()
+    assert lib.selr_plan_create(ctypes.byref(d), ctypes.byref(h)) == code
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    assert lib.selr_plan_create(None, None) == 1
+    assert lib.selr_plan_destroy(None) == 0
+    assert lib.selr_sync_status(None, None) == 1
+    assert lib.selr_solve(None, None, None, None, None, None, None) == 1
+    assert lib.selr_plan_workspace_bytes(None) == 0

@@ -1,0 +1,173 @@
+"""End-to-end GPU parity of selr_solve (Algorithms S1 / S2) against the oracle.
+
+Bar: ||X_gpu - X_oracle||_F / ||X_oracle||_F <= 1e-4 after the same fixed
+number of iterations (FP32 CUDA path vs FP64 oracle), for the batched
+(graph-captured) and the plain per-matrix execution modes.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+from oracle import admm as oadmm
+from oracle.transforms import ifft2c
+from oracle.metrics import rel_l2, rlne, ssos
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_11650_gb300 import build
+    build()
+
+
+def _api():
+    from paper_2107_11650_gb300 import api
+    return api
+
+
+def _dev(a, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _solve_gpu(wl, Y, mask, exec_mode="batched", n_iter=None, tol=-1.0, stream=True):
+    api = _api()
+    d = api.Desc.from_workload(wl, exec=exec_mode, tol=tol)
+    if n_iter is not None:
+        d.max_iter = n_iter
+    plan = api.Plan(d)
+    Yd = _dev(Y)
+    md = _dev(mask, torch.uint8)
+    X = torch.empty_like(Yd)
+    s = torch.cuda.Stream() if stream else torch.cuda.default_stream()
+    with torch.cuda.stream(s):
+        it, rel = api.selr_solve(plan, Yd, md, X, stream=s)
+    st = api.selr_sync_status(plan, s)
+    return X.cpu().numpy().astype(np.complex128), it, rel, st, plan
+
+
+def _oracle_2d(wl, Y, mask, n_iter):
+    X, K, rels = oadmm.shlr(Y, mask, wl, n_iter=n_iter)
+    return X
+
+
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_shlr_small_workload_30_iterations(exec_mode):
+    wl = synth.get_config("shlr_4c_64")
+    inp = synth.make_inputs(wl)
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], exec_mode)
+    assert st == 0 and it == 30
+    Xo = _oracle_2d(wl, inp["Y"], inp["mask"], 30)
+    err = rel_l2(X, Xo)
+    assert err < TOL, err
+    # the reconstruction is a reconstruction
+    assert rlne(ssos(inp["truth"]), ssos(X)) < 0.8 * rlne(ssos(inp["truth"]), ssos(ifft2c(inp["Y"])))
+
+
+def test_shlr_v_poisson_reduced():
+    wl = synth.get_config("shlrv_12c_256").with_(J=4, M=64, N=64, window=8, n_iter=12)
+    inp = synth.make_inputs(wl)
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"])
+    assert st == 0
+    Xo = _oracle_2d(wl, inp["Y"], inp["mask"], 12)
+    assert rel_l2(X, Xo) < TOL
+
+
+def test_shlr_rectangular_ragged():
+    # M != N, window not dividing anything, W = identity, finite lambda
+    wl = synth.Workload(name="rag", model="SHLR_V", J=3, M=48, N=30, window=7, weight=0, mask="random1d",
+                        R=2.5, n_acs=6, sigma_n=1e-3, seed=11, lam=300.0, beta=10.0, tau=10.0, n_iter=10)
+    inp = synth.make_inputs(wl)
+    for mode in ("batched", "plain"):
+        X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], mode)
+        assert st == 0
+        assert rel_l2(X, _oracle_2d(wl, inp["Y"], inp["mask"], 10)) < TOL
+
+
+def test_shlr_hard_dc_and_default_stream():
+    wl = synth.get_config("shlr_4c_64").with_(lam=0.0, n_iter=8)
+    inp = synth.make_inputs(wl)
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], stream=False)
+    assert st == 0
+    assert rel_l2(X, _oracle_2d(wl, inp["Y"], inp["mask"], 8)) < TOL
+
+
+@pytest.mark.parametrize("model", ["SHLR_VP", "SHLR_P"])
+def test_parameter_model_reduced(model):
+    wl = synth.get_config("shlrvp_8c_192_8e").with_(model=model, J=2, M=8, N=48, window=8, n_iter=10)
+    inp = synth.make_inputs(wl)
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"])
+    assert st == 0
+    Xo, K, iters = oadmm.shlr_p(inp["Y"], inp["mask"], wl, n_iter=10)
+    assert rel_l2(X, Xo) < TOL
+
+
+def test_parameter_model_per_position_stopping():
+    wl = synth.get_config("shlrvp_8c_192_8e").with_(J=2, M=6, N=48, window=8, n_iter=40)
+    inp = synth.make_inputs(wl)
+    tol = 1e-4
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], tol=tol)
+    Xo, K, iters = oadmm.shlr_p(inp["Y"], inp["mask"], wl, n_iter=40, tol=tol)
+    assert it == iters.max()
+    assert rel_l2(X, Xo) < 10 * TOL
+
+
+def test_stopping_rule_2d():
+    wl = synth.get_config("shlr_4c_64").with_(n_iter=50)
+    inp = synth.make_inputs(wl)
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], tol=1e-6)
+    s = oadmm.Shlr2D(inp["Y"], inp["mask"], wl)
+    _, rels = s.run(50, tol=1e-6)
+    assert it == len(rels)
+    assert rel < 1e-6
+
+
+def test_full_sampling_hard_dc_fixed_point_full_size():
+    wl = synth.get_config("shlr_12c_256").with_(mask="full", lam=0.0, n_iter=2)
+    inp = synth.make_inputs(wl)
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"])
+    assert st == 0
+    assert rel_l2(X, ifft2c(inp["Y"])) < 1e-6
+
+
+def test_shlr_full_size_two_iterations():
+    """12-coil 256x256 workload, the exact launch configuration the benchmark
+    times (batched, graph-captured), against two full oracle iterations."""
+    wl = synth.get_config("shlr_12c_256")
+    inp = synth.make_inputs(wl)
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], n_iter=2)
+    assert st == 0
+    Xo = _oracle_2d(wl, inp["Y"], inp["mask"], 2)
+    assert rel_l2(X, Xo) < TOL
+
+
+def test_device_status_reports_sweep_cap_and_nonfinite():
+    api = _api()
+    wl = synth.get_config("shlr_4c_64").with_(n_iter=2)
+    inp = synth.make_inputs(wl)
+    d = api.Desc.from_workload(wl, jacobi_max_sweeps=1)
+    plan = api.Plan(d)
+    X = torch.empty_like(_dev(inp["Y"]))
+    api.selr_solve(plan, _dev(inp["Y"]), _dev(inp["mask"], torch.uint8), X)
+    assert api.selr_sync_status(plan) == 4          # SELR_ERR_NO_CONVERGENCE
+    assert api.selr_sync_status(plan) == 0          # cleared by the read
+    Y = inp["Y"].copy()
+    Y[0, 32, 32] = np.nan
+    plan2 = api.Plan(api.Desc.from_workload(wl))
+    api.selr_solve(plan2, _dev(Y), _dev(inp["mask"], torch.uint8), X)
+    assert api.selr_sync_status(plan2) == 5         # SELR_ERR_NONFINITE
+
+
+def test_batched_and_plain_agree_bitwise_repeatable():
+    wl = synth.get_config("shlr_4c_64").with_(n_iter=5)
+    inp = synth.make_inputs(wl)
+    X1, *_ = _solve_gpu(wl, inp["Y"], inp["mask"], "batched")
+    X2, *_ = _solve_gpu(wl, inp["Y"], inp["mask"], "batched")
+    X3, *_ = _solve_gpu(wl, inp["Y"], inp["mask"], "plain")
+    np.testing.assert_array_equal(X1, X2)          # deterministic run to run
+    np.testing.assert_array_equal(X1, X3)          # same kernels, same order per matrix
