@@ -186,8 +186,9 @@ selr_status selr_set_iterations(selr_plan *plan, int32_t max_iter, float tol);
  * pointwise solve and its reduction), 2 hybrid transforms, 3 lifts,
  * 4 Jacobi SVD, 5 SVT apply + multiplier update.
  * selr_profile_enable(plan, on): when on, the following selr_solve calls
- * record CUDA events around every stage of every iteration (in batched mode
- * the whole solve, events included, is captured as one CUDA graph).
+ * record CUDA events on `stream` around every stage of every iteration (in
+ * batched mode each stage is captured as its own CUDA graph and the events
+ * are recorded between graph launches).
  * selr_profile_read(plan, stage, total_ms, count): host outputs with the
  * summed duration of `stage` over the last profiled solve and the number of
  * iterations timed; synchronises on the recorded events. */
@@ -198,6 +199,10 @@ selr_status selr_profile_read(selr_plan *plan, int32_t stage, float *total_ms, i
  * since the last call (SELR_ERR_NO_CONVERGENCE, SELR_ERR_NONFINITE), or
  * SELR_ERR_CUDA if the stream reports an error; clears the record. */
 selr_status selr_sync_status(selr_plan *plan, selr_stream stream);
+
+/* Name of the last CUDA runtime error behind a SELR_ERR_CUDA returned on
+ * the calling host thread (diagnostics; static storage). */
+const char *selr_last_error_string(void);
 
 /* Static, human-readable name of a status code. */
 const char *selr_status_string(selr_status status);

@@ -51,6 +51,7 @@ SIGNATURES = {
     "selr_profile_enable": (c_int32, [c_void_p, c_int32]),
     "selr_profile_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_float), ctypes.POINTER(c_int32)]),
     "selr_status_string": (ctypes.c_char_p, [c_int32]),
+    "selr_last_error_string": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -83,4 +84,6 @@ class SelrError(RuntimeError):
 
 def check(code, where):
     if code != SELR_OK:
+        if code == 3 and _lib is not None:
+            where = f"{where} ({_lib.selr_last_error_string().decode()})"
         raise SelrError(code, where)

@@ -34,20 +34,29 @@ struct selr_plan {
     const void *graph_Y;
     const uint8_t *graph_mask;
     cudaStream_t graph_stream;
-    int graph_iters;          // iterations captured in `graph` (1, or max_iter when profiling)
+    int graph_iters;          // 1: `graph` holds one iteration; 0: per-stage graphs (profiling)
     // stage profiling
     int prof_on;
     int prof_cap;             // iterations with events allocated
     cudaEvent_t *ev;          // [prof_cap][NSTAGE][2]
     int prof_count;           // iterations timed by the last solve
+    cudaGraphExec_t stage_graph[8];   // profiling: one graph per stage
 };
 
 #define NSTAGE 6
 
+static void drop_graphs(selr_plan *p);
+
+// Last CUDA error seen by an entry point on this host thread (diagnostics).
+static thread_local cudaError_t g_last_error = cudaSuccess;
+
 #define CK(x)                                          \
     do {                                               \
         cudaError_t e_ = (x);                          \
-        if (e_ != cudaSuccess) return SELR_ERR_CUDA;   \
+        if (e_ != cudaSuccess) {                       \
+            g_last_error = e_;                         \
+            return SELR_ERR_CUDA;                      \
+        }                                              \
     } while (0)
 
 static bool smooth_even(int n) {
@@ -212,7 +221,7 @@ static selr_status upload(void *dst, const void *src, size_t bytes) {
 
 extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     if (!p) return SELR_OK;
-    if (p->graph) cudaGraphExecDestroy(p->graph);
+    drop_graphs(p);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status,
                     p->twM, p->twN, p->wM, p->wN, p->da, p->db};
@@ -484,9 +493,65 @@ extern "C" selr_status selr_dc(selr_plan *p, const void *Y, const uint8_t *mask,
     return SELR_OK;
 }
 
-static cudaError_t prof_mark(selr_plan *p, int it, int stage, int end, cudaStream_t st) {
-    if (!p->prof_on || it < 0 || it >= p->prof_cap) return cudaSuccess;
-    return cudaEventRecordWithFlags(p->ev[((size_t)it * NSTAGE + stage) * 2 + end], st, cudaEventRecordExternal);
+// The six stages of one ADMM iteration (X, then Z and D) on the plan's state:
+//   0 adjoint of (Z - D/beta), 1 X-update (Eq. 15 / S7), 2 lift sources
+//   (hybrid transforms), 3 lifts, 4 Jacobi SVD, 5 SVT apply + D update.
+// In plain mode stage 3 runs lift, SVD and apply one matrix at a time and
+// stages 4 and 5 are empty.
+static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_t *mask, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    const bool plain = p->d.exec == SELR_EXEC_PLAIN;
+    const int *act = p->model2d ? nullptr : p->active;
+    int *act_next = p->model2d ? nullptr : p->active_next;
+    const int total = p->gs.total;
+    SvtArgs a = svt_args(p);
+    a.mode = 1;
+    a.D = p->D;
+    a.E = p->E;
+    a.active = act;
+    const float ib = 1.0f / p->d.beta;
+    switch (stage) {
+        case 0:
+            if (plain) {
+                for (int m = 0; m < total && e == cudaSuccess; ++m) e = launch_adjoint(p->gs, 0, m, 1, p->E, 0, st);
+                return e;
+            }
+            return launch_adjoint(p->gs, 0, 0, total, p->E, 0, st);
+        case 1:
+            return dc_step(p, Y, mask, p->adjA, p->adjB, p->K, act, act_next, st);
+        case 2:
+            if (p->model2d) {
+                if ((e = transform(p, 0, 1, p->K, p->hybA, st)) != cudaSuccess) return e;
+                return transform(p, 1, 1, p->K, p->hybB, st);
+            }
+            return transform(p, 1, 1, p->K, p->hybB, st);
+        case 3:
+            if (plain) {
+                for (int m = 0; m < total; ++m) {
+                    if ((e = launch_lift(p->gs, 0, m, 1, p->D, 0, ib, p->W, p->B0, 0, act, st)) != cudaSuccess) return e;
+                    if ((e = launch_jacobi(p->gs, m, 1, a, st)) != cudaSuccess) return e;
+                    if ((e = launch_svt_apply(p->gs, m, 1, a, st)) != cudaSuccess) return e;
+                }
+                if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->M, st);
+                return cudaSuccess;
+            }
+            return launch_lift(p->gs, 0, 0, total, p->D, 0, ib, p->W, p->B0, 0, act, st);
+        case 4:
+            return plain ? cudaSuccess : launch_jacobi(p->gs, 0, total, a, st);
+        default:
+            if (plain) return cudaSuccess;
+            if ((e = launch_svt_apply(p->gs, 0, total, a, st)) != cudaSuccess) return e;
+            if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->M, st);
+            return cudaSuccess;
+    }
+}
+
+static cudaError_t admm_iteration(selr_plan *p, const cf *Y, const uint8_t *mask, cudaStream_t st) {
+    for (int s = 0; s < NSTAGE; ++s) {
+        cudaError_t e = admm_stage(p, s, Y, mask, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 static cudaError_t prof_reserve(selr_plan *p, int iters) {
@@ -508,68 +573,27 @@ static cudaError_t prof_reserve(selr_plan *p, int iters) {
     return cudaSuccess;
 }
 
-#define PM(stage, end)                                                         \
-    do {                                                                       \
-        if ((e = prof_mark(p, it, stage, end, st)) != cudaSuccess) return e;   \
-    } while (0)
+static void drop_graphs(selr_plan *p) {
+    if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+    for (int s = 0; s < 8; ++s)
+        if (p->stage_graph[s]) { cudaGraphExecDestroy(p->stage_graph[s]); p->stage_graph[s] = nullptr; }
+}
 
-// One ADMM iteration (X, then Z and D) on the plan's state.  `it` indexes the
-// profiling events (ignored unless profiling is on).
-static cudaError_t admm_iteration(selr_plan *p, const cf *Y, const uint8_t *mask, cudaStream_t st, int it) {
-    cudaError_t e;
-    const bool plain = p->d.exec == SELR_EXEC_PLAIN;
-    const int *act = p->model2d ? nullptr : p->active;
-    int *act_next = p->model2d ? nullptr : p->active_next;
-    const int total = p->gs.total;
-    // X-update: adjoint of (Z - D/beta), then Eq. 15 / S7
-    PM(0, 0);
-    if (plain) {
-        for (int m = 0; m < total; ++m)
-            if ((e = launch_adjoint(p->gs, 0, m, 1, p->E, 0, st)) != cudaSuccess) return e;
-    } else if ((e = launch_adjoint(p->gs, 0, 0, total, p->E, 0, st)) != cudaSuccess) return e;
-    PM(0, 1);
-    PM(1, 0);
-    if ((e = dc_step(p, Y, mask, p->adjA, p->adjB, p->K, act, act_next, st)) != cudaSuccess) return e;
-    PM(1, 1);
-    // lift sources
-    PM(2, 0);
-    if (p->model2d) {
-        if ((e = transform(p, 0, 1, p->K, p->hybA, st)) != cudaSuccess) return e;
-        if ((e = transform(p, 1, 1, p->K, p->hybB, st)) != cudaSuccess) return e;
-    } else {
-        if ((e = transform(p, 1, 1, p->K, p->hybB, st)) != cudaSuccess) return e;
+// Capture [s0, s1) stages (or a whole iteration) into an executable graph.
+static cudaError_t capture(selr_plan *p, int s0, int s1, const cf *Y, const uint8_t *mask, cudaStream_t st,
+                           cudaGraphExec_t *out) {
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int s = s0; s < s1 && e == cudaSuccess; ++s) e = admm_stage(p, s, Y, mask, st);
+    cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (e2 == cudaSuccess) cudaGraphDestroy(g);
+        return e != cudaSuccess ? e : e2;
     }
-    PM(2, 1);
-    SvtArgs a = svt_args(p);
-    a.mode = 1;
-    a.D = p->D;
-    a.E = p->E;
-    a.active = act;
-    const float ib = 1.0f / p->d.beta;
-    if (plain) {
-        // per matrix: lift, SVD and apply launched one matrix at a time
-        PM(3, 0);
-        for (int m = 0; m < total; ++m) {
-            if ((e = launch_lift(p->gs, 0, m, 1, p->D, 0, ib, p->W, p->B0, 0, act, st)) != cudaSuccess) return e;
-            if ((e = launch_jacobi(p->gs, m, 1, a, st)) != cudaSuccess) return e;
-            if ((e = launch_svt_apply(p->gs, m, 1, a, st)) != cudaSuccess) return e;
-        }
-        PM(3, 1);
-    } else {
-        PM(3, 0);
-        if ((e = launch_lift(p->gs, 0, 0, total, p->D, 0, ib, p->W, p->B0, 0, act, st)) != cudaSuccess) return e;
-        PM(3, 1);
-        PM(4, 0);
-        if ((e = launch_jacobi(p->gs, 0, total, a, st)) != cudaSuccess) return e;
-        PM(4, 1);
-        PM(5, 0);
-        if ((e = launch_svt_apply(p->gs, 0, total, a, st)) != cudaSuccess) return e;
-        PM(5, 1);
-    }
-    if (!p->model2d) {
-        if ((e = launch_copy_active(p->active_next, p->active, p->M, st)) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
 }
 
 static cudaError_t admm_init(selr_plan *p, const cf *Y, cudaStream_t st) {
@@ -601,33 +625,44 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
     const bool fixed = p->d.tol < 0.f;
     const bool use_graph = fixed && p->d.exec == SELR_EXEC_BATCHED && st != 0;
     if (p->prof_on) CK(prof_reserve(p, p->d.max_iter));
-    const int giters = p->prof_on ? p->d.max_iter : 1;
+    const int prof = p->prof_on;
     if (use_graph) {
-        if (!p->graph || p->graph_Y != Yv || p->graph_mask != mask || p->graph_stream != st ||
-            p->graph_iters != giters) {
-            if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
-            cudaGraph_t g;
-            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = cudaSuccess;
-            for (int k = 0; k < giters && e == cudaSuccess; ++k) e = admm_iteration(p, Y, mask, st, k);
-            cudaError_t e2 = cudaStreamEndCapture(st, &g);
-            if (e != cudaSuccess || e2 != cudaSuccess) {
-                if (e2 == cudaSuccess) cudaGraphDestroy(g);
-                return SELR_ERR_CUDA;
+        if (p->graph_Y != Yv || p->graph_mask != mask || p->graph_stream != st || p->graph_iters != (prof ? 0 : 1) ||
+            (prof ? !p->stage_graph[0] : !p->graph)) {
+            drop_graphs(p);
+            if (prof) {
+                for (int s = 0; s < NSTAGE; ++s) CK(capture(p, s, s + 1, Y, mask, st, &p->stage_graph[s]));
+            } else {
+                CK(capture(p, 0, NSTAGE, Y, mask, st, &p->graph));
             }
-            e = cudaGraphInstantiate(&p->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) { p->graph = nullptr; return SELR_ERR_CUDA; }
             p->graph_Y = Yv;
             p->graph_mask = mask;
             p->graph_stream = st;
-            p->graph_iters = giters;
+            p->graph_iters = prof ? 0 : 1;
         }
-        for (int k = 0; k < p->d.max_iter; k += giters) CK(cudaGraphLaunch(p->graph, st));
+        for (int k = 0; k < p->d.max_iter; ++k) {
+            if (!prof) {
+                CK(cudaGraphLaunch(p->graph, st));
+                continue;
+            }
+            for (int s = 0; s < NSTAGE; ++s) {
+                CK(cudaEventRecord(p->ev[((size_t)k * NSTAGE + s) * 2], st));
+                CK(cudaGraphLaunch(p->stage_graph[s], st));
+                CK(cudaEventRecord(p->ev[((size_t)k * NSTAGE + s) * 2 + 1], st));
+            }
+        }
         iters = p->d.max_iter;
     } else {
         for (int k = 0; k < p->d.max_iter; ++k) {
-            CK(admm_iteration(p, Y, mask, st, k));
+            if (prof) {
+                for (int s = 0; s < NSTAGE; ++s) {
+                    CK(cudaEventRecord(p->ev[((size_t)k * NSTAGE + s) * 2], st));
+                    CK(admm_stage(p, s, Y, mask, st));
+                    CK(cudaEventRecord(p->ev[((size_t)k * NSTAGE + s) * 2 + 1], st));
+                }
+            } else {
+                CK(admm_iteration(p, Y, mask, st));
+            }
             ++iters;
             if (!fixed) {
                 CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -658,6 +693,8 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
     return SELR_OK;
 }
 
+extern "C" const char *selr_last_error_string(void) { return cudaGetErrorString(g_last_error); }
+
 extern "C" selr_status selr_set_iterations(selr_plan *p, int32_t max_iter, float tol) {
     if (!p || max_iter < 1 || !isfinite(tol)) return SELR_ERR_INVALID_ARG;
     p->d.max_iter = max_iter;
@@ -677,7 +714,6 @@ extern "C" selr_status selr_profile_read(selr_plan *p, int32_t stage, float *tot
     const bool plain = p->d.exec == SELR_EXEC_PLAIN;
     int n = 0;
     for (int it = 0; it < p->prof_count; ++it) {
-        if (plain && (stage == 4 || stage == 5)) break;   // folded into stage 3 in plain mode
         const cudaEvent_t a = p->ev[((size_t)it * NSTAGE + stage) * 2];
         const cudaEvent_t b = p->ev[((size_t)it * NSTAGE + stage) * 2 + 1];
         if (cudaEventSynchronize(b) != cudaSuccess) return SELR_ERR_CUDA;

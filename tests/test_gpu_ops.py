@@ -1,10 +1,14 @@
 """GPU parity of each C-ABI operator against the FP64 oracle.
 
 Every comparison runs the CUDA path through the C ABI (ctypes binding) and
-the oracle on the same seeded inputs.  Tolerances are FP32-level: relative
-Frobenius error <= 2e-6 for the linear operators (one or two roundings per
-output, times a modest sum length) and <= 2e-5 for the SVT (Jacobi in FP32,
-stopping at |x^H y| <= 2e-6 ||x|| ||y||).
+the oracle on the same seeded inputs.  Tolerances are FP32-level:
+* linear operators (transform, lift, adjoint, X-update): relative Frobenius
+  error <= 2e-6 / 5e-6 (one or two roundings per output, short sums);
+* SVT: <= 1e-4.  One-sided Jacobi in FP32 perturbs each column by O(u),
+  u = 2^-24, per significant rotation; a column takes about sweeps * (s - 1)
+  of them (15 * 383 here at most), so the backward error is about
+  u * sqrt(5700) ~ 5e-6 of ||B||, and ||Z|| can be a third of ||B|| when the
+  threshold sits inside the spectrum.  The bound keeps a factor ~6 above that.
 """
 import numpy as np
 import pytest
@@ -165,7 +169,7 @@ def test_svt_matches_oracle(shape):
     assert api.selr_sync_status(plan) == 0
     Z = _host(At)
     ref = osvt.svt(A, t)
-    assert rel_l2(Z, ref) < 2e-5, rel_l2(Z, ref)
+    assert rel_l2(Z, ref) < 1e-4, rel_l2(Z, ref)
     np.testing.assert_array_equal(rank.cpu().numpy(), osvt.svt_rank(A, t))
 
 
