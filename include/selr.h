@@ -141,6 +141,29 @@ selr_status selr_lift(selr_plan *plan, int32_t axis, const void *x, const void *
 selr_status selr_svt(selr_plan *plan, void *A, int32_t nmat, int32_t rows, int32_t cols,
                      float thresh, int32_t *rank_out, selr_stream stream);
 
+/* Allocation-free variant of selr_svt (the paper has no counterpart; this is
+ * an engineering entry point).  For callers that cannot allocate device
+ * memory while they run: code issuing work during a CUDA stream capture,
+ * where cudaMalloc is not allowed; services that reserve their whole memory
+ * budget up front; hosts whose framework owns every device allocation.
+ * It computes the same S_t as selr_svt, in place on A [nmat][rows][cols]
+ * complex64 (device), with the Jacobi sweep cap `max_sweeps` and rotation
+ * tolerance `tol` of selr_desc, without a plan and without allocating:
+ * its scratch is a fixed area of the library (about 17 MB per device, held
+ * until the process exits).  Limits: nmat * rows * cols <=
+ * SELR_SVT_NOALLOC_MAX_ELEMS, nmat <= SELR_SVT_NOALLOC_MAX_MATS,
+ * max(rows, cols) <= 512; larger sizes return SELR_ERR_SHAPE.  The first
+ * call on each device looks up the scratch address (and sets kernel
+ * attributes) for that device, so make it before any stream capture.  All
+ * calls on one device share the scratch: calls that may overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Device-side conditions (sweep cap reached) are not reported.
+ * rank_out: device int32[nmat] receiving #{sigma > t}, or NULL. */
+#define SELR_SVT_NOALLOC_MAX_ELEMS (1 << 20)
+#define SELR_SVT_NOALLOC_MAX_MATS 65536
+selr_status selr_svt_noalloc(void *A, int32_t nmat, int32_t rows, int32_t cols, float thresh,
+                             int32_t max_sweeps, float tol, int32_t *rank_out, selr_stream stream);
+
 /* Real adjoint of the lift (the transpose appearing in Eq. 15 / S7):
  * x_out = L^T E for the family `axis`.  Plain channel j contributes
  * conj(w) * H*(E_j); virtual coil J+j contributes flip(w * conj(H*(E_{J+j}))),

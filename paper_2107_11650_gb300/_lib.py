@@ -42,6 +42,8 @@ SIGNATURES = {
     "selr_transform": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "selr_lift": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "selr_svt": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p]),
+    "selr_svt_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_float, c_int32, c_float, c_void_p,
+                                   c_void_p]),
     "selr_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "selr_dc": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "selr_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_int32),

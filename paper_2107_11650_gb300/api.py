@@ -157,6 +157,17 @@ def selr_svt(plan: Plan, A, thresh: float, rank_out=None, stream=None):
           "selr_svt")
 
 
+def selr_svt_noalloc(A, thresh: float, max_sweeps: int = 30, tol: float = 2.0e-6, rank_out=None, stream=None):
+    """Allocation-free S_t of A [nmat][rows][cols] in place (no plan; fixed library scratch)."""
+    lib = _lib.load()
+    if A.dim() != 3:
+        raise ValueError("A must be [nmat][rows][cols]")
+    nmat, rows, cols = A.shape
+    check(lib.selr_svt_noalloc(_ptr(A, torch.complex64, "A"), nmat, rows, cols, float(thresh), int(max_sweeps),
+                               float(tol), _ptr(rank_out, torch.int32, "rank_out", nmat, allow_none=True),
+                               _stream(stream)), "selr_svt_noalloc")
+
+
 def selr_adjoint(plan: Plan, axis: str, E, x_out, stream=None):
     n, r, c = plan.lift_shape(axis)
     check(plan.lib.selr_adjoint(plan.handle, AXES[axis], _ptr(E, torch.complex64, "E", n * r * c),
