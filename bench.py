@@ -98,12 +98,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- GPU arm
-def kernel_launches_per_iteration(model2d, exec_mode, nmat):
-    """Kernels libselr launches per ADMM iteration (mirrors admm_iteration in selr.cu)."""
+def kernel_launches_per_iteration(model2d, exec_mode, nmat, svd="eig"):
+    """Kernels libselr launches per ADMM iteration (mirrors admm_stage in selr.cu):
+    adjoint, FFTs of the adjoints, DC + reduction, hybrid FFTs, lift, SVT kernels."""
+    svt = 3 if svd == "eig" else 2          # gram + heig + apply, or jacobi + apply
+    fft_a = 2 if model2d else 1
     if exec_mode == "batched":
-        per = 1 + (2 if model2d else 1) + 2 + (2 if model2d else 1) + 3
+        per = 1 + fft_a + 2 + fft_a + 1 + svt
     else:
-        per = nmat + (2 if model2d else 1) + 2 + (2 if model2d else 1) + 3 * nmat
+        per = nmat + fft_a + 2 + fft_a + (1 + svt) * nmat
     return per + (0 if model2d else 1)
 
 
@@ -135,7 +138,7 @@ def run_gpu(args, rank, world):
     model2d = wl.model in ("SHLR", "SHLR_V")
     modes = ["batched", "plain"] if args.exec == "both" else [args.exec]
     for mode in modes:
-        plan = api.Plan(api.Desc.from_workload(wl, exec=mode, max_iter=max(args.warmup, 1)))
+        plan = api.Plan(api.Desc.from_workload(wl, exec=mode, max_iter=max(args.warmup, 1), svd=args.svd))
         nmat = sum(plan.lift_shape(a)[0] for a in (("row", "col") if model2d else ("pe", "param")))
         with torch.cuda.stream(stream):
             api.selr_solve(plan, Y, mask, X, stream=stream)           # W warm-up iterations
@@ -168,7 +171,7 @@ def run_gpu(args, rank, world):
         prof = plan.profile_read()
         st2 = api.selr_sync_status(plan, stream)
         results[mode] = dict(ms=ms, steps=steps, status=max(st, st2), nmat=nmat, clocks=clocks, stages=prof,
-                             launches=steps * kernel_launches_per_iteration(model2d, mode, nmat) + 6)
+                             launches=steps * kernel_launches_per_iteration(model2d, mode, nmat, args.svd) + 6)
         plan.profile(False)
         if mode == "batched":
             results["plan"] = plan
@@ -177,8 +180,15 @@ def run_gpu(args, rank, world):
     plan = results["plan"]
     n, r, c = plan.lift_shape("row" if model2d else "pe")
     l, s = max(r, c), min(r, c)
-    jms, jcnt = results["batched"]["stages"]["jacobi"]
-    jac = dict(ms=jms / max(jcnt, 1), flops=results["batched"]["nmat"] * flops_svd_per_matrix(l, s))
+    nm = results["batched"]["nmat"]
+    st_ = results["batched"]["stages"]
+    # algorithmic flops per launch of each SVT stage (8 l s^2 Gram, 36 s^3 eigensolve, 8 l s^2 apply)
+    algo = {"gram": nm * 8.0 * l * s * s, "svd": nm * 36.0 * s ** 3, "apply": nm * 8.0 * l * s * s}
+    if args.svd == "jacobi":
+        algo["svd"] = nm * flops_svd_per_matrix(l, s)
+    dom = max(algo, key=lambda k: st_[k][0])
+    ms_dom = st_[dom][0] / max(st_[dom][1], 1)
+    jac = dict(ms=ms_dom, flops=algo[dom], stage=dom)
     e2e = time_e2e(plan, Yh, mh, stream, reps=2)
     return results, jac, e2e, wl
 
@@ -274,6 +284,7 @@ def main():
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--exec", default="both", choices=["both", "batched", "plain"])
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--svd", default="eig", choices=["eig", "jacobi"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -302,12 +313,15 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "coils": wl.J, "size": [wl.M, wl.N], "window": wl.window,
                    "model": wl.model, "mask": f"{wl.mask} R={wl.R} acs={wl.n_acs}",
-                   "matrices_per_step": b["nmat"], "exec": "batched (graph-captured)",
+                   "matrices_per_step": b["nmat"], "exec": "batched (graph-captured)", "svd": args.svd,
                    "l2": "per-step state (D, E, work copies: 760 MB) exceeds L2; no flush"},
         "plain": ({"value": world * results["plain"]["steps"] / (results["plain"]["ms"] / 1000.0),
                    "ms_per_step": results["plain"]["ms"] / results["plain"]["steps"],
                    "steps": results["plain"]["steps"]} if "plain" in results else None),
-        "roofline": {"bound": "alu", "kernel": "k_jacobi (one-sided Jacobi SVD of all 512 matrices)",
+        "roofline": {"bound": "alu", "kernel": {"gram": "k_gram (Gram matrices of all 512 lifts)",
+                                                "svd": ("k_jacobi (one-sided Jacobi SVD)" if args.svd == "jacobi" else
+                                                        "k_heig (tridiagonal eigensolver, eigenpairs above t^2)"),
+                                                "apply": "k_apply_eig (Z and multiplier update)"}[jac["stage"]],
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": None, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock",
                      "launch_ms": jac["ms"]},

@@ -75,6 +75,13 @@ typedef enum {
     SELR_EXEC_PLAIN = 1    /* one launch per matrix for lift/SVT/adjoint, no graph           */
 } selr_exec;
 
+/* How S_t is computed (both give the exact SVT up to FP32 rounding). */
+typedef enum {
+    SELR_SVD_EIG = 0,     /* Gram matrix + Hermitian eigensolver for the eigenpairs above t^2 only
+                             (Householder tridiagonal, bisection, inverse iteration); default  */
+    SELR_SVD_JACOBI = 1   /* one-sided Jacobi on the lifted matrix (all singular pairs)          */
+} selr_svd_method;
+
 /* Problem description (Sec. III; Algorithms S1 and S2). */
 typedef struct {
     int32_t model;            /* selr_model                                               */
@@ -92,12 +99,14 @@ typedef struct {
     int32_t jacobi_max_sweeps;/* sweep cap of the one-sided Jacobi SVD                    */
     float jacobi_tol;         /* rotate a pair while |x^H y| > tol * ||x|| ||y||          */
     int32_t exec;             /* selr_exec                                                */
+    int32_t svd_method;       /* selr_svd_method                                          */
 } selr_desc;
 
 typedef struct selr_plan selr_plan;   /* opaque; owns its device workspace */
 
 /* Fill *desc with defaults (SHLR, weight 1, beta = tau = 20, lambda = 1e4,
- * lambda2 = 2, d_init = 1, max_iter = 30, tol = -1, 30 sweeps, tol 2e-6). */
+ * lambda2 = 2, d_init = 1, max_iter = 30, tol = -1, 30 sweeps, tol 2e-6,
+ * batched, SELR_SVD_EIG). */
 void selr_desc_default(selr_desc *desc);
 
 /* Validate *desc and allocate the plan's device workspace on the current
@@ -207,7 +216,8 @@ selr_status selr_set_iterations(selr_plan *plan, int32_t max_iter, float tol);
 /* Stage timing of selr_solve (instrumentation, not part of the method).
  * Stages: 0 lift adjoints, 1 data consistency (FFTs of the adjoints, the
  * pointwise solve and its reduction), 2 hybrid transforms, 3 lifts,
- * 4 Jacobi SVD, 5 SVT apply + multiplier update.
+ * 4 Gram matrices (SELR_SVD_EIG), 5 eigensolver or Jacobi SVD, 6 SVT apply
+ * + multiplier update.  In plain mode stage 3 holds lift, SVD and apply.
  * selr_profile_enable(plan, on): when on, the following selr_solve calls
  * record CUDA events on `stream` around every stage of every iteration (in
  * batched mode each stage is captured as its own CUDA graph and the events

@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "SELR_OK", 1: "SELR_ERR_INVALID_ARG", 2: "SELR_ERR_SHAPE", 3:
 MODELS = {"SHLR": 0, "SHLR_V": 1, "SHLR_P": 2, "SHLR_VP": 3}
 AXES = {"row": 0, "col": 1, "pe": 2, "param": 3}
 EXEC = {"batched": 0, "plain": 1}
+SVD = {"eig": 0, "jacobi": 1}
 
 # Every function declared in include/selr.h, with its ctypes signature.
 c_void_p, c_int32, c_float, c_size_t = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_size_t
@@ -29,7 +30,8 @@ class SelrDesc(ctypes.Structure):
                 ("window", c_int32), ("window_param", c_int32), ("weight", c_int32),
                 ("lambda_", c_float), ("lambda2", c_float), ("beta", c_float), ("tau", c_float),
                 ("d_init", c_float), ("max_iter", c_int32), ("tol", c_float),
-                ("jacobi_max_sweeps", c_int32), ("jacobi_tol", c_float), ("exec_", c_int32)]
+                ("jacobi_max_sweeps", c_int32), ("jacobi_tol", c_float), ("exec_", c_int32),
+                ("svd_method", c_int32)]
 
 
 SIGNATURES = {

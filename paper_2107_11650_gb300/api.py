@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import AXES, EXEC, MODELS, SelrDesc, check
+from ._lib import AXES, EXEC, MODELS, SVD, SelrDesc, check
 
 
 @dataclass
@@ -38,6 +38,7 @@ class Desc:
     jacobi_max_sweeps: int = 30
     jacobi_tol: float = 2.0e-6
     exec: str = "batched"
+    svd: str = "eig"
 
     @classmethod
     def from_workload(cls, w, **over):
@@ -56,6 +57,7 @@ class Desc:
         d.d_init, d.max_iter, d.tol = self.d_init, self.max_iter, self.tol
         d.jacobi_max_sweeps, d.jacobi_tol = self.jacobi_max_sweeps, self.jacobi_tol
         d.exec_ = EXEC[self.exec]
+        d.svd_method = SVD[self.svd]
         return d
 
 
@@ -114,7 +116,7 @@ class Plan:
         check(self.lib.selr_set_iterations(self.handle, int(max_iter), float(tol)), "selr_set_iterations")
         self.desc.max_iter, self.desc.tol = int(max_iter), float(tol)
 
-    STAGES = ("adjoint", "dc", "hybrid_fft", "lift", "jacobi", "apply")
+    STAGES = ("adjoint", "dc", "hybrid_fft", "lift", "gram", "svd", "apply")
 
     def profile(self, on=True):
         check(self.lib.selr_profile_enable(self.handle, 1 if on else 0), "selr_profile_enable")

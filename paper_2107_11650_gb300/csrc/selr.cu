@@ -17,6 +17,10 @@ struct selr_plan {
     long long lift_elems, vec_elems;
     cf *K, *hybA, *hybB, *adjA, *adjB;
     cf *D, *E, *W, *B0;
+    cf *Gp, *V;              // packed Gram matrices / Householder vectors; eigenvectors
+    float *lam;
+    int *rank;
+    long long packed_elems;
     float *sigma;
     int *mat_status;
     double *partial;
@@ -40,10 +44,10 @@ struct selr_plan {
     int prof_cap;             // iterations with events allocated
     cudaEvent_t *ev;          // [prof_cap][NSTAGE][2]
     int prof_count;           // iterations timed by the last solve
-    cudaGraphExec_t stage_graph[8];   // profiling: one graph per stage
+    cudaGraphExec_t stage_graph[8];   // profiling: one graph per stage (NSTAGE <= 8)
 };
 
-#define NSTAGE 6
+#define NSTAGE 7
 
 static void drop_graphs(selr_plan *p);
 
@@ -85,6 +89,7 @@ extern "C" void selr_desc_default(selr_desc *d) {
     d->jacobi_max_sweeps = 30;
     d->jacobi_tol = 2.0e-6f;
     d->exec = SELR_EXEC_BATCHED;
+    d->svd_method = SELR_SVD_EIG;
 }
 
 extern "C" const char *selr_status_string(selr_status s) {
@@ -126,13 +131,15 @@ static Group make_group(int kind, int nmat, int nv, int p, int J, int vc, int M,
 }
 
 static void finish_set(GroupSet *gs) {
-    long long off = 0, soff = 0;
+    long long off = 0, soff = 0, poff = 0;
     int moff = 0;
     gs->start[0] = 0;
     for (int k = 0; k < gs->n; ++k) {
         gs->g[k].off = off;
         gs->g[k].soff = soff;
+        gs->g[k].poff = poff;
         gs->g[k].moff = moff;
+        poff += (long long)gs->g[k].nmat * gs->g[k].s * (gs->g[k].s + 1) / 2;
         off += (long long)gs->g[k].nmat * gs->g[k].rows * gs->g[k].cols;
         soff += (long long)gs->g[k].nmat * gs->g[k].s;
         moff += gs->g[k].nmat;
@@ -151,6 +158,7 @@ static selr_status validate(const selr_desc *d) {
         return SELR_ERR_INVALID_ARG;
     if (d->weight != 0 && d->weight != 1) return SELR_ERR_INVALID_ARG;
     if (d->exec != SELR_EXEC_BATCHED && d->exec != SELR_EXEC_PLAIN) return SELR_ERR_INVALID_ARG;
+    if (d->svd_method != SELR_SVD_EIG && d->svd_method != SELR_SVD_JACOBI) return SELR_ERR_INVALID_ARG;
     const bool two_d = d->model <= SELR_SHLR_V;
     if (two_d) {
         if (d->L != 1) return SELR_ERR_SHAPE;
@@ -222,7 +230,8 @@ static selr_status upload(void *dst, const void *src, size_t bytes) {
 extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     if (!p) return SELR_OK;
     drop_graphs(p);
-    void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->sigma,
+    void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam,
+                    p->rank, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status,
                     p->twM, p->twN, p->wM, p->wN, p->da, p->db};
     for (void *b : bufs)
@@ -264,15 +273,19 @@ extern "C" selr_status selr_plan_create(const selr_desc *d, selr_plan **out) {
     }
     for (int k = 0; k < gs.n; ++k) {
         if (gs.g[k].len > 512 || gs.g[k].s > 1024) { delete p; return SELR_ERR_SHAPE; }
+        if (d->svd_method == SELR_SVD_EIG && gs.g[k].s > 480) { delete p; return SELR_ERR_SHAPE; }
     }
     finish_set(&gs);
     p->lift_elems = 0;
     p->vec_elems = 0;
+    p->packed_elems = 0;
     for (int k = 0; k < gs.n; ++k) {
         p->lift_elems += (long long)gs.g[k].nmat * gs.g[k].rows * gs.g[k].cols;
         p->vec_elems += (long long)gs.g[k].nmat * gs.g[k].s;
+        p->packed_elems += (long long)gs.g[k].nmat * gs.g[k].s * (gs.g[k].s + 1) / 2;
     }
-    if (fft_init_attributes() != cudaSuccess || svt_init_attributes() != cudaSuccess) {
+    if (fft_init_attributes() != cudaSuccess || svt_init_attributes() != cudaSuccess ||
+        eig_init_attributes() != cudaSuccess) {
         delete p;
         return SELR_ERR_CUDA;
     }
@@ -284,7 +297,15 @@ extern "C" selr_status selr_plan_create(const selr_desc *d, selr_plan **out) {
     const size_t kb = sizeof(cf) * (size_t)p->nK;
     AL(p->K, kb); AL(p->hybA, kb); AL(p->hybB, kb); AL(p->adjA, kb); AL(p->adjB, kb);
     const size_t lb = sizeof(cf) * (size_t)p->lift_elems;
-    AL(p->D, lb); AL(p->E, lb); AL(p->W, lb); AL(p->B0, lb);
+    AL(p->D, lb); AL(p->E, lb); AL(p->B0, lb);
+    if (d->svd_method == SELR_SVD_JACOBI) {
+        AL(p->W, lb);
+    } else {
+        AL(p->V, lb);
+        AL(p->Gp, sizeof(cf) * (size_t)p->packed_elems);
+        AL(p->lam, sizeof(float) * (size_t)p->vec_elems);
+        AL(p->rank, sizeof(int) * (size_t)gs.total);
+    }
     AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
     AL(p->mat_status, sizeof(int) * (size_t)gs.total);
     AL(p->partial, sizeof(double) * 2 * (size_t)d->M);
@@ -427,6 +448,35 @@ static SvtArgs svt_args(selr_plan *p) {
     return a;
 }
 
+static EigArgs eig_args(selr_plan *p, const int *active) {
+    EigArgs e;
+    memset(&e, 0, sizeof(e));
+    e.B0 = p->B0;
+    e.Gp = p->Gp;
+    e.lam = p->lam;
+    e.V = p->V;
+    e.rank = p->rank;
+    e.active = active;
+    e.status = p->status;
+    return e;
+}
+
+// S_t of every matrix of `gs` in [m0, m0 + mc): B0 (and W for Jacobi) already filled.
+static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, const SvtArgs &a, int part,
+                             cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (p->d.svd_method == SELR_SVD_JACOBI) {
+        if (part & 2) e = launch_jacobi(gs, m0, mc, a, st);
+        if (e == cudaSuccess && (part & 4)) e = launch_svt_apply(gs, m0, mc, a, st);
+        return e;
+    }
+    const EigArgs ea = eig_args(p, a.active);
+    if (part & 1) e = launch_gram(gs, m0, mc, p->B0, p->Gp, a.active, st);
+    if (e == cudaSuccess && (part & 2)) e = launch_heig(gs, m0, mc, ea, st);
+    if (e == cudaSuccess && (part & 4)) e = launch_apply_eig(gs, m0, mc, ea, a, st);
+    return e;
+}
+
 extern "C" selr_status selr_svt(selr_plan *p, void *A, int32_t nmat, int32_t rows, int32_t cols, float thresh,
                                 int32_t *rank_out, selr_stream stream) {
     if (!p || !A || nmat < 1 || rows < 1 || cols < 1 || !(thresh >= 0.f) || !isfinite(thresh))
@@ -445,17 +495,18 @@ extern "C" selr_status selr_svt(selr_plan *p, void *A, int32_t nmat, int32_t row
     g.thresh = thresh;
     finish_set(&s);
     if (g.len > 512 || g.s > 1024) return SELR_ERR_SHAPE;
-    if ((long long)nmat * rows * cols > p->lift_elems || (long long)nmat * g.s > p->vec_elems || nmat > p->gs.total)
+    if ((long long)nmat * rows * cols > p->lift_elems || (long long)nmat * g.s > p->vec_elems || nmat > p->gs.total ||
+        (p->d.svd_method == SELR_SVD_EIG && ((long long)nmat * g.s * (g.s + 1) / 2 > p->packed_elems || g.s > 480)))
         return SELR_ERR_SHAPE;
     cudaStream_t st = (cudaStream_t)stream;
-    CK(launch_natural_to_vm(s, (const cf *)A, p->W, p->B0, st));
+    const bool jac = p->d.svd_method == SELR_SVD_JACOBI;
+    CK(launch_natural_to_vm(s, (const cf *)A, jac ? p->W : p->B0, jac ? p->B0 : nullptr, st));
     SvtArgs a = svt_args(p);
     a.mode = 0;
     a.Zout = (cf *)A;
     a.z_natural = 1;
     a.rank_out = rank_out;
-    CK(launch_jacobi(s, 0, nmat, a, st));
-    CK(launch_svt_apply(s, 0, nmat, a, st));
+    CK(svd_apply(p, s, 0, nmat, a, 7, st));
     return SELR_OK;
 }
 
@@ -493,14 +544,15 @@ extern "C" selr_status selr_dc(selr_plan *p, const void *Y, const uint8_t *mask,
     return SELR_OK;
 }
 
-// The six stages of one ADMM iteration (X, then Z and D) on the plan's state:
+// The seven stages of one ADMM iteration (X, then Z and D) on the plan's state:
 //   0 adjoint of (Z - D/beta), 1 X-update (Eq. 15 / S7), 2 lift sources
-//   (hybrid transforms), 3 lifts, 4 Jacobi SVD, 5 SVT apply + D update.
-// In plain mode stage 3 runs lift, SVD and apply one matrix at a time and
-// stages 4 and 5 are empty.
+//   (hybrid transforms), 3 lifts, 4 Gram matrices, 5 eigensolver / Jacobi SVD,
+//   6 SVT apply + D update.  In plain mode stage 3 runs lift and the whole SVT
+//   one matrix at a time and stages 4-6 are empty.
 static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_t *mask, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     const bool plain = p->d.exec == SELR_EXEC_PLAIN;
+    const bool jac = p->d.svd_method == SELR_SVD_JACOBI;
     const int *act = p->model2d ? nullptr : p->active;
     int *act_next = p->model2d ? nullptr : p->active_next;
     const int total = p->gs.total;
@@ -510,6 +562,8 @@ static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_
     a.E = p->E;
     a.active = act;
     const float ib = 1.0f / p->d.beta;
+    cf *lift_out = jac ? p->W : p->B0;
+    cf *lift_out2 = jac ? p->B0 : nullptr;
     switch (stage) {
         case 0:
             if (plain) {
@@ -528,19 +582,21 @@ static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_
         case 3:
             if (plain) {
                 for (int m = 0; m < total; ++m) {
-                    if ((e = launch_lift(p->gs, 0, m, 1, p->D, 0, ib, p->W, p->B0, 0, act, st)) != cudaSuccess) return e;
-                    if ((e = launch_jacobi(p->gs, m, 1, a, st)) != cudaSuccess) return e;
-                    if ((e = launch_svt_apply(p->gs, m, 1, a, st)) != cudaSuccess) return e;
+                    if ((e = launch_lift(p->gs, 0, m, 1, p->D, 0, ib, lift_out, lift_out2, 0, act, st)) != cudaSuccess)
+                        return e;
+                    if ((e = svd_apply(p, p->gs, m, 1, a, 7, st)) != cudaSuccess) return e;
                 }
                 if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->M, st);
                 return cudaSuccess;
             }
-            return launch_lift(p->gs, 0, 0, total, p->D, 0, ib, p->W, p->B0, 0, act, st);
+            return launch_lift(p->gs, 0, 0, total, p->D, 0, ib, lift_out, lift_out2, 0, act, st);
         case 4:
-            return plain ? cudaSuccess : launch_jacobi(p->gs, 0, total, a, st);
+            return plain ? cudaSuccess : svd_apply(p, p->gs, 0, total, a, 1, st);
+        case 5:
+            return plain ? cudaSuccess : svd_apply(p, p->gs, 0, total, a, 2, st);
         default:
             if (plain) return cudaSuccess;
-            if ((e = launch_svt_apply(p->gs, 0, total, a, st)) != cudaSuccess) return e;
+            if ((e = svd_apply(p, p->gs, 0, total, a, 4, st)) != cudaSuccess) return e;
             if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->M, st);
             return cudaSuccess;
     }
@@ -711,7 +767,6 @@ extern "C" selr_status selr_profile_enable(selr_plan *p, int32_t on) {
 extern "C" selr_status selr_profile_read(selr_plan *p, int32_t stage, float *total_ms, int32_t *count) {
     if (!p || stage < 0 || stage >= NSTAGE || !total_ms) return SELR_ERR_INVALID_ARG;
     float tot = 0.f;
-    const bool plain = p->d.exec == SELR_EXEC_PLAIN;
     int n = 0;
     for (int it = 0; it < p->prof_count; ++it) {
         const cudaEvent_t a = p->ev[((size_t)it * NSTAGE + stage) * 2];

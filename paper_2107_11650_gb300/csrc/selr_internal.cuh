@@ -42,6 +42,7 @@ struct Group {
     int M, N, L;           // array dims of the source / adjoint arrays
     long long off;         // element offset of matrix 0 in lifted workspaces
     long long soff;        // offset of matrix 0 in per-vector arrays (sigma)
+    long long poff;        // offset of matrix 0 in packed Gram storage (s (s+1) / 2 per matrix)
     int moff;              // index of matrix 0 among all matrices (status words)
     const cf *w;           // weights (length nv) or nullptr (identity)
     const cf *src;         // lift source array
@@ -142,6 +143,23 @@ struct SvtArgs {
 cudaError_t svt_init_attributes();
 cudaError_t launch_jacobi(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
 cudaError_t launch_svt_apply(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
+
+// svt_eig.cu
+struct EigArgs {
+    const cf *B0;
+    cf *Gp;              // packed G in, Householder vectors out (offset g.poff per group)
+    float *lam;          // [mat][s] eigenvalues above the threshold (descending)
+    cf *V;               // [mat][s][s] eigenvectors (vector-major), first rank of them valid
+    int *rank;           // [mat]
+    const int *active;
+    unsigned *status;
+};
+cudaError_t eig_init_attributes();
+cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,
+                        const int *active, cudaStream_t st);
+cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, cudaStream_t st);
+cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, const SvtArgs &a,
+                             cudaStream_t st);
 
 // dc.cu
 struct DcArgs {

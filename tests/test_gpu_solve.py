@@ -37,9 +37,9 @@ def _dev(a, dtype=torch.complex64):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
 
 
-def _solve_gpu(wl, Y, mask, exec_mode="batched", n_iter=None, tol=-1.0, stream=True):
+def _solve_gpu(wl, Y, mask, exec_mode="batched", n_iter=None, tol=-1.0, stream=True, svd="eig"):
     api = _api()
-    d = api.Desc.from_workload(wl, exec=exec_mode, tol=tol)
+    d = api.Desc.from_workload(wl, exec=exec_mode, tol=tol, svd=svd)
     if n_iter is not None:
         d.max_iter = n_iter
     plan = api.Plan(d)
@@ -58,11 +58,12 @@ def _oracle_2d(wl, Y, mask, n_iter):
     return X
 
 
-@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
-def test_shlr_small_workload_30_iterations(exec_mode):
+@pytest.mark.parametrize("exec_mode,svd", [("batched", "eig"), ("plain", "eig"), ("batched", "jacobi"),
+                                          ("plain", "jacobi")])
+def test_shlr_small_workload_30_iterations(exec_mode, svd):
     wl = synth.get_config("shlr_4c_64")
     inp = synth.make_inputs(wl)
-    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], exec_mode)
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], exec_mode, svd=svd)
     assert st == 0 and it == 30
     Xo = _oracle_2d(wl, inp["Y"], inp["mask"], 30)
     err = rel_l2(X, Xo)
@@ -148,7 +149,8 @@ def test_shlr_full_size_two_iterations():
     assert rel_l2(X, Xo) < TOL
 
 
-def test_shlr_full_size_30_iterations_sampled_golden():
+@pytest.mark.parametrize("svd", ["eig", "jacobi"])
+def test_shlr_full_size_30_iterations_sampled_golden(svd):
     """The benchmarked workload (12 coils, 256x256, 30 iterations, batched and
     graph-captured) against FP64 oracle values stored at 4096 seeded sample
     positions by tests/golden/make_golden.py (oracle-only script)."""
@@ -156,7 +158,7 @@ def test_shlr_full_size_30_iterations_sampled_golden():
     g = np.load(path)
     wl = synth.get_config("shlr_12c_256")
     inp = synth.make_inputs(wl)
-    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], n_iter=int(g["n_iter"]))
+    X, it, rel, st, _ = _solve_gpu(wl, inp["Y"], inp["mask"], n_iter=int(g["n_iter"]), svd=svd)
     assert st == 0
     xs = X.ravel()[g["idx"]]
     err = np.linalg.norm(xs - g["values"]) / np.linalg.norm(g["values"])
@@ -168,7 +170,7 @@ def test_device_status_reports_sweep_cap_and_nonfinite():
     api = _api()
     wl = synth.get_config("shlr_4c_64").with_(n_iter=2)
     inp = synth.make_inputs(wl)
-    d = api.Desc.from_workload(wl, jacobi_max_sweeps=1)
+    d = api.Desc.from_workload(wl, jacobi_max_sweeps=1, svd="jacobi")
     plan = api.Plan(d)
     X = torch.empty_like(_dev(inp["Y"]))
     api.selr_solve(plan, _dev(inp["Y"]), _dev(inp["mask"], torch.uint8), X)
