@@ -18,7 +18,7 @@ struct selr_plan {
     cf *K, *hybA, *hybB, *adjA, *adjB;
     cf *D, *E, *W, *B0;
     cf *Gp, *V;              // packed Gram matrices / Householder vectors; eigenvectors
-    float *lam;
+    float *lam, *tri;
     int *rank;
     long long packed_elems;
     float *sigma;
@@ -230,7 +230,7 @@ static selr_status upload(void *dst, const void *src, size_t bytes) {
 extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     if (!p) return SELR_OK;
     drop_graphs(p);
-    void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam,
+    void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
                     p->rank, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status,
                     p->twM, p->twN, p->wM, p->wN, p->da, p->db};
@@ -304,6 +304,7 @@ extern "C" selr_status selr_plan_create(const selr_desc *d, selr_plan **out) {
         AL(p->V, lb);
         AL(p->Gp, sizeof(cf) * (size_t)p->packed_elems);
         AL(p->lam, sizeof(float) * (size_t)p->vec_elems);
+        AL(p->tri, 4 * sizeof(float) * (size_t)p->vec_elems);
         AL(p->rank, sizeof(int) * (size_t)gs.total);
     }
     AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
@@ -456,6 +457,7 @@ static EigArgs eig_args(selr_plan *p, const int *active) {
     e.lam = p->lam;
     e.V = p->V;
     e.rank = p->rank;
+    e.tri = p->tri;
     e.active = active;
     e.status = p->status;
     return e;

@@ -151,6 +151,7 @@ struct EigArgs {
     float *lam;          // [mat][s] eigenvalues above the threshold (descending)
     cf *V;               // [mat][s][s] eigenvectors (vector-major), first rank of them valid
     int *rank;           // [mat]
+    float *tri;          // [mat][4 s]: tridiagonal d, reflector tau, complex sub-diagonal e
     const int *active;
     unsigned *status;
 };

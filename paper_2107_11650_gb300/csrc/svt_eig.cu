@@ -9,13 +9,18 @@
 // matrices of the reconstruction only a few percent of the s singular values
 // exceed t, so the eigensolver is built to find exactly those:
 //   k_gram      G (lower triangle, packed by columns) = B^H B.
-//   k_heig      one CTA per matrix: Householder reduction of G to a Hermitian
+//   k_tridiag   one CTA per matrix: Householder reduction of G to a Hermitian
 //               tridiagonal (Householder vectors kept in the packed buffer),
-//               diagonal phase scaling to a real symmetric tridiagonal T,
+//               with the rank-2 update of each step fused into the next
+//               step's matrix-vector product (one pass over the matrix per
+//               step); k_tridiag_g is the same reduction on global memory for
+//               orders that do not fit in shared memory.
+//   k_eigvec    diagonal phase scaling to a real symmetric tridiagonal T,
 //               Sturm count of the eigenvalues above t^2, 32-way multisection
 //               of each of them (one warp per eigenvalue), inverse iteration
-//               for their eigenvectors with modified Gram-Schmidt inside
-//               clusters of close eigenvalues, and back-transformation.
+//               for their eigenvectors (one thread per vector) with modified
+//               Gram-Schmidt inside clusters of close eigenvalues, and
+//               back-transformation with batches of reflectors.
 //   k_apply_eig Z = sum_i g_i (B v_i) v_i^H per tile of rows of B, fused with
 //               the multiplier update D <- D + tau (A - D/beta - Z) and
 //               E = Z - D/beta (Eqs. 13-14), or writing Z.
@@ -27,11 +32,13 @@
 
 #define EIG_THREADS 512
 #define EIG_WARPS (EIG_THREADS / 32)
-#define EIG_SMEM_MAX_N 224       // packed G of order <= 224 stays in shared memory
-#define EIG_MAXR_CHUNK 32        // eigenvectors handled per back-transformation pass
+#define EIG_SMEM_MAX_N 208       // packed G of order <= 208 stays in shared memory
 #define INV_ITERS 4
+#define EV_HB 8                  // Householder reflectors staged per back-transformation batch
 
 __device__ __forceinline__ long long colstart(int j, int n) { return (long long)j * (2 * n - j + 1) / 2; }
+
+__host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
@@ -141,55 +148,106 @@ __device__ __forceinline__ int sturm_lt(const float *d, const float *f2, int n, 
 
 // Solve (T - lam I) y = z in place (z -> y) by Gaussian elimination with
 // partial pivoting on the tridiagonal (d, f).  u0/u1/u2 are the diagonals of
-// U, lm the multipliers, piv the row interchanges; all length n.  The
-// current row always has two entries (c0 at column k, c1 at column k+1):
-//   no swap: l = f_k / c0, U_k = (c0, c1, 0),          row' = (a_{k+1} - l c1, f_{k+1})
+// U, lm the multipliers, piv the row interchanges; element k of each array is
+// at index k * ST (arrays of several systems are interleaved so that the
+// threads solving them touch distinct shared-memory banks).  The current row
+// always has two entries (c0 at column k, c1 at column k+1):
+//   no swap: l = f_k / c0, U_k = (c0, c1, 0),            row' = (a_{k+1} - l c1, f_{k+1})
 //   swap:    l = c0 / f_k, U_k = (f_k, a_{k+1}, f_{k+1}), row' = (c1 - l a_{k+1}, -l f_{k+1})
-// A zero pivot is replaced by `tiny` (inverse iteration wants a huge, not
-// infinite, growth).
+// The factorisation is done once (factor = true) and reused.  A zero pivot is
+// replaced by `tiny` (inverse iteration wants a huge, not infinite, growth).
+template <int ST>
 __device__ void tri_solve(const float *d, const float *f, int n, float lam, float *z, float *u0, float *u1,
-                          float *u2, float *lm, unsigned char *piv, float tiny) {
-    float c0 = d[0] - lam, c1 = n > 1 ? f[0] : 0.f;
+                          float *u2, float *lm, unsigned char *piv, float tiny, bool factor) {
+    if (factor) {
+        float c0 = d[0] - lam, c1 = n > 1 ? f[0] : 0.f;
+        for (int k = 0; k < n - 1; ++k) {
+            const float fk = f[k];
+            const float an = d[k + 1] - lam;
+            const float fn = k + 1 < n - 1 ? f[k + 1] : 0.f;
+            if (fabsf(c0) >= fabsf(fk)) {
+                if (c0 == 0.f) c0 = tiny;
+                const float l = fk / c0;
+                u0[k * ST] = c0; u1[k * ST] = c1; u2[k * ST] = 0.f; lm[k * ST] = l; piv[k * ST] = 0;
+                c0 = an - l * c1;
+                c1 = fn;
+            } else {
+                const float l = c0 / fk;
+                u0[k * ST] = fk; u1[k * ST] = an; u2[k * ST] = fn; lm[k * ST] = l; piv[k * ST] = 1;
+                c0 = c1 - l * an;
+                c1 = -l * fn;
+            }
+        }
+        if (c0 == 0.f) c0 = tiny;
+        u0[(n - 1) * ST] = c0; u1[(n - 1) * ST] = 0.f; u2[(n - 1) * ST] = 0.f;
+    }
+    float zk = z[0];
     for (int k = 0; k < n - 1; ++k) {
-        const float fk = f[k];
-        const float an = d[k + 1] - lam;
-        const float fn = k + 1 < n - 1 ? f[k + 1] : 0.f;
-        if (fabsf(c0) >= fabsf(fk)) {
-            if (c0 == 0.f) c0 = tiny;
-            const float l = fk / c0;
-            u0[k] = c0; u1[k] = c1; u2[k] = 0.f; lm[k] = l; piv[k] = 0;
-            c0 = an - l * c1;
-            c1 = fn;
+        const float zn = z[(k + 1) * ST];
+        if (piv[k * ST]) {
+            z[k * ST] = zn;
+            zk = zk - lm[k * ST] * zn;
         } else {
-            const float l = c0 / fk;
-            u0[k] = fk; u1[k] = an; u2[k] = fn; lm[k] = l; piv[k] = 1;
-            c0 = c1 - l * an;
-            c1 = -l * fn;
+            z[k * ST] = zk;
+            zk = zn - lm[k * ST] * zk;
         }
     }
-    if (c0 == 0.f) c0 = tiny;
-    u0[n - 1] = c0; u1[n - 1] = 0.f; u2[n - 1] = 0.f;
-    for (int k = 0; k < n - 1; ++k) {
-        if (piv[k]) {
-            const float t = z[k];
-            z[k] = z[k + 1];
-            z[k + 1] = t - lm[k] * z[k + 1];
-        } else {
-            z[k + 1] -= lm[k] * z[k];
+    z[(n - 1) * ST] = zk;
+    float x2 = z[(n - 1) * ST] / u0[(n - 1) * ST];
+    z[(n - 1) * ST] = x2;
+    if (n > 1) {
+        float x1 = (z[(n - 2) * ST] - u1[(n - 2) * ST] * x2) / u0[(n - 2) * ST];
+        z[(n - 2) * ST] = x1;
+        for (int k = n - 3; k >= 0; --k) {
+            const float x0 = (z[k * ST] - u1[k * ST] * x1 - u2[k * ST] * x2) / u0[k * ST];
+            z[k * ST] = x0;
+            x2 = x1;
+            x1 = x0;
         }
     }
-    z[n - 1] /= u0[n - 1];
-    if (n > 1) z[n - 2] = (z[n - 2] - u1[n - 2] * z[n - 1]) / u0[n - 2];
-    for (int k = n - 3; k >= 0; --k) z[k] = (z[k] - u1[k] * z[k + 1] - u2[k] * z[k + 2]) / u0[k];
 }
 
-// ------------------------------------------------------------------ k_heig
-__global__ void __launch_bounds__(EIG_THREADS, 1) k_heig(GroupSet gs, int mat_begin, EigArgs a) {
-    extern __shared__ float esm[];
-    __shared__ float red[EIG_WARPS];
+// ------------------------------------------------------------ tridiagonal
+// Tridiagonal data of one matrix in the plan's `tri` buffer (4 floats per
+// row): d[n] (real diagonal), tau[n] (reflector scales), e[n] complex
+// sub-diagonal (e[k] = T[k+1][k]).
+__device__ __forceinline__ float *tri_d(const EigArgs &a, const Group &g, int mat) {
+    return a.tri + 4 * (g.soff + (long long)mat * g.s);
+}
+
+template <int RPL>
+__device__ __forceinline__ cf pick(const cf (&v)[RPL], int t) {
+    cf r = v[0];
+#pragma unroll
+    for (int u = 1; u < RPL; ++u)
+        if (u == t) r = v[u];
+    return r;
+}
+
+__device__ __forceinline__ cf shfl_cf(cf v, int src) {
+    return mk(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Householder reduction G = Q T Q^H (lower, packed G in shared memory,
+// n <= 32 * RPL).  Lane l of every warp owns rows l, l + 32, ... and keeps
+// their entries of the current reflector v and of the previous step's v and
+// w in registers.  Step k:
+//   1. warp 0 applies the previous step's rank-2 update to column k, forms
+//      the reflector from G[k+1:, k] and publishes v;
+//   2. every warp sweeps its share of the trailing columns j > k once,
+//      applying the previous update G -= v w^H + w v^H and accumulating
+//      p = G v with the updated values: stored entry G(i, j) adds G(i, j) v_j
+//      to the row sum of p_i (registers, per-warp partials in shared memory)
+//      and conj(G(i, j)) v_i to p_j (warp reduction, one column per warp, so
+//      no atomics);
+//   3. all threads: p = tau (sum of partials), K = tau/2 Re(v^H p), w = p - K v.
+// Reflector: x = G[k+1:, k], alpha = -e^{i arg x0} ||x||, v = x - alpha e1,
+// tau = 2 / v^H v, so (I - tau v v^H) x = alpha e1.
+template <int RPL>
+__global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat_begin, EigArgs a) {
+    extern __shared__ __align__(16) unsigned char tsm[];
     __shared__ float s_tau;
-    __shared__ cf s_alpha;
-    __shared__ int s_r;
+    __shared__ float red[EIG_WARPS];
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
@@ -197,32 +255,212 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_heig(GroupSet gs, int mat_be
     const int n = g.s;
     const long long pk = (long long)n * (n + 1) / 2;
     cf *Gglob = a.Gp + g.poff + (long long)mat * pk;
-    const bool in_smem = n <= EIG_SMEM_MAX_N;
-    // shared layout: [v n][p n][ph n] cf, [d n][f n][f^2 n][tau n] float, then the packed
-    // G (if it fits); the eigen stage reuses the packed region as scratch.
-    cf *vb = (cf *)esm;
-    cf *pb = vb + n;
-    cf *ph = pb + n;
-    float *dd = (float *)(ph + n);
-    float *ff = dd + n;
-    float *f2 = ff + n;
-    float *taus = f2 + n;
-    float *work = taus + n;
-    cf *Gs = in_smem ? (cf *)work : Gglob;
+    cf *Gs = (cf *)tsm;                                   // [pk]
+    cf *Pw = Gs + al16((size_t)pk * 8) / 8;              // [EIG_WARPS][n] row-sum partials
+    cf *Cs = Pw + (long long)EIG_WARPS * n;               // [n] column sums
+    cf *vbuf0 = Cs + n, *vbuf1 = vbuf0 + n;               // v of this / previous step
+    cf *wbuf0 = vbuf1 + n, *wbuf1 = wbuf0 + n;            // w of this / previous step
+    int *cst = (int *)(wbuf1 + n);                        // [n]
+    float *td = tri_d(a, g, mat), *ttau = td + n;
+    cf *te = (cf *)(td + 2 * n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float t2 = g.thresh * g.thresh;
-    float *lam_out = a.lam + g.soff + (long long)mat * n;
-    cf *V = a.V + g.off + (long long)mat * n * g.len;   // room for s vectors of length s <= len
-    int *rank_out = a.rank + g.moff + mat;
-
-    if (in_smem)
-        for (long long i = tid; i < pk; i += EIG_THREADS) Gs[i] = Gglob[i];
+    for (int j = tid; j < n; j += EIG_THREADS) {
+        cst[j] = (int)colstart(j, n);
+        vbuf1[j] = wbuf1[j] = mk(0.f, 0.f);
+    }
+    for (long long i = tid; i < pk; i += EIG_THREADS) Gs[i] = Gglob[i];
     __syncthreads();
+    cf vo[RPL], wo[RPL], vn[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) vo[t] = wo[t] = vn[t] = mk(0.f, 0.f);
+    float tau_old = 0.f;
+    cf *vb = vbuf0, *vp = vbuf1, *wb = wbuf0, *wp = wbuf1;
+    for (int k = 0; k + 2 < n; ++k) {
+        // ---- 1. column k and the reflector (warp 0)
+        if (warp == 0) {
+            const cf vk = vp[k], wk = wp[k];
+            cf colv[RPL];
+            float xn2 = 0.f;
+            const int ck = cst[k];
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                const int i = lane + 32 * t;
+                colv[t] = mk(0.f, 0.f);
+                if (32 * t + 31 >= k && 32 * t < n && i >= k && i < n) {
+                    cf gv = Gs[ck + i - k];
+                    if (tau_old != 0.f) {
+                        gv.x -= vo[t].x * wk.x + vo[t].y * wk.y + wo[t].x * vk.x + wo[t].y * vk.y;
+                        gv.y -= vo[t].y * wk.x - vo[t].x * wk.y + wo[t].y * vk.x - wo[t].x * vk.y;
+                        Gs[ck + i - k] = gv;
+                    }
+                    colv[t] = gv;
+                    if (i > k) xn2 += cabs2(gv);
+                }
+            }
+            xn2 = wsum(xn2);
+            const cf x0 = shfl_cf(pick(colv, (k + 1) >> 5), (k + 1) & 31);
+            const float ax0 = sqrtf(cabs2(x0));
+            const float rest = xn2 - ax0 * ax0;
+            float tau = 0.f;
+            cf alpha = x0, v0 = mk(0.f, 0.f);
+            if (rest > 1e-30f * xn2 && xn2 > 0.f) {
+                const float xnorm = sqrtf(xn2);
+                const cf phs = ax0 > 0.f ? mk(x0.x / ax0, x0.y / ax0) : mk(1.f, 0.f);
+                alpha = mk(-phs.x * xnorm, -phs.y * xnorm);
+                tau = 1.f / (xn2 + xnorm * ax0);
+                v0 = mk(phs.x * (ax0 + xnorm), phs.y * (ax0 + xnorm));
+            }
+            cf *hv = Gglob + ck + 1;                          // Householder vector k (global)
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                const int i = lane + 32 * t;
+                if (32 * t < n) {
+                    cf v = mk(0.f, 0.f);
+                    if (i >= k + 1 && i < n) {
+                        v = tau == 0.f ? mk(0.f, 0.f) : (i == k + 1 ? v0 : colv[t]);
+                        hv[i - k - 1] = v;
+                    }
+                    if (i < n) vb[i] = v;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                s_tau = tau;
+                ttau[k] = tau;
+                te[k] = alpha;
+                td[k] = Gs[ck].x;
+            }
+        }
+        __syncthreads();
+        const float tau = s_tau;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            vn[t] = (i < n) ? vb[i] : mk(0.f, 0.f);
+        }
+        // ---- 2. fused update + symv over the trailing columns
+        const bool upd = tau_old != 0.f;
+        cf pa[RPL];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) pa[t] = mk(0.f, 0.f);
+        for (int j = k + 1 + warp; j < n; j += EIG_WARPS) {
+            const cf voj = vp[j], woj = wp[j], vnj = vb[j];
+            const int base = cst[j] - j;
+            float cr = 0.f, ci = 0.f;
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                if (32 * t + 31 >= j && 32 * t < n) {           // warp-uniform: slot t has rows >= j
+                    const int i = lane + 32 * t;
+                    if (i >= j && i < n) {
+                        cf gv = Gs[base + i];
+                        if (upd) {
+                            gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
+                            gv.y -= vo[t].y * woj.x - vo[t].x * woj.y + wo[t].y * voj.x - wo[t].x * voj.y;
+                            Gs[base + i] = gv;
+                        }
+                        pa[t].x += gv.x * vnj.x - gv.y * vnj.y;
+                        pa[t].y += gv.x * vnj.y + gv.y * vnj.x;
+                        if (i > j) {                           // conj(G(i,j)) v_i -> p_j
+                            cr += gv.x * vn[t].x + gv.y * vn[t].y;
+                            ci += gv.x * vn[t].y - gv.y * vn[t].x;
+                        }
+                    }
+                }
+            }
+            cr = wsum(cr);
+            ci = wsum(ci);
+            if (lane == 0) Cs[j] = mk(cr, ci);
+        }
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            if (32 * t < n && i >= k + 1 && i < n) Pw[(long long)warp * n + i] = pa[t];
+        }
+        __syncthreads();
+        // ---- 3. p = tau * (row partials + column sum), K, w (all threads)
+        cf pi = mk(0.f, 0.f), vi = mk(0.f, 0.f);
+        float kv = 0.f;
+        const int i3 = k + 1 + tid;
+        if (i3 < n) {
+            float sr = Cs[i3].x, si = Cs[i3].y;
+            for (int w2 = 0; w2 < EIG_WARPS; ++w2) {
+                const cf q = Pw[(long long)w2 * n + i3];
+                sr += q.x;
+                si += q.y;
+            }
+            pi = mk(tau * sr, tau * si);
+            vi = vb[i3];
+            kv = vi.x * pi.x + vi.y * pi.y;
+        }
+        kv = bsum(kv, red);
+        const float K = 0.5f * tau * kv;
+        if (i3 < n) wb[i3] = mk(pi.x - K * vi.x, pi.y - K * vi.y);
+        if (tid <= k && tid < n) wb[tid] = mk(0.f, 0.f);
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            wo[t] = (i < n) ? wb[i] : mk(0.f, 0.f);
+            vo[t] = vn[t];
+        }
+        tau_old = tau;
+        cf *tv = vp; vp = vb; vb = tv;
+        cf *tw = wp; wp = wb; wb = tw;
+    }
+    // ---- last step's update on the final 2x2 block, then the remaining d, e
+    if (warp == 0) {
+        for (int j = (n >= 2 ? n - 2 : 0); j < n; ++j) {
+            const cf voj = vp[j], woj = wp[j];
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                const int i = lane + 32 * t;
+                if (tau_old != 0.f && 32 * t < n && i >= j && i < n) {
+                    cf gv = Gs[cst[j] + i - j];
+                    gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
+                    gv.y -= vo[t].y * woj.x - vo[t].x * woj.y + wo[t].y * voj.x - wo[t].x * voj.y;
+                    Gs[cst[j] + i - j] = gv;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            if (n >= 2) {
+                td[n - 2] = Gs[cst[n - 2]].x;
+                te[n - 2] = Gs[cst[n - 2] + 1];
+                ttau[n - 2] = 0.f;
+            }
+            td[n - 1] = Gs[cst[n - 1]].x;
+            te[n - 1] = mk(0.f, 0.f);
+            ttau[n - 1] = 0.f;
+        }
+    }
+}
 
-    // ---- Householder reduction to Hermitian tridiagonal (lower)
+// Same reduction with G kept in global memory (orders too large for shared
+// memory): one thread per row half for the symv, warp-per-column rank-2 update.
+__global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int mat_begin, EigArgs a) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    __shared__ float red[EIG_WARPS];
+    __shared__ float s_tau;
+    __shared__ cf s_alpha;
+    int mat;
+    const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    if (is_frozen(g, mat, a.active)) return;
+    const int n = g.s;
+    const long long pk = (long long)n * (n + 1) / 2;
+    cf *Gs = a.Gp + g.poff + (long long)mat * pk;
+    cf *vb = (cf *)tsm;
+    cf *pb = vb + n;
+    int *cst = (int *)(pb + n);
+    float *td = tri_d(a, g, mat), *ttau = td + n;
+    cf *te = (cf *)(td + 2 * n);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = tid; j < n; j += EIG_THREADS) cst[j] = (int)colstart(j, n);
+    __syncthreads();
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
-        cf *col = Gs + colstart(k, n) + 1;     // x = G[k+1 .. n-1][k]
+        cf *col = Gs + cst[k] + 1;
         float xn2 = 0.f;
         for (int i = tid; i < m; i += EIG_THREADS) xn2 += cabs2(col[i]);
         xn2 = bsum(xn2, red);
@@ -230,6 +468,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_heig(GroupSet gs, int mat_be
         const float ax0 = sqrtf(cabs2(x0));
         const float rest = xn2 - ax0 * ax0;
         if (tid == 0) {
+            td[k] = Gs[cst[k]].x;
             if (!(rest > 1e-30f * xn2) || xn2 == 0.f) {
                 s_tau = 0.f;
                 s_alpha = x0;
@@ -237,53 +476,62 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_heig(GroupSet gs, int mat_be
                 const float xnorm = sqrtf(xn2);
                 const cf phs = ax0 > 0.f ? mk(x0.x / ax0, x0.y / ax0) : mk(1.f, 0.f);
                 s_alpha = mk(-phs.x * xnorm, -phs.y * xnorm);
-                s_tau = 1.f / (xn2 + xnorm * ax0);          // 2 / v^H v
+                s_tau = 1.f / (xn2 + xnorm * ax0);
                 vb[0] = mk(phs.x * (ax0 + xnorm), phs.y * (ax0 + xnorm));
             }
+            ttau[k] = s_tau;
+            te[k] = s_alpha;
         }
         __syncthreads();
         const float tau = s_tau;
-        if (tid == 0) taus[k] = tau;
-        cf *hv = Gglob + colstart(k, n) + 1;   // Householder vector k stored in place of column k
         if (tau == 0.f) {
-            if (tid == 0) { vb[0] = mk(0.f, 0.f); ph[k] = s_alpha; }
+            for (int i = tid; i < m; i += EIG_THREADS) col[i] = mk(0.f, 0.f);   // zero reflector
             __syncthreads();
             continue;
         }
         for (int i = tid + 1; i < m; i += EIG_THREADS) vb[i] = col[i];
         __syncthreads();
-        for (int i = tid; i < m; i += EIG_THREADS) hv[i] = vb[i];
-        if (tid == 0) ph[k] = s_alpha;        // sub-diagonal entry e_k (temporarily in ph)
-        // p = tau * Gt v over trailing rows/cols k+1 .. n-1 (trailing index i <-> row k+1+i)
-        for (int i = tid; i < m; i += EIG_THREADS) {
+        for (int i = tid; i < m; i += EIG_THREADS) col[i] = vb[i];              // reflector in place
+        // symv: two threads per row (halves of the row), loop bound padded to a multiple of
+        // 32 so that every lane reaches the pair shuffle (inactive lanes add zeros)
+        const int nrow2 = 2 * m, nrow2_pad = (nrow2 + 31) & ~31;
+        for (int t2i = tid; t2i < nrow2_pad; t2i += EIG_THREADS) {
+            const bool act = t2i < nrow2;
+            const int i = t2i >> 1, half = t2i & 1;
             const int I = k + 1 + i;
+            const int j0 = act ? (half ? (m >> 1) : 0) : 0, j1 = act ? (half ? m : (m >> 1)) : 0;
             float sr = 0.f, si = 0.f;
-            for (int j = 0; j <= i; ++j) {          // G(I, J) stored, J = k+1+j <= I
-                const cf gv = Gs[colstart(k + 1 + j, n) + (I - (k + 1 + j))];
+            int j = j0;
+            for (; j < j1 && j <= i; ++j) {
+                const int J = k + 1 + j;
+                const cf gv = Gs[cst[J] + (I - J)];
                 const cf v = vb[j];
                 sr += gv.x * v.x - gv.y * v.y;
                 si += gv.x * v.y + gv.y * v.x;
             }
-            const cf *ci = Gs + colstart(I, n);
-            for (int j = i + 1; j < m; ++j) {       // conj(G(J, I)), J > I
-                const cf gv = ci[j - i];
-                const cf v = vb[j];
-                sr += gv.x * v.x + gv.y * v.y;
-                si += gv.x * v.y - gv.y * v.x;
+            if (j < j1) {
+                const cf *ci = Gs + cst[I];
+                for (; j < j1; ++j) {
+                    const cf gv = ci[j - i];
+                    const cf v = vb[j];
+                    sr += gv.x * v.x + gv.y * v.y;
+                    si += gv.x * v.y - gv.y * v.x;
+                }
             }
-            pb[i] = mk(tau * sr, tau * si);
+            sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+            si += __shfl_xor_sync(0xffffffffu, si, 1);
+            if (act && !half) pb[i] = mk(tau * sr, tau * si);
         }
         __syncthreads();
         float kv = 0.f;
-        for (int i = tid; i < m; i += EIG_THREADS) kv += vb[i].x * pb[i].x + vb[i].y * pb[i].y;   // Re(v^H p)
+        for (int i = tid; i < m; i += EIG_THREADS) kv += vb[i].x * pb[i].x + vb[i].y * pb[i].y;
         kv = bsum(kv, red);
         const float K = 0.5f * tau * kv;
-        for (int i = tid; i < m; i += EIG_THREADS) pb[i] = mk(pb[i].x - K * vb[i].x, pb[i].y - K * vb[i].y);  // w
+        for (int i = tid; i < m; i += EIG_THREADS) pb[i] = mk(pb[i].x - K * vb[i].x, pb[i].y - K * vb[i].y);
         __syncthreads();
-        // rank-2 update of the trailing lower triangle: G(I,J) -= v_i conj(w_j) + w_i conj(v_j)
         for (int j = warp; j < m; j += EIG_WARPS) {
             const cf vj = vb[j], wj = pb[j];
-            cf *cj = Gs + colstart(k + 1 + j, n);
+            cf *cj = Gs + cst[k + 1 + j];
             for (int i = j + lane; i < m; i += 32) {
                 const cf vi = vb[i], wi = pb[i];
                 cf gv = cj[i - j];
@@ -294,60 +542,130 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_heig(GroupSet gs, int mat_be
         }
         __syncthreads();
     }
-    // diagonal, last sub-diagonal
-    for (int k = tid; k < n; k += EIG_THREADS) dd[k] = Gs[colstart(k, n)].x;
     if (tid == 0) {
-        if (n >= 2) ph[n - 2] = Gs[colstart(n - 2, n) + 1];
-        if (n >= 2) taus[n - 2] = 0.f;
-        taus[n - 1] = 0.f;
-    }
-    __syncthreads();
-    // phases making the tridiagonal real: f_k = |e_k|, ph_{k+1} = ph_k e_k / |e_k|
-    if (tid == 0) {
-        cf cur = mk(1.f, 0.f);
-        for (int k = 0; k < n; ++k) {
-            const cf e = k + 1 < n ? ph[k] : mk(0.f, 0.f);
-            const float ae = sqrtf(cabs2(e));
-            ph[k] = cur;
-            if (k + 1 < n) {
-                ff[k] = ae;
-                f2[k] = ae * ae;
-                if (ae > 0.f) cur = cmul(cur, mk(e.x / ae, e.y / ae));
-            }
+        if (n >= 2) {
+            td[n - 2] = Gs[cst[n - 2]].x;
+            te[n - 2] = Gs[cst[n - 2] + 1];
+            ttau[n - 2] = 0.f;
         }
-        if (n >= 1) { ff[n - 1] = 0.f; f2[n - 1] = 0.f; }
+        td[n - 1] = Gs[cst[n - 1]].x;
+        te[n - 1] = mk(0.f, 0.f);
+        ttau[n - 1] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------- eigvec
+// Shared-memory layout of k_eigvec (16-byte aligned regions).
+struct EvLayout {
+    size_t ph, dd, ff, f2, taus, lam, clu, zv, lu0, lu1, lu2, llm, lpv, yc, hb, total;
+};
+__host__ __device__ inline EvLayout ev_layout(int n, int chunk, int st) {
+    EvLayout L;
+    size_t o = 0;
+    L.ph = o; o += al16((size_t)n * 8);
+    L.dd = o; o += al16((size_t)n * 4);
+    L.ff = o; o += al16((size_t)n * 4);
+    L.f2 = o; o += al16((size_t)n * 4);
+    L.taus = o; o += al16((size_t)n * 4);
+    L.lam = o; o += al16((size_t)n * 4);
+    L.clu = o; o += al16((size_t)n * 4);
+    L.zv = o; o += al16((size_t)st * n * 4);
+    L.lu0 = o; o += al16((size_t)st * n * 4);
+    L.lu1 = o; o += al16((size_t)st * n * 4);
+    L.lu2 = o; o += al16((size_t)st * n * 4);
+    L.llm = o; o += al16((size_t)st * n * 4);
+    L.lpv = o; o += al16((size_t)st * n);
+    L.yc = o; o += al16((size_t)chunk * n * 8);
+    L.hb = o; o += al16((size_t)EV_HB * n * 8);
+    L.total = o;
+    return L;
+}
+
+// Eigenpairs of T above t^2 and their back-transformation (see file header).
+// IV_CHUNK eigenvectors are solved per inverse-iteration pass; their arrays
+// are interleaved with the odd stride IV_ST (> IV_CHUNK) so that both the
+// thread-per-vector solves and the warp-per-vector reductions avoid bank
+// conflicts.
+template <int IV_CHUNK, int IV_ST>
+__global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_begin, EigArgs a) {
+    extern __shared__ __align__(16) unsigned char vsm[];
+    __shared__ float red[4];
+    __shared__ int s_r;
+    int mat;
+    const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    if (is_frozen(g, mat, a.active)) return;
+    const int n = g.s;
+    const long long pk = (long long)n * (n + 1) / 2;
+    const cf *Gglob = a.Gp + g.poff + (long long)mat * pk;     // Householder vectors
+    const EvLayout LY = ev_layout(n, IV_CHUNK, IV_ST);
+    cf *ph = (cf *)(vsm + LY.ph);
+    float *dd = (float *)(vsm + LY.dd), *ff = (float *)(vsm + LY.ff), *f2 = (float *)(vsm + LY.f2);
+    float *taus = (float *)(vsm + LY.taus), *lamv = (float *)(vsm + LY.lam);
+    int *clu = (int *)(vsm + LY.clu);
+    float *zv = (float *)(vsm + LY.zv), *lu0 = (float *)(vsm + LY.lu0), *lu1 = (float *)(vsm + LY.lu1);
+    float *lu2 = (float *)(vsm + LY.lu2), *llm = (float *)(vsm + LY.llm);
+    unsigned char *lpv = vsm + LY.lpv;
+    cf *Yc = (cf *)(vsm + LY.yc);
+    cf *hb = (cf *)(vsm + LY.hb);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float t2 = g.thresh * g.thresh;
+    const float *td = tri_d(a, g, mat), *ttau = td + n;
+    const cf *te = (const cf *)(td + 2 * n);
+    float *lam_out = a.lam + g.soff + (long long)mat * n;
+    cf *V = a.V + g.off + (long long)mat * n * g.len;
+    int *rank_out = a.rank + g.moff + mat;
+    // T real: f_k = |e_k|; phases ph_0 = 1, ph_{k+1} = ph_k e_k / |e_k| (warp-0 product scan)
+    for (int k = tid; k < n; k += EIG_THREADS) {
+        dd[k] = td[k];
+        taus[k] = ttau[k];
+        const float ae = k + 1 < n ? sqrtf(cabs2(te[k])) : 0.f;
+        ff[k] = ae;
+        f2[k] = ae * ae;
+    }
+    if (warp == 0) {
+        const int per = (n + 31) / 32, k0 = lane * per, k1 = min(n, k0 + per);
+        cf loc = mk(1.f, 0.f);
+        for (int k = k0; k < k1; ++k) {
+            const cf e = k + 1 < n ? te[k] : mk(0.f, 0.f);
+            const float ae = sqrtf(cabs2(e));
+            if (ae > 0.f) loc = cmul(loc, mk(e.x / ae, e.y / ae));
+        }
+        // exclusive product scan of the lane products
+        cf incl = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const cf up = shfl_cf(incl, max(lane - o, 0));
+            if (lane >= o) incl = cmul(up, incl);
+        }
+        cf cur = shfl_cf(incl, max(lane - 1, 0));
+        if (lane == 0) cur = mk(1.f, 0.f);
+        for (int k = k0; k < k1; ++k) {
+            ph[k] = cur;
+            const cf e = k + 1 < n ? te[k] : mk(0.f, 0.f);
+            const float ae = sqrtf(cabs2(e));
+            if (ae > 0.f) cur = cmul(cur, mk(e.x / ae, e.y / ae));
+        }
     }
     __syncthreads();
-
-    // ---- eigenvalues above t^2
-    float gl = 0.f, gu = 0.f, fmax2 = 0.f;
     if (tid == 0) {
-        gl = FLT_MAX; gu = -FLT_MAX;
+        float gl = FLT_MAX, gu = -FLT_MAX, fm2 = 0.f;
         for (int k = 0; k < n; ++k) {
             const float r0 = (k > 0 ? ff[k - 1] : 0.f) + (k + 1 < n ? ff[k] : 0.f);
             gl = fminf(gl, dd[k] - r0);
             gu = fmaxf(gu, dd[k] + r0);
-            fmax2 = fmaxf(fmax2, f2[k]);
+            fm2 = fmaxf(fm2, f2[k]);
         }
-        red[0] = gl; red[1] = gu; red[2] = fmax2;
+        const float pivmin = FLT_MIN * fmaxf(1.f, fm2);
+        red[0] = gl; red[1] = gu; red[2] = pivmin;
+        s_r = n - ((t2 >= gu) ? n : sturm_lt(dd, f2, n, t2, pivmin));
     }
     __syncthreads();
-    gl = red[0]; gu = red[1]; fmax2 = red[2];
+    const float gl = red[0], gu = red[1], pivmin = red[2];
     const float tnorm = fmaxf(fabsf(gl), fabsf(gu));
-    const float pivmin = FLT_MIN * fmaxf(1.f, fmax2);
-    if (tid == 0) {
-        const int below = (t2 >= gu) ? n : sturm_lt(dd, f2, n, t2, pivmin);
-        s_r = n - below;
-    }
-    __syncthreads();
     const int r = s_r;
     if (tid == 0) *rank_out = r;
     if (r == 0) return;
-    // reuse shared memory beyond the tridiagonal arrays for the eigen stage
-    float *lamv = work;                               // [r]
-    int *clu = (int *)(lamv + n);                     // cluster start flags [r]
-    float *zv = (float *)(clu + n);                   // [min(r, chunk)][n] real eigenvectors of T
-    // multisection: warp per eigenvalue (q-th largest, ascending index n-1-q)
     for (int q = warp; q < r; q += EIG_WARPS) {
         const int j = n - 1 - q;
         float lo = fmaxf(gl, t2), hi = gu;
@@ -366,7 +684,6 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_heig(GroupSet gs, int mat_be
         if (lane == 0) lamv[q] = 0.5f * (lo + hi);
     }
     __syncthreads();
-    // clusters of close eigenvalues (descending order) and distinctness perturbation
     if (tid == 0) {
         const float ortol = 1e-3f * tnorm;
         const float sep = 10.f * FLT_EPSILON * tnorm;
@@ -377,85 +694,84 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_heig(GroupSet gs, int mat_be
     }
     __syncthreads();
     for (int q = tid; q < r; q += EIG_THREADS) lam_out[q] = lamv[q];
-    // eigenvectors in chunks of EIG_MAXR_CHUNK: inverse iteration + MGS within clusters,
-    // then back-transformation v = Q P z.
-    float *scratch = zv + (long long)EIG_MAXR_CHUNK * n;   // per warp: 4n floats + n bytes
-    for (int q0 = 0; q0 < r; q0 += EIG_MAXR_CHUNK) {
-        const int qc = min(EIG_MAXR_CHUNK, r - q0);
-        // a warp owns a cluster (its members in this chunk, in order); cluster starts are
-        // re-opened at the chunk boundary (members of a split cluster are orthogonalised
-        // against earlier members of the same chunk only).
-        for (int w = warp; w < qc; w += EIG_WARPS) {
-            const int q = q0 + w;
-            const bool starts = (w == 0) || clu[q];
-            if (!starts) continue;
-            int end = w + 1;
-            while (end < qc && !clu[q0 + end]) ++end;
-            float *u0 = scratch + (long long)warp * (4 * n + n / 4 + 1);
-            float *u1 = u0 + n, *u2 = u1 + n, *lm = u2 + n;
-            unsigned char *piv = (unsigned char *)(lm + n);
-            for (int mbr = w; mbr < end; ++mbr) {
-                float *z = zv + (long long)mbr * n;
-                const float lm_ = lamv[q0 + mbr];
-                for (int i = lane; i < n; i += 32)
-                    z[i] = 1.f + 0.25f * (float)(((i * 7919 + (q0 + mbr) * 104729) % 997) - 498) / 498.f;
-                __syncwarp();
-                for (int it = 0; it < INV_ITERS; ++it) {
-                    if (lane == 0) tri_solve(dd, ff, n, lm_, z, u0, u1, u2, lm, piv, FLT_EPSILON * tnorm + pivmin);
-                    __syncwarp();
-                    // orthogonalise against earlier members of the cluster
+    for (int q0 = 0; q0 < r; q0 += IV_CHUNK) {
+        const int qc = min(IV_CHUNK, r - q0);
+        for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
+            const int q = idx / n, i = idx - q * n;
+            zv[i * IV_ST + q] = 1.f + 0.25f * (float)(((i * 7919 + (q0 + q) * 104729) % 997) - 498) / 498.f;
+        }
+        __syncthreads();
+        for (int it = 0; it < INV_ITERS; ++it) {
+            if (tid < qc)
+                tri_solve<IV_ST>(dd, ff, n, lamv[q0 + tid], zv + tid, lu0 + tid, lu1 + tid, lu2 + tid, llm + tid,
+                                 lpv + tid, FLT_EPSILON * tnorm + pivmin, it == 0);
+            __syncthreads();
+            for (int w = warp; w < qc; w += EIG_WARPS) {
+                if (!(w == 0 || clu[q0 + w])) continue;
+                int end = w + 1;
+                while (end < qc && !clu[q0 + end]) ++end;
+                for (int mbr = w; mbr < end; ++mbr) {
                     for (int o = w; o < mbr; ++o) {
-                        const float *zo = zv + (long long)o * n;
                         float dot = 0.f;
-                        for (int i = lane; i < n; i += 32) dot += zo[i] * z[i];
+                        for (int i = lane; i < n; i += 32) dot += zv[i * IV_ST + o] * zv[i * IV_ST + mbr];
                         dot = wsum(dot);
-                        for (int i = lane; i < n; i += 32) z[i] -= dot * zo[i];
+                        for (int i = lane; i < n; i += 32) zv[i * IV_ST + mbr] -= dot * zv[i * IV_ST + o];
                         __syncwarp();
                     }
                     float nrm = 0.f;
-                    for (int i = lane; i < n; i += 32) nrm += z[i] * z[i];
+                    for (int i = lane; i < n; i += 32) nrm += zv[i * IV_ST + mbr] * zv[i * IV_ST + mbr];
                     nrm = wsum(nrm);
                     const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
-                    for (int i = lane; i < n; i += 32) z[i] *= inv;
+                    for (int i = lane; i < n; i += 32) zv[i * IV_ST + mbr] *= inv;
                     __syncwarp();
                 }
             }
+            __syncthreads();
+        }
+        // back-transformation y = Q P z, reflectors applied for k = n-3 .. 0 in batches of EV_HB
+        for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
+            const int w = idx / n, i = idx - w * n;
+            Yc[idx] = cscale(ph[i], zv[i * IV_ST + w]);
         }
         __syncthreads();
-        // back-transformation: y = P z (complex), then y <- H_k y for k = n-3 .. 0.
-        cf *Yc = (cf *)scratch;                                    // [qc][n]
-        for (long long idx = tid; idx < (long long)qc * n; idx += EIG_THREADS) {
-            const int w = (int)(idx / n), i = (int)(idx - (long long)w * n);
-            Yc[idx] = cscale(ph[i], zv[(long long)w * n + i]);
-        }
-        __syncthreads();
-        for (int k = n - 3; k >= 0; --k) {
-            const float tau = taus[k];
-            if (tau == 0.f) continue;
-            const int m = n - k - 1;
-            const cf *hv = Gglob + colstart(k, n) + 1;
-            for (int i = tid; i < m; i += EIG_THREADS) vb[i] = hv[i];
+        for (int kb = n - 3; kb >= 0; kb -= EV_HB) {
+            const int nbat = min(EV_HB, kb + 1);
+            // stage reflectors kb, kb-1, ..., kb-nbat+1 (reflector k has n-k-1 entries)
+            for (int b = 0; b < nbat; ++b) {
+                const int k = kb - b;
+                const int m = n - k - 1;
+                const cf *hv = Gglob + colstart(k, n) + 1;
+                for (int i = tid; i < m; i += EIG_THREADS) hb[(long long)b * n + i] = hv[i];
+            }
             __syncthreads();
             for (int w = warp; w < qc; w += EIG_WARPS) {
-                cf *y = Yc + (long long)w * n + k + 1;
-                float sr = 0.f, si = 0.f;
-                for (int i = lane; i < m; i += 32) {          // v^H y
-                    const cf v = vb[i], yy = y[i];
-                    sr += v.x * yy.x + v.y * yy.y;
-                    si += v.x * yy.y - v.y * yy.x;
-                }
-                sr = wsum(sr) * tau;
-                si = wsum(si) * tau;
-                for (int i = lane; i < m; i += 32) {
-                    const cf v = vb[i];
-                    y[i].x -= v.x * sr - v.y * si;
-                    y[i].y -= v.x * si + v.y * sr;
+                for (int b = 0; b < nbat; ++b) {
+                    const int k = kb - b;
+                    const float tau = taus[k];
+                    if (tau == 0.f) continue;
+                    const int m = n - k - 1;
+                    const cf *vk = hb + (long long)b * n;
+                    cf *y = Yc + (long long)w * n + k + 1;
+                    float sr = 0.f, si = 0.f;
+                    for (int i = lane; i < m; i += 32) {
+                        const cf v = vk[i], yy = y[i];
+                        sr += v.x * yy.x + v.y * yy.y;
+                        si += v.x * yy.y - v.y * yy.x;
+                    }
+                    sr = wsum(sr) * tau;
+                    si = wsum(si) * tau;
+                    for (int i = lane; i < m; i += 32) {
+                        const cf v = vk[i];
+                        y[i].x -= v.x * sr - v.y * si;
+                        y[i].y -= v.x * si + v.y * sr;
+                    }
+                    __syncwarp();
                 }
             }
             __syncthreads();
         }
-        for (long long idx = tid; idx < (long long)qc * n; idx += EIG_THREADS) {
-            const int w = (int)(idx / n), i = (int)(idx - (long long)w * n);
+        for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
+            const int w = idx / n, i = idx - w * n;
             const cf y = Yc[idx];
             if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(a.status, (unsigned)ST_NONFINITE);
             V[(long long)(q0 + w) * n + i] = y;
@@ -578,26 +894,23 @@ cudaError_t eig_init_attributes() {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     g_eig_smem_max = optin - 2048;
-    e = cudaFuncSetAttribute(k_heig, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
+    const int mx = g_eig_smem_max;
+    e = cudaFuncSetAttribute(k_tridiag<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag_g, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<16, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<8, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_apply_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
 }
 
-// shared bytes needed by k_heig for order n
-static size_t heig_smem(int n) {
-    const size_t pk = (size_t)n * (n + 1) / 2;
-    const bool in_smem = n <= EIG_SMEM_MAX_N;
-    size_t b = 3 * (size_t)n * sizeof(cf) + 4 * (size_t)n * sizeof(float);
-    const size_t gbytes = (in_smem ? pk : 0) * sizeof(cf);
-    // eigen stage: lam [n] + clu [n] + z [chunk][n] + per-warp (4n + n/4 + 1) floats, or Y [chunk][n] cf
-    const size_t per_warp = (4 * (size_t)n + n / 4 + 1) * sizeof(float);
-    const size_t st1 = 2 * (size_t)n * 4 + (size_t)EIG_MAXR_CHUNK * n * sizeof(float) +
-                       (size_t)EIG_WARPS * per_warp;
-    const size_t st2 = 2 * (size_t)n * 4 + (size_t)EIG_MAXR_CHUNK * n * sizeof(float) +
-                       (size_t)EIG_MAXR_CHUNK * n * sizeof(cf);
-    const size_t st = st1 > st2 ? st1 : st2;
-    return b + (gbytes > st ? gbytes : st);
+static size_t tridiag_smem(int n) {
+    return al16((size_t)n * (n + 1) / 2 * 8) + (size_t)(EIG_WARPS + 5) * n * 8 + (size_t)n * 4 + 16;
 }
+static size_t tridiag_g_smem(int n) { return 2 * (size_t)n * 8 + (size_t)n * 4 + 16; }
+static int ev_chunk(int nmax) { return nmax <= 352 ? 16 : 8; }
 
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,
                         const int *active, cudaStream_t st) {
@@ -612,13 +925,37 @@ cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const 
     return cudaGetLastError();
 }
 
+template <int RPL>
+static void tridiag_launch(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, size_t smem,
+                           cudaStream_t st) {
+    k_tridiag<RPL><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea);
+}
+
 cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, cudaStream_t st) {
     if (mat_count <= 0) return cudaSuccess;
     if (g_eig_smem_max == 0) return cudaErrorNotReady;
+    int nmax = 0;
+    for (int k = 0; k < gs.n; ++k) nmax = max(nmax, gs.g[k].s);
+    // 1. tridiagonalisation
+    if (nmax <= EIG_SMEM_MAX_N) {
+        const size_t smem = tridiag_smem(nmax);
+        if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
+        if (nmax <= 32) tridiag_launch<1>(gs, mat_begin, mat_count, ea, smem, st);
+        else if (nmax <= 64) tridiag_launch<2>(gs, mat_begin, mat_count, ea, smem, st);
+        else if (nmax <= 128) tridiag_launch<4>(gs, mat_begin, mat_count, ea, smem, st);
+        else tridiag_launch<7>(gs, mat_begin, mat_count, ea, smem, st);
+    } else {
+        k_tridiag_g<<<mat_count, EIG_THREADS, tridiag_g_smem(nmax), st>>>(gs, mat_begin, ea);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // 2. eigenpairs above t^2 and back-transformation
+    const int chunk = ev_chunk(nmax);
     size_t smem = 0;
-    for (int k = 0; k < gs.n; ++k) smem = max(smem, heig_smem(gs.g[k].s));
+    for (int k = 0; k < gs.n; ++k) smem = max(smem, ev_layout(gs.g[k].s, chunk, chunk + 1).total);
     if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
-    k_heig<<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea);
+    if (chunk == 16) k_eigvec<16, 17><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea);
+    else k_eigvec<8, 9><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea);
     return cudaGetLastError();
 }
 
