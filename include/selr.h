@@ -233,6 +233,57 @@ selr_status selr_profile_read(selr_plan *plan, int32_t stage, float *total_ms, i
  * SELR_ERR_CUDA if the stream reports an error; clears the record. */
 selr_status selr_sync_status(selr_plan *plan, selr_stream stream);
 
+/* ---------------------------------------------------------------------
+ * Reverse mode, for unrolled reconstructions whose per-iteration SVT
+ * thresholds and multiplier steps are learned (differentiating through the
+ * iteration of Algorithm S1; the paper fixes these scalars and has no
+ * reverse pass).  Cotangents use the real inner product Re tr(X^H Y) of
+ * complex arrays, so the VJP of a complex-linear map is its conjugate
+ * transpose.
+ * --------------------------------------------------------------------- */
+
+/* VJP of Z = S_t(A) (Eqs. 16-17) for nmat matrices A [nmat][rows][cols]
+ * (complex64, device, natural row-major layout, not modified) and the
+ * cotangent Zbar of the same shape.  With B = A (cols <= rows) or A^T and
+ * G = B^H B = V diag(lambda) V^H, S_t(B) = B h(G) with
+ * h(lambda) = max(1 - t / sqrt(lambda), 0), and
+ *   Bbar = Zbar h(G) + B (Gbar + Gbar^H),
+ *   Gbar = V [Gamma o (V^H B^H Zbar V)] V^H,
+ *   Gamma_ij = (h(lambda_i) - h(lambda_j)) / (lambda_i - lambda_j)
+ *              (h'(lambda) at ties; evaluated as t / (s_i s_j (s_i + s_j)),
+ *              s = sqrt(lambda), when both exceed t, which has no cancellation),
+ *   tbar = -Re sum_{lambda_i > t^2} (V^H B^H Zbar V)_ii / sqrt(lambda_i).
+ * The eigenpairs of G come from one-sided Jacobi on [B; I] with the plan's
+ * jacobi_max_sweeps / jacobi_tol (a matrix reaching the cap is reported by
+ * selr_sync_status as SELR_ERR_NO_CONVERGENCE).  Abar: [nmat][rows][cols]
+ * device output (may not alias A or Zbar).  tbar: device float receiving
+ * the threshold cotangent summed over the nmat matrices.  Shapes as for
+ * selr_svt plus min(rows, cols) <= 480; the first call allocates the
+ * plan's reverse-mode workspace (about 11 lifted arrays). */
+selr_status selr_svt_vjp(selr_plan *plan, const void *A, const void *Zbar, int32_t nmat, int32_t rows,
+                         int32_t cols, float thresh, void *Abar, float *tbar, selr_stream stream);
+
+/* VJP of the X-update of Eq. 15 / S7 as computed by selr_dc:
+ * K = (lambda U Y + beta S) / den, den = lambda U + beta (d_a + d_b), S the
+ * sum of the transformed lift adjoints.  Given Kbar [L][J][M][N] (device),
+ * writes Sbar = beta Kbar / den into adj_out and, if Ybar is not NULL,
+ * Ybar = lambda U Kbar / den; with lambda <= 0 (hard consistency, K = Y on
+ * sampled points) Sbar = Kbar / (d_a + d_b) off the mask, 0 on it, and
+ * Ybar = Kbar on it.  Where den is 0 both are 0 (the forward writes 0
+ * there).  The caller applies the inverse transforms of the two adjoint
+ * families to Sbar.  mask: [L][M][N] uint8, device. */
+selr_status selr_dc_vjp(selr_plan *plan, const uint8_t *mask, const void *Kbar, void *adj_out, void *Ybar,
+                        selr_stream stream);
+
+/* out = a x + b y + c z over n complex64 elements (device; y or z NULL drops
+ * its term; out may alias any input). */
+selr_status selr_axpby(int64_t n, float a, const void *x, float b, const void *y, float c, const void *z,
+                       void *out, selr_stream stream);
+
+/* *out = Re sum_i conj(x_i) y_i over n complex64 elements (device), reduced
+ * in a fixed order in double precision; out is a device float. */
+selr_status selr_dot_re(selr_plan *plan, int64_t n, const void *x, const void *y, float *out, selr_stream stream);
+
 /* Name of the last CUDA runtime error behind a SELR_ERR_CUDA returned on
  * the calling host thread (diagnostics; static storage). */
 const char *selr_last_error_string(void);

@@ -56,6 +56,12 @@ SIGNATURES = {
     "selr_profile_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_float), ctypes.POINTER(c_int32)]),
     "selr_status_string": (ctypes.c_char_p, [c_int32]),
     "selr_last_error_string": (ctypes.c_char_p, []),
+    "selr_svt_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p,
+                               c_void_p, c_void_p]),
+    "selr_dc_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "selr_axpby": (c_int32, [ctypes.c_int64, c_float, c_void_p, c_float, c_void_p, c_float, c_void_p, c_void_p,
+                             c_void_p]),
+    "selr_dot_re": (c_int32, [c_void_p, ctypes.c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None

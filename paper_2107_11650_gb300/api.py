@@ -199,3 +199,41 @@ def selr_solve(plan: Plan, Y, mask, X_out, stream=None):
 def selr_sync_status(plan: Plan, stream=None) -> int:
     """Synchronise and return the device-side status code (0 = SELR_OK)."""
     return int(plan.lib.selr_sync_status(plan.handle, _stream(stream)))
+
+
+# ------------------------------------------------------------- reverse mode
+def selr_svt_vjp(plan: Plan, A, Zbar, thresh: float, Abar, tbar, stream=None):
+    """Abar <- VJP of S_t at A for cotangent Zbar; tbar (device float32[1]) <- dL/dt."""
+    if A.dim() != 3:
+        raise ValueError("A must be [nmat][rows][cols]")
+    nmat, rows, cols = A.shape
+    n = A.numel()
+    check(plan.lib.selr_svt_vjp(plan.handle, _ptr(A, torch.complex64, "A"), _ptr(Zbar, torch.complex64, "Zbar", n),
+                                nmat, rows, cols, float(thresh), _ptr(Abar, torch.complex64, "Abar", n),
+                                _ptr(tbar, torch.float32, "tbar", 1), _stream(stream)), "selr_svt_vjp")
+
+
+def selr_dc_vjp(plan: Plan, mask, Kbar, adj_out, Ybar=None, stream=None):
+    d = plan.desc
+    check(plan.lib.selr_dc_vjp(plan.handle, _ptr(mask, torch.uint8, "mask", d.L * d.M * d.N),
+                               _ptr(Kbar, torch.complex64, "Kbar", plan.nK),
+                               _ptr(adj_out, torch.complex64, "adj_out", plan.nK),
+                               _ptr(Ybar, torch.complex64, "Ybar", plan.nK, allow_none=True), _stream(stream)),
+          "selr_dc_vjp")
+
+
+def selr_axpby(out, a, x, b=0.0, y=None, c=0.0, z=None, stream=None):
+    """out = a x + b y + c z (complex64 device arrays of equal size)."""
+    lib = _lib.load()
+    n = x.numel()
+    check(lib.selr_axpby(n, float(a), _ptr(x, torch.complex64, "x"), float(b),
+                         _ptr(y, torch.complex64, "y", n, allow_none=True), float(c),
+                         _ptr(z, torch.complex64, "z", n, allow_none=True), _ptr(out, torch.complex64, "out", n),
+                         _stream(stream)), "selr_axpby")
+
+
+def selr_dot_re(plan: Plan, x, y, out, stream=None):
+    """out (device float32[1]) <- Re sum conj(x) y."""
+    n = x.numel()
+    check(plan.lib.selr_dot_re(plan.handle, n, _ptr(x, torch.complex64, "x"), _ptr(y, torch.complex64, "y", n),
+                               _ptr(out, torch.float32, "out", 1), _stream(stream)), "selr_dot_re")

@@ -1,0 +1,320 @@
+// Reverse-mode pieces of the unrolled reconstruction: the vector-Jacobian
+// product of the SVT (Eqs. 16-17) through the Daleckii-Krein formula, the
+// X-update (Eq. 15) scaling, and small batched linear-algebra helpers.
+//
+// SVT VJP.  For B (len x s, s <= len) with G = B^H B = V diag(lambda) V^H,
+//     Z = S_t(B) = B h(G),   h(lambda) = max(1 - t / sqrt(lambda), 0).
+// For a cotangent Zbar (real inner product Re tr(Zbar^H dZ)):
+//     Bbar = Zbar h(G) + B (Gbar + Gbar^H),
+//     Gbar = V [Gamma o (V^H B^H Zbar V)] V^H,
+//     Gamma_ij = (h(lambda_i) - h(lambda_j)) / (lambda_i - lambda_j)
+//               (h'(lambda_i) where lambda_i = lambda_j),
+//     tbar = -Re sum_{lambda_i > t^2} (V^H B^H Zbar V)_ii / sqrt(lambda_i).
+// dh(G) follows the Daleckii-Krein theorem for the matrix function h; the
+// divided difference is the 1 / (sigma_i^2 - sigma_j^2) term of the
+// singular-vector derivative, guarded by evaluating it in a form without
+// cancellation (k_gamma).  The eigenpairs of G come from one-sided Jacobi on
+// [B; I] (k_augment, k_jacobi with rotations chosen on B, k_split_aug):
+// V = the accumulated rotations is unitary to working precision even inside
+// clusters of small singular values, lambda_i = ||B v_i||^2.
+#include "selr_internal.cuh"
+
+#include <float.h>
+
+// ------------------------------------------------------------------- GEMM
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b] for row-major complex matrices.
+// op: 0 = N, 1 = T (transpose), 2 = H (conjugate transpose), 3 = C (conjugate).
+// A: op(A) is m x k; B: op(B) is k x n; lda/ldb/ldc are row strides of the
+// stored matrices, sa/sb/sc batch strides (elements).
+#define GM_T 32
+#define GM_K 16
+__device__ __forceinline__ cf opload(const cf *M, int op, long long ld, int r, int c) {
+    // element (r, c) of op(M)
+    cf v = (op == 0 || op == 3) ? M[(long long)r * ld + c] : M[(long long)c * ld + r];
+    if (op == 2 || op == 3) v.y = -v.y;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_cgemm(int m, int n, int k, cf alpha, const cf *A, int opa, long long lda,
+                                               long long sa, const cf *B, int opb, long long ldb, long long sb,
+                                               cf beta, cf *C, long long ldc, long long sc) {
+    __shared__ cf As[GM_K][GM_T + 1], Bs[GM_K][GM_T + 1];
+    const int b = blockIdx.z;
+    const cf *Ab = A + (long long)b * sa, *Bb = B + (long long)b * sb;
+    cf *Cb = C + (long long)b * sc;
+    const int r0 = blockIdx.y * GM_T, c0 = blockIdx.x * GM_T;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;     // 2x2 outputs per thread
+    float ar[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, ai[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int k0 = 0; k0 < k; k0 += GM_K) {
+        for (int idx = threadIdx.x; idx < GM_K * GM_T; idx += 256) {
+            const int kk = idx % GM_K, rr = idx / GM_K;
+            const int gk = k0 + kk;
+            As[kk][rr] = (r0 + rr < m && gk < k) ? opload(Ab, opa, lda, r0 + rr, gk) : mk(0.f, 0.f);
+            Bs[kk][rr] = (c0 + rr < n && gk < k) ? opload(Bb, opb, ldb, gk, c0 + rr) : mk(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GM_K; ++kk) {
+            const cf a0 = As[kk][ty], a1 = As[kk][ty + 16], b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+            const cf aa[2] = {a0, a1}, bb[2] = {b0, b1};
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    ar[u][w] = fmaf(aa[u].x, bb[w].x, fmaf(-aa[u].y, bb[w].y, ar[u][w]));
+                    ai[u][w] = fmaf(aa[u].x, bb[w].y, fmaf(aa[u].y, bb[w].x, ai[u][w]));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            const int r = r0 + ty + 16 * u, c = c0 + tx + 16 * w;
+            if (r < m && c < n) {
+                const cf acc = mk(ar[u][w], ai[u][w]);
+                cf out = cmul(alpha, acc);
+                if (beta.x != 0.f || beta.y != 0.f) out = cadd(out, cmul(beta, Cb[(long long)r * ldc + c]));
+                Cb[(long long)r * ldc + c] = out;
+            }
+        }
+}
+
+cudaError_t launch_cgemm(int batch, int m, int n, int k, cf alpha, const cf *A, int opa, long long lda, long long sa,
+                         const cf *B, int opb, long long ldb, long long sb, cf beta, cf *C, long long ldc,
+                         long long sc, cudaStream_t st) {
+    if (batch <= 0 || m <= 0 || n <= 0) return cudaSuccess;
+    dim3 grid((n + GM_T - 1) / GM_T, (m + GM_T - 1) / GM_T, batch);
+    k_cgemm<<<grid, 256, 0, st>>>(m, n, k, alpha, A, opa, lda, sa, B, opb, ldb, sb, beta, C, ldc, sc);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- SVT VJP parts
+__device__ __forceinline__ float hfun(float lam, float t) {
+    const float sg = sqrtf(fmaxf(lam, 0.f));
+    return sg > t ? 1.f - t / sg : 0.f;
+}
+
+// M[b][i][j] <- Gamma_ij M[b][i][j] (eigenvalues in any order).  Written in
+// sigma = sqrt(lambda) so that no difference of nearly equal numbers is formed:
+//   both above t:  (h(l_i) - h(l_j)) / (l_i - l_j) = t / (s_i s_j (s_i + s_j))
+//                  (at s_i = s_j this is h'(lambda) = t / (2 s^3): no guard needed);
+//   one above t:   h(l_i) / (l_i - l_j) with l_i > t^2 >= l_j;   none: 0.
+__global__ void k_gamma(int s, const float *lam, float t, cf *M, long long sm, long long sl) {
+    const int b = blockIdx.y;
+    const float *lb = lam + (long long)b * sl;
+    cf *Mb = M + (long long)b * sm;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < s * s; idx += gridDim.x * blockDim.x) {
+        const int i = idx / s, j = idx - i * s;
+        const float li = fmaxf(lb[i], 0.f), lj = fmaxf(lb[j], 0.f);
+        const float si = sqrtf(li), sj = sqrtf(lj);
+        const bool ai = si > t, aj = sj > t;
+        float gmm = 0.f;
+        if (ai && aj) gmm = t / (si * sj * (si + sj));
+        else if (ai) gmm = (1.f - t / si) / (li - lj);
+        else if (aj) gmm = (1.f - t / sj) / (lj - li);
+        Mb[idx] = cscale(Mb[idx], gmm);
+    }
+}
+
+// Vs[b][q][i] = f(lam[b][q]) * V[b][q][i] with f = h (mode 0) or 1/sqrt(lam) on the
+// selected pairs (mode 1: lam > t^2, else 0).  V stored eigenvector-major.
+__global__ void k_scale_vecs(int s, const float *lam, float t, const cf *V, cf *Vs, long long sv, long long sl,
+                             int mode) {
+    const int b = blockIdx.y;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < s * s; idx += gridDim.x * blockDim.x) {
+        const int q = idx / s;
+        const float l = lam[(long long)b * sl + q];
+        const float sg = sqrtf(fmaxf(l, 0.f));
+        float f;
+        if (mode == 0) f = hfun(l, t);
+        else f = sg > t ? 1.f / sg : 0.f;
+        Vs[(long long)b * sv + idx] = cscale(V[(long long)b * sv + idx], f);
+    }
+}
+
+// out[b] = -Re sum_i (V^H C V)_ii / sqrt(lam_i) over lam_i > t^2, summed over b into
+// *tbar (single block, fixed order => deterministic).  Ct holds V^H C V.
+__global__ void k_tbar(int batch, int s, const float *lam, float t, const cf *Ct, long long sm, long long sl,
+                       float *tbar) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (long long idx = threadIdx.x; idx < (long long)batch * s; idx += blockDim.x) {
+        const int b = (int)(idx / s), i = (int)(idx - (long long)b * s);
+        const double sg = sqrt((double)fmaxf(lam[(long long)b * sl + i], 0.f));
+        if (sg > t) acc -= (double)Ct[(long long)b * sm + (long long)i * s + i].x / sg;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *tbar = (float)red[0];
+}
+
+// M <- M + M^H (square, per batch), in place on the lower/upper pairs.
+__global__ void k_herm_sum(int s, cf *M, long long sm) {
+    const int b = blockIdx.y;
+    cf *Mb = M + (long long)b * sm;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < s * s; idx += gridDim.x * blockDim.x) {
+        const int i = idx / s, j = idx - i * s;
+        if (j > i) continue;
+        const cf a = Mb[(long long)i * s + j], c = Mb[(long long)j * s + i];
+        const cf v = mk(a.x + c.x, a.y - c.y);
+        Mb[(long long)i * s + j] = v;
+        Mb[(long long)j * s + i] = cconj(v);
+    }
+}
+
+cudaError_t launch_gamma(int batch, int s, const float *lam, float t, cf *M, long long sm, long long sl,
+                         cudaStream_t st) {
+    dim3 grid((s * s + 255) / 256, batch);
+    k_gamma<<<grid, 256, 0, st>>>(s, lam, t, M, sm, sl);
+    return cudaGetLastError();
+}
+cudaError_t launch_scale_vecs(int batch, int s, const float *lam, float t, const cf *V, cf *Vs, long long sv,
+                              long long sl, int mode, cudaStream_t st) {
+    dim3 grid((s * s + 255) / 256, batch);
+    k_scale_vecs<<<grid, 256, 0, st>>>(s, lam, t, V, Vs, sv, sl, mode);
+    return cudaGetLastError();
+}
+cudaError_t launch_tbar(int batch, int s, const float *lam, float t, const cf *Ct, long long sm, long long sl,
+                        float *tbar, cudaStream_t st) {
+    k_tbar<<<1, 256, 0, st>>>(batch, s, lam, t, Ct, sm, sl, tbar);
+    return cudaGetLastError();
+}
+cudaError_t launch_herm_sum(int batch, int s, cf *M, long long sm, cudaStream_t st) {
+    dim3 grid((s * s + 255) / 256, batch);
+    k_herm_sum<<<grid, 256, 0, st>>>(s, M, sm);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- BLAS-1 helpers
+// out = a x + b y (+ c z), complex64 arrays of n elements (y, z may be null).
+__global__ void k_axpbypcz(long long n, float a, const cf *x, float b, const cf *y, float c, const cf *z, cf *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        cf v = cscale(x[i], a);
+        if (y) v = cadd(v, cscale(y[i], b));
+        if (z) v = cadd(v, cscale(z[i], c));
+        out[i] = v;
+    }
+}
+cudaError_t launch_axpbypcz(long long n, float a, const cf *x, float b, const cf *y, float c, const cf *z, cf *out,
+                            cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = min((n + 255) / 256, (long long)152 * 8);
+    k_axpbypcz<<<(unsigned)blocks, 256, 0, st>>>(n, a, x, b, y, c, z, out);
+    return cudaGetLastError();
+}
+
+// *out = Re <x, y> = sum Re(conj(x_i) y_i), fixed-order two-level reduction.
+__global__ void k_dot_partial(long long n, const cf *x, const cf *y, double *part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (double)x[i].x * y[i].x + (double)x[i].y * y[i].y;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void k_dot_final(int nb, const double *part, float *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0;
+        for (int i = 0; i < nb; ++i) a += part[i];
+        *out = (float)a;
+    }
+}
+#define DOT_BLOCKS 304
+cudaError_t launch_dot_re(long long n, const cf *x, const cf *y, double *part, float *out, cudaStream_t st) {
+    k_dot_partial<<<DOT_BLOCKS, 256, 0, st>>>(n, x, y, part);
+    k_dot_final<<<1, 32, 0, st>>>(DOT_BLOCKS, part, out);
+    return cudaGetLastError();
+}
+
+// X-update VJP: out[i] = beta Kbar[i] / den(i) where den = lambda U + beta (d_a + d_b)
+// (hard consistency: out = Kbar / (d_a + d_b) on unsampled points, 0 on sampled ones);
+// zero where den == 0.  ybar (nullable) receives lambda U Kbar / den.
+__global__ void k_dc_vjp(DcArgs a, const cf *Kbar, cf *out, cf *ybar) {
+    const long long total = (long long)a.L * a.J * a.M * a.N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int kn = (int)(i % a.N);
+        const long long r1 = i / a.N;
+        const int m = (int)(r1 % a.M);
+        const int l = (int)(r1 / ((long long)a.M * a.J));
+        const float u = a.mask[((long long)l * a.M + m) * a.N + kn] ? 1.f : 0.f;
+        const float dd = a.da[kn] + (a.model2d ? a.db[m] : a.db[l]);
+        const cf kb = Kbar[i];
+        cf o = mk(0.f, 0.f), yb = mk(0.f, 0.f);
+        if (a.lambda > 0.f) {
+            const float den = a.lambda * u + a.beta * dd;
+            if (den != 0.f) {
+                o = cscale(kb, a.beta / den);
+                yb = cscale(kb, a.lambda * u / den);
+            }
+        } else if (u > 0.f) {
+            yb = kb;
+        } else if (dd != 0.f) {
+            o = cscale(kb, 1.f / dd);
+        }
+        out[i] = o;
+        if (ybar) ybar[i] = yb;
+    }
+}
+cudaError_t launch_dc_vjp(const DcArgs &a, const cf *Kbar, cf *out, cf *ybar, cudaStream_t st) {
+    const long long total = (long long)a.L * a.J * a.M * a.N;
+    const long long blocks = min((total + 255) / 256, (long long)152 * 8);
+    k_dc_vjp<<<(unsigned)blocks, 256, 0, st>>>(a, Kbar, out, ybar);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- Jacobi on [B; I] (VJP)
+// aug[b][q] = [Bt[b][q][0..len); e_q] : column q of B followed by column q of
+// the identity, so that one-sided Jacobi with rotations chosen on the first
+// len entries leaves [B Q; Q] (Q unitary, B Q with orthogonal columns).
+__global__ void k_augment(int s, int len, const cf *Bt, cf *aug) {
+    const int b = blockIdx.y;
+    const int L = len + s;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)s * L;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(idx / L), e = (int)(idx - (long long)q * L);
+        cf v;
+        if (e < len) v = Bt[(long long)b * s * len + (long long)q * len + e];
+        else v = mk(e - len == q ? 1.f : 0.f, 0.f);
+        aug[(long long)b * s * L + idx] = v;
+    }
+}
+cudaError_t launch_augment(int batch, int s, int len, const cf *Bt, cf *aug, cudaStream_t st) {
+    if (batch <= 0) return cudaSuccess;
+    const long long per = (long long)s * (len + s);
+    dim3 grid((unsigned)min((per + 255) / 256, 64LL), batch);
+    k_augment<<<grid, 256, 0, st>>>(s, len, Bt, aug);
+    return cudaGetLastError();
+}
+
+// Vt[b][q][i] = Q[i][q] (eigenvector-major, row stride s, batch stride s*s) and
+// lam[b][q] = sigma[b][q]^2: the eigenpairs of G = B^H B.
+__global__ void k_split_aug(int s, int len, const cf *aug, const float *sigma, cf *Vt, float *lam) {
+    const int b = blockIdx.y;
+    const int L = len + s;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < s * s; idx += gridDim.x * blockDim.x) {
+        const int q = idx / s, i = idx - q * s;
+        Vt[(long long)b * s * s + idx] = aug[(long long)b * s * L + (long long)q * L + len + i];
+        if (i == 0) {
+            const float sg = sigma[(long long)b * s + q];
+            lam[(long long)b * s + q] = sg * sg;
+        }
+    }
+}
+cudaError_t launch_split_aug(int batch, int s, int len, const cf *aug, const float *sigma, cf *Vt, float *lam,
+                             cudaStream_t st) {
+    if (batch <= 0) return cudaSuccess;
+    dim3 grid((unsigned)min((s * s + 255) / 256, 64), batch);
+    k_split_aug<<<grid, 256, 0, st>>>(s, len, aug, sigma, Vt, lam);
+    return cudaGetLastError();
+}

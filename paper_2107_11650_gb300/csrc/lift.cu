@@ -127,3 +127,29 @@ cudaError_t launch_natural_to_vm(const GroupSet &gs, const cf *A, cf *out, cf *o
     k_nat_to_vm<<<grid, LIFT_THREADS, 0, st>>>(gs, A, out, out2);
     return cudaGetLastError();
 }
+
+// Copy vector-major matrices back to natural layout [nmat][rows][cols].
+__global__ void __launch_bounds__(LIFT_THREADS)
+k_vm_to_nat(GroupSet gs, const cf *in, cf *A) {
+    int mat;
+    const int gi = find_group(gs, blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    const int per = g.rows * g.cols;
+    const long long mbase = g.off + (long long)mat * per;
+    for (int idx = blockIdx.y * LIFT_PER_BLOCK + threadIdx.x; idx < min(per, (int)(blockIdx.y + 1) * LIFT_PER_BLOCK);
+         idx += LIFT_THREADS) {
+        const int v = idx / g.len, e = idx - v * g.len;
+        int r, c;
+        if (g.trans) { r = v; c = e; } else { r = e; c = v; }
+        A[mbase + (long long)r * g.cols + c] = in[mbase + idx];
+    }
+}
+
+cudaError_t launch_vm_to_natural(const GroupSet &gs, const cf *in, cf *A, cudaStream_t st) {
+    if (gs.total <= 0) return cudaSuccess;
+    int maxper = 0;
+    for (int k = 0; k < gs.n; ++k) maxper = max(maxper, gs.g[k].rows * gs.g[k].cols);
+    dim3 grid(gs.total, (maxper + LIFT_PER_BLOCK - 1) / LIFT_PER_BLOCK);
+    k_vm_to_nat<<<grid, LIFT_THREADS, 0, st>>>(gs, in, A);
+    return cudaGetLastError();
+}

@@ -45,6 +45,10 @@ struct selr_plan {
     cudaEvent_t *ev;          // [prof_cap][NSTAGE][2]
     int prof_count;           // iterations timed by the last solve
     cudaGraphExec_t stage_graph[8];   // profiling: one graph per stage (NSTAGE <= 8)
+    // reverse-mode workspaces (allocated on the first VJP call)
+    cf *gw_Z, *gw_Bbar, *gw_S1, *gw_S2, *gw_S3, *gw_S4, *gw_V, *gw_aug;
+    float *gw_lam;
+    double *gw_part;
 };
 
 #define NSTAGE 7
@@ -230,6 +234,10 @@ static selr_status upload(void *dst, const void *src, size_t bytes) {
 extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     if (!p) return SELR_OK;
     drop_graphs(p);
+    void *gbufs[] = {p->gw_Z, p->gw_Bbar, p->gw_S1, p->gw_S2, p->gw_S3, p->gw_S4, p->gw_V, p->gw_aug, p->gw_lam,
+                     p->gw_part};
+    for (void *b : gbufs)
+        if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
                     p->rank, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status,
@@ -752,6 +760,127 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
 }
 
 extern "C" const char *selr_last_error_string(void) { return cudaGetErrorString(g_last_error); }
+
+// ------------------------------------------------------------ reverse mode
+static selr_status grad_workspace(selr_plan *p) {
+    if (p->gw_Z) return SELR_OK;
+    const size_t lb = sizeof(cf) * (size_t)p->lift_elems;
+    // s x s scratch fits in s x len (s <= len); [B; I] needs s (len + s) <= 2 s len.
+    // Buffers already allocated by an earlier, partly failed call are kept.
+    struct { void **ptr; size_t bytes; } req[] = {
+        {(void **)&p->gw_Bbar, lb}, {(void **)&p->gw_S1, lb}, {(void **)&p->gw_S2, lb},
+        {(void **)&p->gw_S3, lb},   {(void **)&p->gw_S4, lb}, {(void **)&p->gw_V, lb},
+        {(void **)&p->gw_aug, 2 * lb}, {(void **)&p->gw_lam, sizeof(float) * (size_t)p->vec_elems},
+        {(void **)&p->gw_part, sizeof(double) * 512},
+        {(void **)&p->gw_Z, lb},     // last: marks the workspace as complete
+    };
+    for (auto &r : req) {
+        if (*r.ptr) continue;
+        const selr_status s = alloc(p, r.ptr, r.bytes);
+        if (s != SELR_OK) return s;
+    }
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zbar, int32_t nmat, int32_t rows,
+                                    int32_t cols, float thresh, void *Abar, float *tbar, selr_stream stream) {
+    if (!p || !A || !Zbar || !Abar || !tbar || nmat < 1 || rows < 1 || cols < 1 || !(thresh >= 0.f) ||
+        !isfinite(thresh))
+        return SELR_ERR_INVALID_ARG;
+    GroupSet gs;
+    memset(&gs, 0, sizeof(gs));
+    gs.n = 1;
+    Group &g = gs.g[0];
+    g.kind = G_ROW;
+    g.nmat = nmat;
+    g.rows = rows;
+    g.cols = cols;
+    g.trans = cols > rows ? 1 : 0;
+    g.s = g.trans ? rows : cols;
+    g.len = g.trans ? cols : rows;
+    g.thresh = thresh;
+    finish_set(&gs);
+    const int n = g.s, len = g.len;
+    if (len > 512 || n > 480) return SELR_ERR_SHAPE;
+    if ((long long)nmat * rows * cols > p->lift_elems || (long long)nmat * n > p->vec_elems || nmat > p->gs.total)
+        return SELR_ERR_SHAPE;
+    selr_status ws = grad_workspace(p);
+    if (ws != SELR_OK) return ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    // Bt (vector-major: row q of Bt is column q of B) and Zbar in the same layout
+    CK(launch_natural_to_vm(gs, (const cf *)A, p->gw_S1, nullptr, st));
+    CK(launch_natural_to_vm(gs, (const cf *)Zbar, p->gw_Z, nullptr, st));
+    // every eigenpair of G = B^H B by one-sided Jacobi on [B; I]: orthonormal V even
+    // inside clusters of small eigenvalues, which the Gamma weights still separate
+    GroupSet ga = gs;
+    ga.g[0].len = len + n;
+    ga.g[0].dlen = len;
+    CK(launch_augment(nmat, n, len, p->gw_S1, p->gw_aug, st));
+    SvtArgs ja;
+    memset(&ja, 0, sizeof(ja));
+    ja.W = p->gw_aug;
+    ja.sigma = p->sigma;
+    ja.mat_status = p->mat_status;
+    ja.status = p->status;
+    ja.max_sweeps = p->d.jacobi_max_sweeps;
+    ja.tol = p->d.jacobi_tol;
+    CK(launch_jacobi(ga, 0, nmat, ja, st));
+    const long long sbl = (long long)n * len, ss = (long long)n * n;
+    cf *Vt = p->gw_V;
+    CK(launch_split_aug(nmat, n, len, p->gw_aug, p->sigma, Vt, p->gw_lam, st));
+    const cf one = mk(1.f, 0.f), zero = mk(0.f, 0.f);
+    cf *Bt = p->gw_S1;
+    // C = B^H Zbar = conj(Bt) Zt^T
+    CK(launch_cgemm(nmat, n, n, len, one, Bt, 3, len, sbl, p->gw_Z, 1, len, sbl, zero, p->gw_S2, n, ss, st));
+    // Ct = V^H C V = conj(Vt) C Vt^T
+    CK(launch_cgemm(nmat, n, n, n, one, Vt, 3, n, ss, p->gw_S2, 0, n, ss, zero, p->gw_S3, n, ss, st));
+    CK(launch_cgemm(nmat, n, n, n, one, p->gw_S3, 0, n, ss, Vt, 1, n, ss, zero, p->gw_S4, n, ss, st));
+    CK(launch_tbar(nmat, n, p->gw_lam, thresh, p->gw_S4, ss, n, tbar, st));
+    CK(launch_gamma(nmat, n, p->gw_lam, thresh, p->gw_S4, ss, n, st));
+    // Gbar = V (Gamma o Ct) V^H = Vt^T S4 conj(Vt); then Gbar + Gbar^H
+    CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, ss, p->gw_S4, 0, n, ss, zero, p->gw_S2, n, ss, st));
+    CK(launch_cgemm(nmat, n, n, n, one, p->gw_S2, 0, n, ss, Vt, 3, n, ss, zero, p->gw_S3, n, ss, st));
+    CK(launch_herm_sum(nmat, n, p->gw_S3, ss, st));
+    // h(G) = V h(Lambda) V^H = Vt^T conj(h o Vt)
+    CK(launch_scale_vecs(nmat, n, p->gw_lam, thresh, Vt, p->gw_S4, ss, n, 0, st));
+    CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, ss, p->gw_S4, 3, n, ss, zero, p->gw_S2, n, ss, st));
+    // Bbar^T = h(G)^T Zt + (Gbar + Gbar^H)^T Bt
+    CK(launch_cgemm(nmat, n, len, n, one, p->gw_S2, 1, n, ss, p->gw_Z, 0, len, sbl, zero, p->gw_Bbar, len, sbl, st));
+    CK(launch_cgemm(nmat, n, len, n, one, p->gw_S3, 1, n, ss, Bt, 0, len, sbl, one, p->gw_Bbar, len, sbl, st));
+    CK(launch_vm_to_natural(gs, p->gw_Bbar, (cf *)Abar, st));
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_dc_vjp(selr_plan *p, const uint8_t *mask, const void *Kbar, void *adj_out, void *Ybar,
+                                   selr_stream stream) {
+    if (!p || !mask || !Kbar || !adj_out) return SELR_ERR_INVALID_ARG;
+    DcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.model2d = p->model2d;
+    a.L = p->L; a.J = p->J; a.M = p->M; a.N = p->N;
+    a.mask = mask;
+    a.da = p->da; a.db = p->db;
+    a.lambda = p->d.lambda;
+    a.beta = p->d.beta;
+    CK(launch_dc_vjp(a, (const cf *)Kbar, (cf *)adj_out, (cf *)Ybar, (cudaStream_t)stream));
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_axpby(int64_t n, float a, const void *x, float b, const void *y, float c, const void *z,
+                                  void *out, selr_stream stream) {
+    if (n < 0 || !x || !out) return SELR_ERR_INVALID_ARG;
+    CK(launch_axpbypcz(n, a, (const cf *)x, b, (const cf *)y, c, (const cf *)z, (cf *)out, (cudaStream_t)stream));
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_dot_re(selr_plan *p, int64_t n, const void *x, const void *y, float *out,
+                                   selr_stream stream) {
+    if (!p || n < 0 || !x || !y || !out) return SELR_ERR_INVALID_ARG;
+    selr_status ws = grad_workspace(p);
+    if (ws != SELR_OK) return ws;
+    CK(launch_dot_re(n, (const cf *)x, (const cf *)y, p->gw_part, out, (cudaStream_t)stream));
+    return SELR_OK;
+}
 
 extern "C" selr_status selr_set_iterations(selr_plan *p, int32_t max_iter, float tol) {
     if (!p || max_iter < 1 || !isfinite(tol)) return SELR_ERR_INVALID_ARG;

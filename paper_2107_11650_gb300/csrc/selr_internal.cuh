@@ -39,6 +39,7 @@ struct Group {
     int trans;
     int s, len;
     float thresh;          // SVT threshold of this family
+    int dlen;              // Jacobi: inner products over the first dlen entries only (0: len)
     int M, N, L;           // array dims of the source / adjoint arrays
     long long off;         // element offset of matrix 0 in lifted workspaces
     long long soff;        // offset of matrix 0 in per-vector arrays (sigma)
@@ -122,6 +123,7 @@ cudaError_t launch_lift(const GroupSet &gs, int gfirst, int mat_begin, int mat_c
 cudaError_t launch_adjoint(const GroupSet &gs, int gfirst, int mat_begin, int mat_count,
                            const cf *E, int e_natural, cudaStream_t st);
 cudaError_t launch_natural_to_vm(const GroupSet &gs, const cf *A, cf *out, cf *out2, cudaStream_t st);
+cudaError_t launch_vm_to_natural(const GroupSet &gs, const cf *in, cf *A, cudaStream_t st);
 
 // svt.cu
 struct SvtArgs {
@@ -162,6 +164,24 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
 cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, const SvtArgs &a,
                              cudaStream_t st);
 
+// grad.cu
+cudaError_t launch_cgemm(int batch, int m, int n, int k, cf alpha, const cf *A, int opa, long long lda, long long sa,
+                         const cf *B, int opb, long long ldb, long long sb, cf beta, cf *C, long long ldc,
+                         long long sc, cudaStream_t st);
+cudaError_t launch_gamma(int batch, int s, const float *lam, float t, cf *M, long long sm, long long sl,
+                         cudaStream_t st);
+cudaError_t launch_scale_vecs(int batch, int s, const float *lam, float t, const cf *V, cf *Vs, long long sv,
+                              long long sl, int mode, cudaStream_t st);
+cudaError_t launch_tbar(int batch, int s, const float *lam, float t, const cf *Ct, long long sm, long long sl,
+                        float *tbar, cudaStream_t st);
+cudaError_t launch_herm_sum(int batch, int s, cf *M, long long sm, cudaStream_t st);
+cudaError_t launch_axpbypcz(long long n, float a, const cf *x, float b, const cf *y, float c, const cf *z, cf *out,
+                            cudaStream_t st);
+cudaError_t launch_dot_re(long long n, const cf *x, const cf *y, double *part, float *out, cudaStream_t st);
+cudaError_t launch_augment(int batch, int s, int len, const cf *Bt, cf *aug, cudaStream_t st);
+cudaError_t launch_split_aug(int batch, int s, int len, const cf *aug, const float *sigma, cf *Vt, float *lam,
+                             cudaStream_t st);
+
 // dc.cu
 struct DcArgs {
     int model2d;
@@ -177,6 +197,7 @@ struct DcArgs {
     unsigned *status;
 };
 cudaError_t launch_dc(const DcArgs &a, cudaStream_t st);
+cudaError_t launch_dc_vjp(const DcArgs &a, const cf *Kbar, cf *out, cf *ybar, cudaStream_t st);
 cudaError_t launch_rel_finalize(const double *partial, int M, int per_m, float tol, float *rel,
                                 int *active_next, cudaStream_t st);
 cudaError_t launch_fill(cf *p, long long n, cf v, cudaStream_t st);

@@ -49,9 +49,11 @@ __device__ __forceinline__ bool frozen(const Group &g, int mat, const int *activ
 }
 
 // Orthogonalise columns x and y (length len) in place; returns 1 if rotated.
-__device__ __forceinline__ int rotate_pair(cf *x, cf *y, int len, float tol, int lane) {
+// The rotation is chosen from the first dlen entries and applied to all len
+// (dlen < len: Jacobi on [B; I], which accumulates the rotations below B).
+__device__ __forceinline__ int rotate_pair(cf *x, cf *y, int len, int dlen, float tol, int lane) {
     float a = 0.f, b = 0.f, cr = 0.f, ci = 0.f;
-    for (int e = lane; e < len; e += 32) {
+    for (int e = lane; e < dlen; e += 32) {
         const cf xv = x[e], yv = y[e];
         a = fmaf(xv.x, xv.x, fmaf(xv.y, xv.y, a));
         b = fmaf(yv.x, yv.x, fmaf(yv.y, yv.y, b));
@@ -101,7 +103,7 @@ __device__ void copy_out(cf *dst, const cf *src, int n) {
 }
 
 // Round-robin sweep over the `cnt` columns starting at `base` (smem).
-__device__ void intra_rounds(cf *base, int cnt, int len, float tol, int *rot) {
+__device__ void intra_rounds(cf *base, int cnt, int len, int dlen, float tol, int *rot) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (cnt < 2) return;
     const int P = cnt + (cnt & 1);
@@ -110,7 +112,8 @@ __device__ void intra_rounds(cf *base, int cnt, int len, float tol, int *rot) {
         for (int i = warp; i < P / 2; i += JAC_WARPS) {
             int p, q;
             rr_pair(P, r, i, &p, &q);
-            if (p < cnt && q < cnt) mine += rotate_pair(base + (long long)p * len, base + (long long)q * len, len, tol, lane);
+            if (p < cnt && q < cnt)
+                mine += rotate_pair(base + (long long)p * len, base + (long long)q * len, len, dlen, tol, lane);
         }
         if (lane == 0 && mine) atomicAdd(rot, mine);
         __syncthreads();
@@ -118,14 +121,15 @@ __device__ void intra_rounds(cf *base, int cnt, int len, float tol, int *rot) {
 }
 
 // All cross pairs between block I (cntI columns at bI) and block J (cntJ at bJ).
-__device__ void cross_rounds(cf *bI, int cntI, cf *bJ, int cntJ, int len, float tol, int *rot) {
+__device__ void cross_rounds(cf *bI, int cntI, cf *bJ, int cntJ, int len, int dlen, float tol, int *rot) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int P = max(cntI, cntJ);
     for (int r = 0; r < P; ++r) {
         int mine = 0;
         for (int k = warp; k < P; k += JAC_WARPS) {
             const int q = (k + r) % P;
-            if (k < cntI && q < cntJ) mine += rotate_pair(bI + (long long)k * len, bJ + (long long)q * len, len, tol, lane);
+            if (k < cntI && q < cntJ)
+                mine += rotate_pair(bI + (long long)k * len, bJ + (long long)q * len, len, dlen, tol, lane);
         }
         if (lane == 0 && mine) atomicAdd(rot, mine);
         __syncthreads();
@@ -140,7 +144,7 @@ k_jacobi(GroupSet gs, int mat_begin, SvtArgs a, int cap_vecs_bytes) {
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
     if (frozen(g, mat, a.active)) return;
-    const int s = g.s, len = g.len;
+    const int s = g.s, len = g.len, dlen = g.dlen > 0 ? g.dlen : g.len;
     cf *W = a.W + g.off + (long long)mat * s * len;
     const int cap = cap_vecs_bytes / (int)(len * sizeof(cf));   // columns that fit in smem
     int sweeps = 0;
@@ -151,7 +155,7 @@ k_jacobi(GroupSet gs, int mat_begin, SvtArgs a, int cap_vecs_bytes) {
         for (sweeps = 1; sweeps <= a.max_sweeps; ++sweeps) {
             if (threadIdx.x == 0) rot = 0;
             __syncthreads();
-            intra_rounds(jsm, s, len, a.tol, &rot);
+            intra_rounds(jsm, s, len, dlen, a.tol, &rot);
             const int r = rot;
             __syncthreads();
             if (r == 0) { converged = true; break; }
@@ -168,12 +172,12 @@ k_jacobi(GroupSet gs, int mat_begin, SvtArgs a, int cap_vecs_bytes) {
                 const int cI = min(bc, s - I * bc);
                 copy_in(slotI, W + (long long)I * bc * len, cI * len);
                 __syncthreads();
-                intra_rounds(slotI, cI, len, a.tol, &rot);
+                intra_rounds(slotI, cI, len, dlen, a.tol, &rot);
                 for (int J = I + 1; J < nb; ++J) {
                     const int cJ = min(bc, s - J * bc);
                     copy_in(slotJ, W + (long long)J * bc * len, cJ * len);
                     __syncthreads();
-                    cross_rounds(slotI, cI, slotJ, cJ, len, a.tol, &rot);
+                    cross_rounds(slotI, cI, slotJ, cJ, len, dlen, a.tol, &rot);
                     copy_out(W + (long long)J * bc * len, slotJ, cJ * len);
                     __syncthreads();
                 }
@@ -191,7 +195,7 @@ k_jacobi(GroupSet gs, int mat_begin, SvtArgs a, int cap_vecs_bytes) {
     bool bad = false;
     for (int v = warp; v < s; v += JAC_WARPS) {
         float acc = 0.f;
-        for (int e = lane; e < len; e += 32) {
+        for (int e = lane; e < dlen; e += 32) {
             const cf x = W[(long long)v * len + e];
             acc = fmaf(x.x, x.x, fmaf(x.y, x.y, acc));
         }
