@@ -255,7 +255,8 @@ selr_status selr_sync_status(selr_plan *plan, selr_stream stream);
  *   tbar = -Re sum_{lambda_i > t^2} (V^H B^H Zbar V)_ii / sqrt(lambda_i).
  * The eigenpairs of G come from one-sided Jacobi on [B; I] with the plan's
  * jacobi_max_sweeps / jacobi_tol (a matrix reaching the cap is reported by
- * selr_sync_status as SELR_ERR_NO_CONVERGENCE).  Abar: [nmat][rows][cols]
+ * selr_sync_status as SELR_ERR_NO_CONVERGENCE), followed by one
+ * Newton-Schulz orthonormalisation step of the accumulated rotations.  Abar: [nmat][rows][cols]
  * device output (may not alias A or Zbar).  tbar: device float receiving
  * the threshold cotangent summed over the nmat matrices.  Shapes as for
  * selr_svt plus min(rows, cols) <= 480; the first call allocates the

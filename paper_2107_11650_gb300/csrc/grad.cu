@@ -14,9 +14,13 @@
 // divided difference is the 1 / (sigma_i^2 - sigma_j^2) term of the
 // singular-vector derivative, guarded by evaluating it in a form without
 // cancellation (k_gamma).  The eigenpairs of G come from one-sided Jacobi on
-// [B; I] (k_augment, k_jacobi with rotations chosen on B, k_split_aug):
-// V = the accumulated rotations is unitary to working precision even inside
-// clusters of small singular values, lambda_i = ||B v_i||^2.
+// [B; I] (k_augment, k_jacobi with rotations chosen on B, k_split_aug): the
+// accumulated rotations Q stay orthonormal inside clusters of small singular
+// values, where eigenvectors from inverse iteration would not.  Each FP32
+// rotation is unitary only to O(u), so after ~sweeps * s rotations Q^H Q - I
+// reaches ~1e-5; one Newton-Schulz (polar) step [BQ; Q] <- [BQ; Q](3I - Q^H Q)/2
+// squares that error away and keeps the top block equal to B Q.  Then
+// lambda_i = ||B v_i||^2.
 #include "selr_internal.cuh"
 
 #include <float.h>
@@ -298,23 +302,37 @@ cudaError_t launch_augment(int batch, int s, int len, const cf *Bt, cf *aug, cud
 }
 
 // Vt[b][q][i] = Q[i][q] (eigenvector-major, row stride s, batch stride s*s) and
-// lam[b][q] = sigma[b][q]^2: the eigenpairs of G = B^H B.
-__global__ void k_split_aug(int s, int len, const cf *aug, const float *sigma, cf *Vt, float *lam) {
+// lam[b][q] = ||(B Q)[:, q]||^2: the eigenpairs of G = B^H B.  One warp per q.
+__global__ void k_split_aug(int s, int len, const cf *aug, cf *Vt, float *lam) {
     const int b = blockIdx.y;
     const int L = len + s;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < s * s; idx += gridDim.x * blockDim.x) {
-        const int q = idx / s, i = idx - q * s;
-        Vt[(long long)b * s * s + idx] = aug[(long long)b * s * L + (long long)q * L + len + i];
-        if (i == 0) {
-            const float sg = sigma[(long long)b * s + q];
-            lam[(long long)b * s + q] = sg * sg;
-        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = blockIdx.x * nw + warp; q < s; q += gridDim.x * nw) {
+        const cf *col = aug + (long long)b * s * L + (long long)q * L;
+        float acc = 0.f;
+        for (int e = lane; e < len; e += 32) acc = fmaf(col[e].x, col[e].x, fmaf(col[e].y, col[e].y, acc));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) lam[(long long)b * s + q] = acc;
+        for (int i = lane; i < s; i += 32) Vt[(long long)b * s * s + (long long)q * s + i] = col[len + i];
     }
 }
-cudaError_t launch_split_aug(int batch, int s, int len, const cf *aug, const float *sigma, cf *Vt, float *lam,
-                             cudaStream_t st) {
+cudaError_t launch_split_aug(int batch, int s, int len, const cf *aug, cf *Vt, float *lam, cudaStream_t st) {
     if (batch <= 0) return cudaSuccess;
-    dim3 grid((unsigned)min((s * s + 255) / 256, 64), batch);
-    k_split_aug<<<grid, 256, 0, st>>>(s, len, aug, sigma, Vt, lam);
+    dim3 grid((unsigned)((s + 7) / 8), batch);
+    k_split_aug<<<grid, 256, 0, st>>>(s, len, aug, Vt, lam);
+    return cudaGetLastError();
+}
+
+// M[b] <- M[b] + v I (square s x s, row stride s, batch stride sm).
+__global__ void k_add_diag(int s, cf *M, long long sm, float v) {
+    const int b = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x)
+        M[(long long)b * sm + (long long)i * s + i].x += v;
+}
+cudaError_t launch_add_diag(int batch, int s, cf *M, long long sm, float v, cudaStream_t st) {
+    if (batch <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((s + 255) / 256), batch);
+    k_add_diag<<<grid, 256, 0, st>>>(s, M, sm, v);
     return cudaGetLastError();
 }

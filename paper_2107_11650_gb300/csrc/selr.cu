@@ -46,7 +46,7 @@ struct selr_plan {
     int prof_count;           // iterations timed by the last solve
     cudaGraphExec_t stage_graph[8];   // profiling: one graph per stage (NSTAGE <= 8)
     // reverse-mode workspaces (allocated on the first VJP call)
-    cf *gw_Z, *gw_Bbar, *gw_S1, *gw_S2, *gw_S3, *gw_S4, *gw_V, *gw_aug;
+    cf *gw_Z, *gw_Bbar, *gw_S1, *gw_S2, *gw_S3, *gw_S4, *gw_V, *gw_aug, *gw_aug2;
     float *gw_lam;
     double *gw_part;
 };
@@ -234,8 +234,8 @@ static selr_status upload(void *dst, const void *src, size_t bytes) {
 extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     if (!p) return SELR_OK;
     drop_graphs(p);
-    void *gbufs[] = {p->gw_Z, p->gw_Bbar, p->gw_S1, p->gw_S2, p->gw_S3, p->gw_S4, p->gw_V, p->gw_aug, p->gw_lam,
-                     p->gw_part};
+    void *gbufs[] = {p->gw_Z, p->gw_Bbar, p->gw_S1, p->gw_S2, p->gw_S3, p->gw_S4, p->gw_V, p->gw_aug, p->gw_aug2,
+                     p->gw_lam, p->gw_part};
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
@@ -770,7 +770,7 @@ static selr_status grad_workspace(selr_plan *p) {
     struct { void **ptr; size_t bytes; } req[] = {
         {(void **)&p->gw_Bbar, lb}, {(void **)&p->gw_S1, lb}, {(void **)&p->gw_S2, lb},
         {(void **)&p->gw_S3, lb},   {(void **)&p->gw_S4, lb}, {(void **)&p->gw_V, lb},
-        {(void **)&p->gw_aug, 2 * lb}, {(void **)&p->gw_lam, sizeof(float) * (size_t)p->vec_elems},
+        {(void **)&p->gw_aug, 2 * lb}, {(void **)&p->gw_aug2, 2 * lb}, {(void **)&p->gw_lam, sizeof(float) * (size_t)p->vec_elems},
         {(void **)&p->gw_part, sizeof(double) * 512},
         {(void **)&p->gw_Z, lb},     // last: marks the workspace as complete
     };
@@ -826,9 +826,15 @@ extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zba
     ja.tol = p->d.jacobi_tol;
     CK(launch_jacobi(ga, 0, nmat, ja, st));
     const long long sbl = (long long)n * len, ss = (long long)n * n;
-    cf *Vt = p->gw_V;
-    CK(launch_split_aug(nmat, n, len, p->gw_aug, p->sigma, Vt, p->gw_lam, st));
+    const long long La = (long long)len + n, sa = (long long)n * La;
     const cf one = mk(1.f, 0.f), zero = mk(0.f, 0.f);
+    // one polar step: Aug2^T = (1.5 I - 0.5 Q^H Q)^T Aug^T (rows of Aug^T are the columns)
+    CK(launch_cgemm(nmat, n, n, n, mk(-0.5f, 0.f), p->gw_aug + len, 3, La, sa, p->gw_aug + len, 1, La, sa, zero,
+                    p->gw_S2, n, ss, st));
+    CK(launch_add_diag(nmat, n, p->gw_S2, ss, 1.5f, st));
+    CK(launch_cgemm(nmat, n, (int)La, n, one, p->gw_S2, 1, n, ss, p->gw_aug, 0, La, sa, zero, p->gw_aug2, La, sa, st));
+    cf *Vt = p->gw_V;
+    CK(launch_split_aug(nmat, n, len, p->gw_aug2, Vt, p->gw_lam, st));
     cf *Bt = p->gw_S1;
     // C = B^H Zbar = conj(Bt) Zt^T
     CK(launch_cgemm(nmat, n, n, len, one, Bt, 3, len, sbl, p->gw_Z, 1, len, sbl, zero, p->gw_S2, n, ss, st));

@@ -179,8 +179,8 @@ cudaError_t launch_axpbypcz(long long n, float a, const cf *x, float b, const cf
                             cudaStream_t st);
 cudaError_t launch_dot_re(long long n, const cf *x, const cf *y, double *part, float *out, cudaStream_t st);
 cudaError_t launch_augment(int batch, int s, int len, const cf *Bt, cf *aug, cudaStream_t st);
-cudaError_t launch_split_aug(int batch, int s, int len, const cf *aug, const float *sigma, cf *Vt, float *lam,
-                             cudaStream_t st);
+cudaError_t launch_split_aug(int batch, int s, int len, const cf *aug, cf *Vt, float *lam, cudaStream_t st);
+cudaError_t launch_add_diag(int batch, int s, cf *M, long long sm, float v, cudaStream_t st);
 
 // dc.cu
 struct DcArgs {
