@@ -288,9 +288,53 @@ def cpu_baseline(wl, steps=1):
                       "ADMM iteration, scaled to a full iteration by that fraction"}
 
 
+def run_reference_unrolled(args):
+    """Oracle arm of the unrolled batch: FP64 forward + reverse pass of the
+    smallest instance (8 coils, 128x128), scaled to the whole batch by the
+    SVT work ratio sum_i nmat_i l_i s_i^2 / (nmat_0 l_0 s_0^2)."""
+    from oracle.unrolled import unrolled_2d_vjp
+    wls = synth.unrolled_batch()
+    n_iter = wls[0].n_iter
+
+    def work(w):
+        tot = 0
+        for nv, nmat in ((w.N, w.M), (w.M, w.N)):
+            l, s = max(nv - w.window + 1, w.J * w.window), min(nv - w.window + 1, w.J * w.window)
+            tot += nmat * l * s * s
+        return tot
+
+    w0 = min(wls, key=work)
+    inp = synth.make_inputs(w0)
+    rng = np.random.default_rng(77)
+    Xb = rng.standard_normal(inp["Y"].shape) + 1j * rng.standard_normal(inp["Y"].shape)
+    ts = np.full(n_iter, 1.0 / w0.beta)
+    taus = np.full(n_iter, w0.tau)
+    scale = sum(work(w) for w in wls) / work(w0)
+    vals = []
+    for _ in range(max(args.steps, 1)):
+        t0 = time.perf_counter()
+        unrolled_2d_vjp(inp["Y"], inp["mask"], w0, ts, taus, Xb)
+        dt = time.perf_counter() - t0
+        vals.append(len(wls) * n_iter / (dt * scale))
+    v = float(np.median(vals))
+    line = {"metric": "instance-iterations/s, forward + backward, 16 uneven unrolled SHLR instances",
+            "value": v, "unit": "instance-iters/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * len(wls) * n_iter / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "unrolled_16_uneven", "unrolled_iterations": n_iter},
+            "cpu_baseline": {"value": v, "unit": "instance-iters/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"FP64 forward + reverse pass of the {w0.J}-coil {w0.M}x{w0.N} instance, "
+                                       f"scaled by the SVT work ratio {scale:.1f} of the batch"},
+            "e2e": {"value": v, "unit": "instance-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return line
+
+
 def run_reference(args, rank, world):
     if world > 1 and rank != 0:
         return None
+    if args.config == "unrolled_16_uneven":
+        return run_reference_unrolled(args)
     wl = synth.get_config(args.config)
     for _ in range(args.warmup if args.warmup < 1 else 1):
         oracle_sample(wl, frac_mats=8)
@@ -311,6 +355,94 @@ def run_reference(args, rank, world):
                                        "scaled to one iteration by the SVT share"},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
+    print(json.dumps(line))
+    return line
+
+
+def run_unrolled(args, rank, world):
+    """Uneven batch of 16 unrolled SHLR reconstructions (10 iterations, shared
+    learnable t_k, tau_k): a step is one forward + hand-written backward pass of
+    the whole batch; value = instance-iterations per second."""
+    import torch
+    from paper_2107_11650_gb300 import api, build
+    from paper_2107_11650_gb300.unrolled import UnrolledBatch
+
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+        build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    wls = synth.unrolled_batch()
+    n_iter = wls[0].n_iter
+    inputs = [synth.make_inputs(instance_workload(w, rank)) for w in wls]
+    Yh = [torch.from_numpy(i["Y"].astype(np.complex64)) for i in inputs]
+    Ys = [y.cuda() for y in Yh]
+    masks = [torch.from_numpy(i["mask"].astype(np.uint8)).cuda() for i in inputs]
+    rng = np.random.default_rng(77 + rank)
+    Xbs = [torch.from_numpy((rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape)).astype(np.complex64))
+           .cuda() for y in Yh]
+    net = UnrolledBatch([api.Desc.from_workload(w) for w in wls], masks, n_iter)
+
+    def step(Ys_):
+        net.zero_grad(set_to_none=True)
+        Xs = net([y.requires_grad_(False) for y in Ys_])
+        loss = sum((xb.conj() * x).real.sum() for xb, x in zip(Xbs, Xs))
+        loss.backward()
+        return loss
+
+    for _ in range(max(args.warmup, 1)):
+        step(Ys)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    with torch.no_grad():
+        for _ in range(args.steps):
+            net(Ys)
+    e1.record()
+    e1.synchronize()
+    fwd_ms = max_over_ranks(e0.elapsed_time(e1), world) / args.steps
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev) if rank == 0 else None
+    if clk:
+        clk.start()
+        time.sleep(0.3)
+    e0.record()
+    for _ in range(args.steps):
+        step(Ys)
+    e1.record()
+    e1.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    clocks = clk.stop() if clk else None
+    # end to end: k-space from pinned host memory, loss and parameter gradients back to the host
+    Yp = [y.pin_memory() for y in Yh]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Yd = [y.cuda(non_blocking=True) for y in Yp]
+        loss = step(Yd)
+        out = torch.cat([loss.reshape(1), net.ts.grad, net.taus.grad]).cpu()
+    e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0), world)
+    units = len(wls) * n_iter
+    if rank != 0:
+        return None
+    line = {
+        "metric": "instance-iterations/s, forward + backward, 16 uneven unrolled SHLR instances",
+        "value": whole_job_value(world, args.steps * units, ms), "unit": "instance-iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "unrolled_16_uneven", "instances": [f"{w.J}c {w.M}x{w.N}" for w in wls],
+                   "window": wls[0].window, "unrolled_iterations": n_iter,
+                   "l2": "per-step checkpoints and lifted arrays (GBs) exceed L2; no flush"},
+        "forward_ms_per_step": fwd_ms, "backward_over_forward": (ms / args.steps - fwd_ms) / fwd_ms,
+        "roofline": None,
+        "e2e": {"value": whole_job_value(world, args.steps * units, e2e_ms), "unit": "instance-iters/s",
+                "h2d_bytes_per_step": sum(y.numel() * 8 for y in Yh), "d2h_bytes_per_step": 4 * (1 + 2 * n_iter)},
+        "clocks": clocks,
+    }
     print(json.dumps(line))
     return line
 
@@ -336,6 +468,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.config == "unrolled_16_uneven":
+        run_unrolled(args, rank, world)
         return
 
     results, jac, e2e, wl = run_gpu(args, rank, world)

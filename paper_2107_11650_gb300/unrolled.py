@@ -215,3 +215,25 @@ class UnrolledSHLR(torch.nn.Module):
 
     def forward(self, Y):
         return UnrolledFunction.apply(Y, self.ts, self.taus, self.engine)
+
+
+class UnrolledBatch(torch.nn.Module):
+    """A batch of unrolled reconstructions of uneven sizes sharing t_k and tau_k
+    (one engine and one plan per instance; the gradients of the shared
+    parameters are summed over the instances by autograd)."""
+
+    def __init__(self, descs, masks, n_iter: int):
+        super().__init__()
+        if not descs or len(descs) != len(masks):
+            raise ValueError("one mask per description is required")
+        if len({(d.beta, d.tau) for d in descs}) != 1:
+            raise ValueError("instances sharing t_k, tau_k must share beta and tau")
+        self.engines = [Unrolled2D(d, m, n_iter) for d, m in zip(descs, masks)]
+        dev = self.engines[0].dev
+        self.ts = torch.nn.Parameter(torch.full((n_iter,), 1.0 / descs[0].beta, dtype=torch.float32, device=dev))
+        self.taus = torch.nn.Parameter(torch.full((n_iter,), descs[0].tau, dtype=torch.float32, device=dev))
+
+    def forward(self, Ys):
+        if len(Ys) != len(self.engines):
+            raise ValueError("one k-space array per instance is required")
+        return [UnrolledFunction.apply(Y, self.ts, self.taus, e) for Y, e in zip(Ys, self.engines)]

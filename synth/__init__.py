@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .configs import CONFIGS, Workload, get_config  # noqa: F401
+from .configs import CONFIGS, Workload, get_config, unrolled_batch  # noqa: F401
 
 
 # ---------------------------------------------------------------- transforms

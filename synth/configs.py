@@ -62,3 +62,20 @@ CONFIGS = {
 
 def get_config(name: str) -> Workload:
     return CONFIGS[name]
+
+
+def unrolled_batch(n_inst: int = 16, n_iter: int = 10):
+    """The uneven batch of the differentiable unrolled reconstruction: n_inst
+    SHLR instances with M = N in 128..320 and 8..32 coils (every size and
+    coil count of the lists appears), window 6 (so C p = 6 J <= 192), 1D
+    random masks R = 4 with N/16 ACS lines, noise 1e-3, n_iter unrolled
+    iterations.  Deterministic: instance i takes sizes[i % 6], coils[3 i % 5]."""
+    sizes = [128, 160, 192, 240, 256, 320]
+    coils = [8, 12, 16, 24, 32]
+    out = []
+    for i in range(n_inst):
+        n = sizes[i % len(sizes)]
+        out.append(Workload(name=f"unrolled_{i:02d}", model="SHLR", J=coils[(3 * i) % len(coils)], M=n, N=n,
+                            window=6, mask="random1d", R=4.0, n_acs=n // 16, sigma_n=1e-3, seed=500 + i,
+                            beta=20.0, tau=20.0, n_iter=n_iter))
+    return out

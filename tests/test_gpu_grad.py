@@ -241,3 +241,41 @@ def test_unrolled_keeps_only_k_and_d_per_iteration():
     assert len(ckpts) == 3
     for K, D in ckpts:
         assert K.shape == Y.shape and set(D) == {"row", "col"}
+
+
+def test_unrolled_batch_sums_instance_gradients():
+    """Two instances of different sizes sharing t_k, tau_k: the gradients are
+    the sums of the instances' FP64 reference gradients."""
+    from paper_2107_11650_gb300.unrolled import UnrolledBatch
+    api = _api()
+    n = 3
+    base = get_config("shlr_4c_64").with_(window=4, mask="random1d", R=3.0, n_acs=4)
+    cases = [(base, (2, 16, 12)), (base.with_(model="SHLR", seed=7), (3, 20, 24))]
+    rng = np.random.default_rng(21)
+    ref_t = np.zeros(n)
+    ref_tau = np.zeros(n)
+    descs, masks, Ys, Xbs = [], [], [], []
+    ts = (1.0 / base.beta) * (1.0 + 0.05 * np.arange(n))
+    taus = base.tau * np.ones(n)
+    for cfg, small in cases:
+        inp = synth.make_inputs(cfg, small=small)
+        c = cfg.with_(J=small[0], M=small[1], N=small[2])
+        Xb = _crandn(rng, *inp["Y"].shape)
+        t_, tau_, _ = ounr.unrolled_2d_vjp(inp["Y"], inp["mask"], c, ts, taus, Xb)
+        ref_t += t_
+        ref_tau += tau_
+        descs.append(api.Desc.from_workload(c))
+        masks.append(torch.from_numpy(inp["mask"]).cuda())
+        Ys.append(_dev(inp["Y"]))
+        Xbs.append(_dev(Xb))
+    net = UnrolledBatch(descs, masks, n)
+    with torch.no_grad():
+        net.ts.copy_(torch.tensor(ts))
+        net.taus.copy_(torch.tensor(taus))
+    Xs = net(Ys)
+    loss = sum((xb.conj() * x).real.sum() for xb, x in zip(Xbs, Xs))
+    loss.backward()
+    g_t = net.ts.grad.cpu().numpy().astype(np.float64)
+    g_tau = net.taus.grad.cpu().numpy().astype(np.float64)
+    assert np.abs(g_t - ref_t).max() <= 2e-3 * np.abs(ref_t).max(), (g_t, ref_t)
+    assert np.abs(g_tau - ref_tau).max() <= 2e-3 * np.abs(ref_tau).max(), (g_tau, ref_tau)
