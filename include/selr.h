@@ -253,9 +253,12 @@ selr_status selr_sync_status(selr_plan *plan, selr_stream stream);
  *              (h'(lambda) at ties; evaluated as t / (s_i s_j (s_i + s_j)),
  *              s = sqrt(lambda), when both exceed t, which has no cancellation),
  *   tbar = -Re sum_{lambda_i > t^2} (V^H B^H Zbar V)_ii / sqrt(lambda_i).
- * The eigenpairs of G come from one-sided Jacobi on [B; I] with the plan's
- * jacobi_max_sweeps / jacobi_tol (a matrix reaching the cap is reported by
- * selr_sync_status as SELR_ERR_NO_CONVERGENCE), followed by one
+ * All eigenpairs of G are computed: with svd_method = SELR_SVD_EIG by the
+ * Gram / Householder-tridiagonal / inverse-iteration solver of selr_svt,
+ * re-orthogonalising across whole eigenvalue clusters; with
+ * SELR_SVD_JACOBI by one-sided Jacobi on [B; I] (the plan's
+ * jacobi_max_sweeps / jacobi_tol; a matrix reaching the cap is reported by
+ * selr_sync_status as SELR_ERR_NO_CONVERGENCE) followed by one
  * Newton-Schulz orthonormalisation step of the accumulated rotations.  Abar: [nmat][rows][cols]
  * device output (may not alias A or Zbar).  tbar: device float receiving
  * the threshold cotangent summed over the nmat matrices.  Shapes as for

@@ -46,8 +46,9 @@ struct selr_plan {
     int prof_count;           // iterations timed by the last solve
     cudaGraphExec_t stage_graph[8];   // profiling: one graph per stage (NSTAGE <= 8)
     // reverse-mode workspaces (allocated on the first VJP call)
-    cf *gw_Z, *gw_Bbar, *gw_S1, *gw_S2, *gw_S3, *gw_S4, *gw_V, *gw_aug, *gw_aug2;
-    float *gw_lam;
+    cf *gw_Z, *gw_Bbar, *gw_S1, *gw_S2, *gw_S3, *gw_S4, *gw_V, *gw_aug, *gw_aug2, *gw_Gp;
+    float *gw_lam, *gw_tri, *gw_zs;
+    int *gw_rank;
     double *gw_part;
 };
 
@@ -235,7 +236,7 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     if (!p) return SELR_OK;
     drop_graphs(p);
     void *gbufs[] = {p->gw_Z, p->gw_Bbar, p->gw_S1, p->gw_S2, p->gw_S3, p->gw_S4, p->gw_V, p->gw_aug, p->gw_aug2,
-                     p->gw_lam, p->gw_part};
+                     p->gw_Gp, p->gw_lam, p->gw_tri, p->gw_zs, p->gw_rank, p->gw_part};
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
@@ -765,17 +766,25 @@ extern "C" const char *selr_last_error_string(void) { return cudaGetErrorString(
 static selr_status grad_workspace(selr_plan *p) {
     if (p->gw_Z) return SELR_OK;
     const size_t lb = sizeof(cf) * (size_t)p->lift_elems;
-    // s x s scratch fits in s x len (s <= len); [B; I] needs s (len + s) <= 2 s len.
+    const bool jac = p->d.svd_method == SELR_SVD_JACOBI;
+    // s x s scratch fits in s x len (s <= len).  Jacobi path: [B; I] needs s (len + s) <= 2 s len.
+    // Eigensolver path: packed Gram / Householder storage, tridiagonals, and the
+    // tridiagonal-basis eigenvectors (s x s floats per matrix).
     // Buffers already allocated by an earlier, partly failed call are kept.
-    struct { void **ptr; size_t bytes; } req[] = {
-        {(void **)&p->gw_Bbar, lb}, {(void **)&p->gw_S1, lb}, {(void **)&p->gw_S2, lb},
-        {(void **)&p->gw_S3, lb},   {(void **)&p->gw_S4, lb}, {(void **)&p->gw_V, lb},
-        {(void **)&p->gw_aug, 2 * lb}, {(void **)&p->gw_aug2, 2 * lb}, {(void **)&p->gw_lam, sizeof(float) * (size_t)p->vec_elems},
-        {(void **)&p->gw_part, sizeof(double) * 512},
-        {(void **)&p->gw_Z, lb},     // last: marks the workspace as complete
+    struct { void **ptr; size_t bytes; bool need; } req[] = {
+        {(void **)&p->gw_Bbar, lb, true}, {(void **)&p->gw_S1, lb, true}, {(void **)&p->gw_S2, lb, true},
+        {(void **)&p->gw_S3, lb, true},   {(void **)&p->gw_S4, lb, true}, {(void **)&p->gw_V, lb, true},
+        {(void **)&p->gw_lam, sizeof(float) * (size_t)p->vec_elems, true},
+        {(void **)&p->gw_part, sizeof(double) * 512, true},
+        {(void **)&p->gw_aug, 2 * lb, jac}, {(void **)&p->gw_aug2, 2 * lb, jac},
+        {(void **)&p->gw_Gp, sizeof(cf) * (size_t)p->packed_elems, !jac},
+        {(void **)&p->gw_tri, 4 * sizeof(float) * (size_t)p->vec_elems, !jac},
+        {(void **)&p->gw_rank, sizeof(int) * (size_t)p->gs.total, !jac},
+        {(void **)&p->gw_zs, sizeof(float) * (size_t)p->lift_elems, !jac},
+        {(void **)&p->gw_Z, lb, true},     // last: marks the workspace as complete
     };
     for (auto &r : req) {
-        if (*r.ptr) continue;
+        if (!r.need || *r.ptr) continue;
         const selr_status s = alloc(p, r.ptr, r.bytes);
         if (s != SELR_OK) return s;
     }
@@ -810,46 +819,67 @@ extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zba
     // Bt (vector-major: row q of Bt is column q of B) and Zbar in the same layout
     CK(launch_natural_to_vm(gs, (const cf *)A, p->gw_S1, nullptr, st));
     CK(launch_natural_to_vm(gs, (const cf *)Zbar, p->gw_Z, nullptr, st));
-    // every eigenpair of G = B^H B by one-sided Jacobi on [B; I]: orthonormal V even
-    // inside clusters of small eigenvalues, which the Gamma weights still separate
-    GroupSet ga = gs;
-    ga.g[0].len = len + n;
-    ga.g[0].dlen = len;
-    CK(launch_augment(nmat, n, len, p->gw_S1, p->gw_aug, st));
-    SvtArgs ja;
-    memset(&ja, 0, sizeof(ja));
-    ja.W = p->gw_aug;
-    ja.sigma = p->sigma;
-    ja.mat_status = p->mat_status;
-    ja.status = p->status;
-    ja.max_sweeps = p->d.jacobi_max_sweeps;
-    ja.tol = p->d.jacobi_tol;
-    CK(launch_jacobi(ga, 0, nmat, ja, st));
     const long long sbl = (long long)n * len, ss = (long long)n * n;
-    const long long La = (long long)len + n, sa = (long long)n * La;
     const cf one = mk(1.f, 0.f), zero = mk(0.f, 0.f);
-    // one polar step: Aug2^T = (1.5 I - 0.5 Q^H Q)^T Aug^T (rows of Aug^T are the columns)
-    CK(launch_cgemm(nmat, n, n, n, mk(-0.5f, 0.f), p->gw_aug + len, 3, La, sa, p->gw_aug + len, 1, La, sa, zero,
-                    p->gw_S2, n, ss, st));
-    CK(launch_add_diag(nmat, n, p->gw_S2, ss, 1.5f, st));
-    CK(launch_cgemm(nmat, n, (int)La, n, one, p->gw_S2, 1, n, ss, p->gw_aug, 0, La, sa, zero, p->gw_aug2, La, sa, st));
     cf *Vt = p->gw_V;
-    CK(launch_split_aug(nmat, n, len, p->gw_aug2, Vt, p->gw_lam, st));
+    long long sv;                       // batch stride of Vt (row stride n)
+    if (p->d.svd_method == SELR_SVD_JACOBI) {
+        // every eigenpair of G = B^H B by one-sided Jacobi on [B; I]
+        GroupSet ga = gs;
+        ga.g[0].len = len + n;
+        ga.g[0].dlen = len;
+        CK(launch_augment(nmat, n, len, p->gw_S1, p->gw_aug, st));
+        SvtArgs ja;
+        memset(&ja, 0, sizeof(ja));
+        ja.W = p->gw_aug;
+        ja.sigma = p->sigma;
+        ja.mat_status = p->mat_status;
+        ja.status = p->status;
+        ja.max_sweeps = p->d.jacobi_max_sweeps;
+        ja.tol = p->d.jacobi_tol;
+        CK(launch_jacobi(ga, 0, nmat, ja, st));
+        const long long La = (long long)len + n, sa = (long long)n * La;
+        // one polar step: Aug2^T = (1.5 I - 0.5 Q^H Q)^T Aug^T (rows of Aug^T are the columns)
+        CK(launch_cgemm(nmat, n, n, n, mk(-0.5f, 0.f), p->gw_aug + len, 3, La, sa, p->gw_aug + len, 1, La, sa,
+                        zero, p->gw_S2, n, ss, st));
+        CK(launch_add_diag(nmat, n, p->gw_S2, ss, 1.5f, st));
+        CK(launch_cgemm(nmat, n, (int)La, n, one, p->gw_S2, 1, n, ss, p->gw_aug, 0, La, sa, zero, p->gw_aug2, La,
+                        sa, st));
+        CK(launch_split_aug(nmat, n, len, p->gw_aug2, Vt, p->gw_lam, st));
+        sv = ss;
+    } else {
+        // every eigenpair of G = B^H B: Gram, Householder tridiagonalisation and inverse
+        // iteration with re-orthogonalisation across the whole of each eigenvalue cluster
+        if ((long long)nmat * n * (n + 1) / 2 > p->packed_elems) return SELR_ERR_SHAPE;
+        EigArgs ea;
+        memset(&ea, 0, sizeof(ea));
+        ea.B0 = p->gw_S1;
+        ea.Gp = p->gw_Gp;
+        ea.lam = p->gw_lam;
+        ea.V = Vt;
+        ea.rank = p->gw_rank;
+        ea.tri = p->gw_tri;
+        ea.status = p->status;
+        ea.zsave = p->gw_zs;
+        CK(launch_gram(gs, 0, nmat, p->gw_S1, p->gw_Gp, nullptr, st));
+        CK(launch_heig(gs, 0, nmat, ea, st));
+        sv = sbl;
+    }
     cf *Bt = p->gw_S1;
     // C = B^H Zbar = conj(Bt) Zt^T
     CK(launch_cgemm(nmat, n, n, len, one, Bt, 3, len, sbl, p->gw_Z, 1, len, sbl, zero, p->gw_S2, n, ss, st));
     // Ct = V^H C V = conj(Vt) C Vt^T
-    CK(launch_cgemm(nmat, n, n, n, one, Vt, 3, n, ss, p->gw_S2, 0, n, ss, zero, p->gw_S3, n, ss, st));
-    CK(launch_cgemm(nmat, n, n, n, one, p->gw_S3, 0, n, ss, Vt, 1, n, ss, zero, p->gw_S4, n, ss, st));
+    CK(launch_cgemm(nmat, n, n, n, one, Vt, 3, n, sv, p->gw_S2, 0, n, ss, zero, p->gw_S3, n, ss, st));
+    CK(launch_cgemm(nmat, n, n, n, one, p->gw_S3, 0, n, ss, Vt, 1, n, sv, zero, p->gw_S4, n, ss, st));
     CK(launch_tbar(nmat, n, p->gw_lam, thresh, p->gw_S4, ss, n, tbar, st));
     CK(launch_gamma(nmat, n, p->gw_lam, thresh, p->gw_S4, ss, n, st));
     // Gbar = V (Gamma o Ct) V^H = Vt^T S4 conj(Vt); then Gbar + Gbar^H
-    CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, ss, p->gw_S4, 0, n, ss, zero, p->gw_S2, n, ss, st));
-    CK(launch_cgemm(nmat, n, n, n, one, p->gw_S2, 0, n, ss, Vt, 3, n, ss, zero, p->gw_S3, n, ss, st));
+    CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, sv, p->gw_S4, 0, n, ss, zero, p->gw_S2, n, ss, st));
+    CK(launch_cgemm(nmat, n, n, n, one, p->gw_S2, 0, n, ss, Vt, 3, n, sv, zero, p->gw_S3, n, ss, st));
     CK(launch_herm_sum(nmat, n, p->gw_S3, ss, st));
     // h(G) = V h(Lambda) V^H = Vt^T conj(h o Vt)
-    CK(launch_scale_vecs(nmat, n, p->gw_lam, thresh, Vt, p->gw_S4, ss, n, 0, st));
-    CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, ss, p->gw_S4, 3, n, ss, zero, p->gw_S2, n, ss, st));
+    CK(launch_scale_vecs(nmat, n, p->gw_lam, thresh, Vt, p->gw_S4, sv, n, 0, st));
+    CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, sv, p->gw_S4, 3, n, sv, zero, p->gw_S2, n, ss, st));
     // Bbar^T = h(G)^T Zt + (Gbar + Gbar^H)^T Bt
     CK(launch_cgemm(nmat, n, len, n, one, p->gw_S2, 1, n, ss, p->gw_Z, 0, len, sbl, zero, p->gw_Bbar, len, sbl, st));
     CK(launch_cgemm(nmat, n, len, n, one, p->gw_S3, 1, n, ss, Bt, 0, len, sbl, one, p->gw_Bbar, len, sbl, st));

@@ -156,6 +156,8 @@ struct EigArgs {
     float *tri;          // [mat][4 s]: tridiagonal d, reflector tau, complex sub-diagonal e
     const int *active;
     unsigned *status;
+    float *zsave;        // non-null: every eigenpair (not only those above t^2), with the
+                         // tridiagonal-basis vectors kept here ([mat] at g.off + mat s len)
 };
 cudaError_t eig_init_attributes();
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,

@@ -21,6 +21,12 @@
 //               for their eigenvectors (one thread per vector) with modified
 //               Gram-Schmidt inside clusters of close eigenvalues, and
 //               back-transformation with batches of reflectors.
+//               With EigArgs::zsave set, every eigenpair is computed (the
+//               reverse-mode derivative needs them all): clusters of close
+//               eigenvalues then span several chunks of vectors, so each
+//               inverse-iteration pass also orthogonalises (twice, modified
+//               Gram-Schmidt) against the members of the same cluster found in
+//               earlier chunks, whose tridiagonal-basis vectors are kept in zsave.
 //   k_apply_eig Z = sum_i g_i (B v_i) v_i^H per tile of rows of B, fused with
 //               the multiplier update D <- D + tau (A - D/beta - Z) and
 //               E = Z - D/beta (Eqs. 13-14), or writing Z.
@@ -590,12 +596,14 @@ template <int IV_CHUNK, int IV_ST>
 __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_begin, EigArgs a) {
     extern __shared__ __align__(16) unsigned char vsm[];
     __shared__ float red[4];
-    __shared__ int s_r;
+    __shared__ int s_r, s_cst, s_wend;
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
     if (is_frozen(g, mat, a.active)) return;
     const int n = g.s;
+    const bool allp = a.zsave != nullptr;
+    float *zs = allp ? a.zsave + g.off + (long long)mat * n * g.len : nullptr;
     const long long pk = (long long)n * (n + 1) / 2;
     const cf *Gglob = a.Gp + g.poff + (long long)mat * pk;     // Householder vectors
     const EvLayout LY = ev_layout(n, IV_CHUNK, IV_ST);
@@ -609,7 +617,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
     cf *Yc = (cf *)(vsm + LY.yc);
     cf *hb = (cf *)(vsm + LY.hb);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float t2 = g.thresh * g.thresh;
+    const float t2 = allp ? -FLT_MAX : g.thresh * g.thresh;
     const float *td = tri_d(a, g, mat), *ttau = td + n;
     const cf *te = (const cf *)(td + 2 * n);
     float *lam_out = a.lam + g.soff + (long long)mat * n;
@@ -658,7 +666,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
         }
         const float pivmin = FLT_MIN * fmaxf(1.f, fm2);
         red[0] = gl; red[1] = gu; red[2] = pivmin;
-        s_r = n - ((t2 >= gu) ? n : sturm_lt(dd, f2, n, t2, pivmin));
+        s_r = allp ? n : n - ((t2 >= gu) ? n : sturm_lt(dd, f2, n, t2, pivmin));
     }
     __syncthreads();
     const float gl = red[0], gu = red[1], pivmin = red[2];
@@ -701,11 +709,37 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
             zv[i * IV_ST + q] = 1.f + 0.25f * (float)(((i * 7919 + (q0 + q) * 104729) % 997) - 498) / 498.f;
         }
         __syncthreads();
+        if (allp && tid == 0) {
+            // the cluster of vector q0 may have started in an earlier chunk: its members
+            // there are [s_cst, q0), its members here [q0, q0 + s_wend)
+            int c = q0;
+            while (c > 0 && !clu[c]) --c;
+            int w = 1;
+            while (w < qc && !clu[q0 + w]) ++w;
+            s_cst = c;
+            s_wend = w;
+        }
+        __syncthreads();
         for (int it = 0; it < INV_ITERS; ++it) {
             if (tid < qc)
                 tri_solve<IV_ST>(dd, ff, n, lamv[q0 + tid], zv + tid, lu0 + tid, lu1 + tid, lu2 + tid, llm + tid,
                                  lpv + tid, FLT_EPSILON * tnorm + pivmin, it == 0);
             __syncthreads();
+            if (allp && s_cst < q0) {
+                for (int w = warp; w < s_wend; w += EIG_WARPS) {
+                    for (int pass = 0; pass < 2; ++pass) {
+                        for (int o = s_cst; o < q0; ++o) {
+                            const float *zo = zs + (long long)o * n;
+                            float dot = 0.f;
+                            for (int i = lane; i < n; i += 32) dot += zv[i * IV_ST + w] * zo[i];
+                            dot = wsum(dot);
+                            for (int i = lane; i < n; i += 32) zv[i * IV_ST + w] -= dot * zo[i];
+                            __syncwarp();
+                        }
+                    }
+                }
+                __syncthreads();
+            }
             for (int w = warp; w < qc; w += EIG_WARPS) {
                 if (!(w == 0 || clu[q0 + w])) continue;
                 int end = w + 1;
@@ -727,6 +761,12 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
                 }
             }
             __syncthreads();
+        }
+        if (allp) {
+            for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
+                const int w = idx / n, i = idx - w * n;
+                zs[(long long)(q0 + w) * n + i] = zv[i * IV_ST + w];
+            }
         }
         // back-transformation y = Q P z, reflectors applied for k = n-3 .. 0 in batches of EV_HB
         for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {

@@ -73,8 +73,9 @@ SVT_CASES = [(3, 9, 6, 0.8), (2, 6, 9, 0.8), (4, 21, 8, 0.85), (2, 57, 32, 0.93)
              (2, 113, 128, 0.97)]
 
 
+@pytest.mark.parametrize("svd", ["eig", "jacobi"])
 @pytest.mark.parametrize("nmat,rows,cols,decay", SVT_CASES)
-def test_svt_vjp_matches_oracle(nmat, rows, cols, decay):
+def test_svt_vjp_matches_oracle(nmat, rows, cols, decay, svd):
     api = _api()
     rng = np.random.default_rng(rows * 31 + cols)
     As, Zbs, ts = [], [], []
@@ -93,7 +94,7 @@ def test_svt_vjp_matches_oracle(nmat, rows, cols, decay):
     for i in range(nmat):
         ref_Ab[i], tb = osvt.svt_vjp(A[i], Zb[i], t)
         ref_tb += tb
-    plan = api.Plan(api.Desc(model="SHLR", J=12, M=256, N=256, window=16))
+    plan = api.Plan(api.Desc(model="SHLR", J=12, M=256, N=256, window=16, svd=svd))
     dA, dZb = _dev(A), _dev(Zb)
     dAb = torch.empty_like(dA)
     dtb = torch.zeros(1, dtype=torch.float32, device="cuda")
