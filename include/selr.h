@@ -253,19 +253,22 @@ selr_status selr_sync_status(selr_plan *plan, selr_stream stream);
  *              (h'(lambda) at ties; evaluated as t / (s_i s_j (s_i + s_j)),
  *              s = sqrt(lambda), when both exceed t, which has no cancellation),
  *   tbar = -Re sum_{lambda_i > t^2} (V^H B^H Zbar V)_ii / sqrt(lambda_i).
- * All eigenpairs of G are computed: with svd_method = SELR_SVD_EIG by the
- * Gram / Householder-tridiagonal / inverse-iteration solver of selr_svt,
- * re-orthogonalising across whole eigenvalue clusters; with
- * SELR_SVD_JACOBI by one-sided Jacobi on [B; I] (the plan's
- * jacobi_max_sweeps / jacobi_tol; a matrix reaching the cap is reported by
- * selr_sync_status as SELR_ERR_NO_CONVERGENCE) followed by one
- * Newton-Schulz orthonormalisation step of the accumulated rotations.  Abar: [nmat][rows][cols]
- * device output (may not alias A or Zbar).  tbar: device float receiving
- * the threshold cotangent summed over the nmat matrices.  Shapes as for
- * selr_svt plus min(rows, cols) <= 480; the first call allocates the
- * plan's reverse-mode workspace (about 11 lifted arrays). */
+ * svd_method = SELR_SVD_EIG (default): only the r pairs above t^2 are computed
+ * (the eigensolver of selr_svt); the blocks of Gamma that involve the other
+ * pairs are applied as resolvents R_q = sum_{lambda_j <= t^2} v_j v_j^H /
+ * (lambda_q - lambda_j), one tridiagonal solve per right-hand side, so the
+ * rest costs O(r s len).  SELR_SVD_JACOBI: every pair by one-sided Jacobi on
+ * [B; I] (the plan's jacobi_max_sweeps / jacobi_tol; a matrix reaching the
+ * cap is reported by selr_sync_status as SELR_ERR_NO_CONVERGENCE), one
+ * Newton-Schulz orthonormalisation step and dense s x s products.
+ * Abar: [nmat][rows][cols] device output (may not alias A or Zbar).  tbar:
+ * device float receiving the threshold cotangent summed over the nmat
+ * matrices.  Z_out: NULL, or [nmat][rows][cols] device output receiving
+ * S_t(A) itself (computed on the way).  Shapes as for selr_svt plus
+ * min(rows, cols) <= 480; the first call allocates the plan's reverse-mode
+ * workspace (about 16 lifted arrays). */
 selr_status selr_svt_vjp(selr_plan *plan, const void *A, const void *Zbar, int32_t nmat, int32_t rows,
-                         int32_t cols, float thresh, void *Abar, float *tbar, selr_stream stream);
+                         int32_t cols, float thresh, void *Abar, float *tbar, void *Z_out, selr_stream stream);
 
 /* VJP of the X-update of Eq. 15 / S7 as computed by selr_dc:
  * K = (lambda U Y + beta S) / den, den = lambda U + beta (d_a + d_b), S the

@@ -57,7 +57,7 @@ SIGNATURES = {
     "selr_status_string": (ctypes.c_char_p, [c_int32]),
     "selr_last_error_string": (ctypes.c_char_p, []),
     "selr_svt_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p,
-                               c_void_p, c_void_p]),
+                               c_void_p, c_void_p, c_void_p]),
     "selr_dc_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "selr_axpby": (c_int32, [ctypes.c_int64, c_float, c_void_p, c_float, c_void_p, c_float, c_void_p, c_void_p,
                              c_void_p]),

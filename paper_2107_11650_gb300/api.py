@@ -202,15 +202,18 @@ def selr_sync_status(plan: Plan, stream=None) -> int:
 
 
 # ------------------------------------------------------------- reverse mode
-def selr_svt_vjp(plan: Plan, A, Zbar, thresh: float, Abar, tbar, stream=None):
-    """Abar <- VJP of S_t at A for cotangent Zbar; tbar (device float32[1]) <- dL/dt."""
+def selr_svt_vjp(plan: Plan, A, Zbar, thresh: float, Abar, tbar, Z_out=None, stream=None):
+    """Abar <- VJP of S_t at A for cotangent Zbar; tbar (device float32[1]) <- dL/dt;
+    Z_out (optional) <- S_t(A)."""
     if A.dim() != 3:
         raise ValueError("A must be [nmat][rows][cols]")
     nmat, rows, cols = A.shape
     n = A.numel()
     check(plan.lib.selr_svt_vjp(plan.handle, _ptr(A, torch.complex64, "A"), _ptr(Zbar, torch.complex64, "Zbar", n),
                                 nmat, rows, cols, float(thresh), _ptr(Abar, torch.complex64, "Abar", n),
-                                _ptr(tbar, torch.float32, "tbar", 1), _stream(stream)), "selr_svt_vjp")
+                                _ptr(tbar, torch.float32, "tbar", 1),
+                                _ptr(Z_out, torch.complex64, "Z_out", n, allow_none=True), _stream(stream)),
+          "selr_svt_vjp")
 
 
 def selr_dc_vjp(plan: Plan, mask, Kbar, adj_out, Ybar=None, stream=None):

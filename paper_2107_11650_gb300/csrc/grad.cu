@@ -336,3 +336,283 @@ cudaError_t launch_add_diag(int batch, int s, cf *M, long long sm, float v, cuda
     k_add_diag<<<grid, 256, 0, st>>>(s, M, sm, v);
     return cudaGetLastError();
 }
+
+// ------------------------------------------------------- low-rank reverse mode
+// With r = #{lambda > t^2} pairs (v_q, lambda_q) of G = B^H B, sigma_q = sqrt(lambda_q),
+// h_q = 1 - t / sigma_q, u_q = B v_q, g_q = Zbar v_q and C = B^H Zbar, the blocks of
+// Gamma o (V^H C V) that involve eigenvectors below the threshold reduce to the
+// resolvents R_q = sum_{lambda_j <= t^2} v_j v_j^H / (lambda_q - lambda_j):
+//     y_q = R_q C^H v_q = R_q Zbar^H u_q,     z_q = R_q C v_q = R_q B^H g_q,
+//     Gbar = V1 (Gamma11 o C11) V1^H + sum_q h_q (v_q y_q^H + z_q v_q^H),
+//     C11_pq = u_p^H g_q,  Gamma11_pq = t / (s_p s_q (s_p + s_q)),
+// so with M2 = Gamma11 o (C11 + C11^H) and x_q = h_q (y_q + z_q):
+//     Bbar = Zbar h(G) + B (Gbar + Gbar^H)
+//          = sum_q [h_q g_q + sum_p u_p M2_pq + B x_q] v_q^H + sum_q u_q x_q^H,
+//     S_t(B) = sum_q h_q u_q v_q^H,   tbar = -Re sum_q C11_qq / sigma_q.
+// Everything is O(r s len) besides the eigensolver and the 2 r resolvent solves
+// (k_resolvent).  Per-matrix slots: vm-sized (s len) at g.off + mat s len for U, Gv
+// (r x len), V, X (r x s), M2 (r x r), Ab (r x len); 2 s len for W, Y (2 r x s).
+#define LR_QB 8
+#define LR_THREADS 256
+
+__device__ __forceinline__ float lr_wsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(LR_THREADS) k_lr_front(GroupSet gs, const cf *Bt, const cf *Zt, const cf *V,
+                                                         const int *rank, cf *U, cf *Gv, cf *W) {
+    extern __shared__ __align__(16) cf lsm[];
+    int mat;
+    const int gi = find_group(gs, blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    const int n = g.s, len = g.len, r = rank[g.moff + mat];
+    const long long base = g.off + (long long)mat * n * len;
+    cf *vq = lsm, *us = lsm + LR_QB * n, *gq = us + LR_QB * len;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = LR_THREADS / 32;
+    for (int q0 = 0; q0 < r; q0 += LR_QB) {
+        const int qc = min(LR_QB, r - q0);
+        for (int idx = tid; idx < LR_QB * n; idx += LR_THREADS) {
+            const int qq = idx / n, i = idx - qq * n;
+            vq[idx] = qq < qc ? V[base + (long long)(q0 + qq) * n + i] : mk(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int e = tid; e < len; e += LR_THREADS) {
+            float ur[LR_QB], ui[LR_QB], gr[LR_QB], gi_[LR_QB];
+#pragma unroll
+            for (int qq = 0; qq < LR_QB; ++qq) ur[qq] = ui[qq] = gr[qq] = gi_[qq] = 0.f;
+            for (int i = 0; i < n; ++i) {
+                const cf b = Bt[base + (long long)i * len + e], z = Zt[base + (long long)i * len + e];
+#pragma unroll
+                for (int qq = 0; qq < LR_QB; ++qq) {
+                    const cf v = vq[qq * n + i];
+                    ur[qq] = fmaf(b.x, v.x, fmaf(-b.y, v.y, ur[qq]));
+                    ui[qq] = fmaf(b.x, v.y, fmaf(b.y, v.x, ui[qq]));
+                    gr[qq] = fmaf(z.x, v.x, fmaf(-z.y, v.y, gr[qq]));
+                    gi_[qq] = fmaf(z.x, v.y, fmaf(z.y, v.x, gi_[qq]));
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < LR_QB; ++qq) {
+                us[qq * len + e] = mk(ur[qq], ui[qq]);
+                gq[qq * len + e] = mk(gr[qq], gi_[qq]);
+                if (qq < qc) {
+                    U[base + (long long)(q0 + qq) * len + e] = mk(ur[qq], ui[qq]);
+                    Gv[base + (long long)(q0 + qq) * len + e] = mk(gr[qq], gi_[qq]);
+                }
+            }
+        }
+        __syncthreads();
+        // w1_q[i] = sum_e conj(Zbar[e][i]) u_q[e],  w2_q[i] = sum_e conj(B[e][i]) g_q[e]
+        for (int i = warp; i < n; i += nw) {
+            float a1r[LR_QB], a1i[LR_QB], a2r[LR_QB], a2i[LR_QB];
+#pragma unroll
+            for (int qq = 0; qq < LR_QB; ++qq) a1r[qq] = a1i[qq] = a2r[qq] = a2i[qq] = 0.f;
+            for (int e = lane; e < len; e += 32) {
+                const cf z = Zt[base + (long long)i * len + e], b = Bt[base + (long long)i * len + e];
+#pragma unroll
+                for (int qq = 0; qq < LR_QB; ++qq) {
+                    const cf u = us[qq * len + e], gg = gq[qq * len + e];
+                    a1r[qq] = fmaf(z.x, u.x, fmaf(z.y, u.y, a1r[qq]));
+                    a1i[qq] = fmaf(z.x, u.y, fmaf(-z.y, u.x, a1i[qq]));
+                    a2r[qq] = fmaf(b.x, gg.x, fmaf(b.y, gg.y, a2r[qq]));
+                    a2i[qq] = fmaf(b.x, gg.y, fmaf(-b.y, gg.x, a2i[qq]));
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < LR_QB; ++qq) {
+                const float s1r = lr_wsum(a1r[qq]), s1i = lr_wsum(a1i[qq]);
+                const float s2r = lr_wsum(a2r[qq]), s2i = lr_wsum(a2i[qq]);
+                if (lane == 0 && qq < qc) {
+                    W[2 * base + (long long)(2 * (q0 + qq)) * n + i] = mk(s1r, s1i);
+                    W[2 * base + (long long)(2 * (q0 + qq) + 1) * n + i] = mk(s2r, s2i);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// C11 = U^H Gv (r x r), M2 = Gamma11 o (C11 + C11^H), tpart[mat] = -Re sum_q C11_qq / sigma_q.
+__global__ void __launch_bounds__(LR_THREADS) k_lr_mid(GroupSet gs, const cf *U, const cf *Gv, const float *lam,
+                                                       const int *rank, float t, cf *C11, cf *M2, double *tpart) {
+    int mat;
+    const int gi = find_group(gs, blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    const int n = g.s, len = g.len, r = rank[g.moff + mat];
+    const long long base = g.off + (long long)mat * n * len;
+    const float *lm = lam + g.soff + (long long)mat * n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = LR_THREADS / 32;
+    for (int pq = warp; pq < r * r; pq += nw) {
+        const int p = pq / r, q = pq - p * r;
+        float cr = 0.f, ci = 0.f;
+        for (int e = lane; e < len; e += 32) {
+            const cf u = U[base + (long long)p * len + e], gg = Gv[base + (long long)q * len + e];
+            cr = fmaf(u.x, gg.x, fmaf(u.y, gg.y, cr));
+            ci = fmaf(u.x, gg.y, fmaf(-u.y, gg.x, ci));
+        }
+        cr = lr_wsum(cr);
+        ci = lr_wsum(ci);
+        if (lane == 0) C11[base + pq] = mk(cr, ci);
+    }
+    __syncthreads();
+    for (int pq = tid; pq < r * r; pq += LR_THREADS) {
+        const int p = pq / r, q = pq - p * r;
+        const float sp = sqrtf(fmaxf(lm[p], 0.f)), sq = sqrtf(fmaxf(lm[q], 0.f));
+        const float gam = t / (sp * sq * (sp + sq));
+        const cf a = C11[base + pq], b = C11[base + (long long)q * r + p];
+        M2[base + pq] = mk(gam * (a.x + b.x), gam * (a.y - b.y));
+    }
+    if (tid == 0) {
+        double acc = 0.0;
+        for (int q = 0; q < r; ++q) acc -= (double)C11[base + (long long)q * r + q].x / sqrt((double)fmaxf(lm[q], 0.f));
+        tpart[g.moff + mat] = acc;
+    }
+}
+
+// x_q = h_q (y_q + z_q);  a_q = h_q g_q + sum_p u_p M2_pq + B x_q.
+__global__ void __launch_bounds__(LR_THREADS) k_lr_back(GroupSet gs, const cf *Bt, const cf *U, const cf *Gv,
+                                                        const cf *M2, const cf *Yv, const float *lam, const int *rank,
+                                                        float t, cf *X, cf *Ab) {
+    extern __shared__ __align__(16) cf lsm[];
+    int mat;
+    const int gi = find_group(gs, blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    const int n = g.s, len = g.len, r = rank[g.moff + mat];
+    const long long base = g.off + (long long)mat * n * len;
+    const float *lm = lam + g.soff + (long long)mat * n;
+    cf *xs = lsm;                       // LR_QB x n
+    const int tid = threadIdx.x;
+    for (int q0 = 0; q0 < r; q0 += LR_QB) {
+        const int qc = min(LR_QB, r - q0);
+        for (int idx = tid; idx < LR_QB * n; idx += LR_THREADS) {
+            const int qq = idx / n, i = idx - qq * n;
+            cf x = mk(0.f, 0.f);
+            if (qq < qc) {
+                const int q = q0 + qq;
+                const float sg = sqrtf(fmaxf(lm[q], 0.f));
+                const float h = sg > t ? 1.f - t / sg : 0.f;
+                const cf y = Yv[2 * base + (long long)(2 * q) * n + i], z = Yv[2 * base + (long long)(2 * q + 1) * n + i];
+                x = mk(h * (y.x + z.x), h * (y.y + z.y));
+                X[base + (long long)q * n + i] = x;
+            }
+            xs[idx] = x;
+        }
+        __syncthreads();
+        for (int e = tid; e < len; e += LR_THREADS) {
+            float ar[LR_QB], ai[LR_QB];
+#pragma unroll
+            for (int qq = 0; qq < LR_QB; ++qq) ar[qq] = ai[qq] = 0.f;
+            for (int i = 0; i < n; ++i) {
+                const cf b = Bt[base + (long long)i * len + e];
+#pragma unroll
+                for (int qq = 0; qq < LR_QB; ++qq) {
+                    const cf x = xs[qq * n + i];
+                    ar[qq] = fmaf(b.x, x.x, fmaf(-b.y, x.y, ar[qq]));
+                    ai[qq] = fmaf(b.x, x.y, fmaf(b.y, x.x, ai[qq]));
+                }
+            }
+            for (int p = 0; p < r; ++p) {
+                const cf u = U[base + (long long)p * len + e];
+#pragma unroll
+                for (int qq = 0; qq < LR_QB; ++qq) {
+                    if (qq < qc) {
+                        const cf m = M2[base + (long long)p * r + q0 + qq];
+                        ar[qq] = fmaf(u.x, m.x, fmaf(-u.y, m.y, ar[qq]));
+                        ai[qq] = fmaf(u.x, m.y, fmaf(u.y, m.x, ai[qq]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < LR_QB; ++qq) {
+                if (qq < qc) {
+                    const int q = q0 + qq;
+                    const float sg = sqrtf(fmaxf(lm[q], 0.f));
+                    const float h = sg > t ? 1.f - t / sg : 0.f;
+                    const cf gg = Gv[base + (long long)q * len + e];
+                    Ab[base + (long long)q * len + e] = mk(ar[qq] + h * gg.x, ai[qq] + h * gg.y);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Bbar^T[v][e] = sum_q a_q[e] conj(v_q[v]) + u_q[e] conj(x_q[v]);
+// Zt[v][e] (if non-null) = sum_q h_q u_q[e] conj(v_q[v]).  Block: 32 e x 8 v.
+__global__ void __launch_bounds__(LR_THREADS) k_lr_out(GroupSet gs, const cf *U, const cf *Ab, const cf *V,
+                                                       const cf *X, const float *lam, const int *rank, float t,
+                                                       cf *Bbart, cf *Zt) {
+    int mat;
+    const int gi = find_group(gs, blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    const int n = g.s, len = g.len, r = rank[g.moff + mat];
+    const long long base = g.off + (long long)mat * n * len;
+    const float *lm = lam + g.soff + (long long)mat * n;
+    const int e = blockIdx.y * 32 + (threadIdx.x & 31);
+    const int v = blockIdx.z * 8 + (threadIdx.x >> 5);
+    if (e >= len || v >= n) return;
+    float br = 0.f, bi = 0.f, zr = 0.f, zi = 0.f;
+    for (int q = 0; q < r; ++q) {
+        const cf a = Ab[base + (long long)q * len + e], u = U[base + (long long)q * len + e];
+        const cf vv = V[base + (long long)q * n + v], x = X[base + (long long)q * n + v];
+        // a conj(vv) + u conj(x)
+        br = fmaf(a.x, vv.x, fmaf(a.y, vv.y, br));
+        bi = fmaf(a.y, vv.x, fmaf(-a.x, vv.y, bi));
+        br = fmaf(u.x, x.x, fmaf(u.y, x.y, br));
+        bi = fmaf(u.y, x.x, fmaf(-u.x, x.y, bi));
+        if (Zt) {
+            const float sg = sqrtf(fmaxf(lm[q], 0.f));
+            const float h = sg > t ? 1.f - t / sg : 0.f;
+            zr = fmaf(h, u.x * vv.x + u.y * vv.y, zr);
+            zi = fmaf(h, u.y * vv.x - u.x * vv.y, zi);
+        }
+    }
+    Bbart[base + (long long)v * len + e] = mk(br, bi);
+    if (Zt) Zt[base + (long long)v * len + e] = mk(zr, zi);
+}
+
+// *out = sum of nm per-matrix partials in index order (single block).
+__global__ void k_sum_partials(int nm, const double *part, float *out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) acc += part[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (float)red[0];
+}
+
+static bool g_lr_attr = false;
+
+cudaError_t launch_lowrank_vjp(const GroupSet &gs, int nmat, const cf *Bt, const cf *Zt, const cf *V, const float *lam,
+                               const int *rank, float t, const LrBuffers &b, float *tbar, cf *Bbart, cf *Zout_t,
+                               const EigArgs &ea, cudaStream_t st) {
+    if (nmat <= 0) return cudaSuccess;
+    int nmax = 0, lmax = 0;
+    for (int k = 0; k < gs.n; ++k) { nmax = max(nmax, gs.g[k].s); lmax = max(lmax, gs.g[k].len); }
+    const size_t sm_front = sizeof(cf) * LR_QB * ((size_t)nmax + 2 * lmax);
+    const size_t sm_back = sizeof(cf) * LR_QB * (size_t)nmax;
+    cudaError_t e = cudaSuccess;
+    if (!g_lr_attr) {
+        e = cudaFuncSetAttribute(k_lr_front, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return e;
+        g_lr_attr = true;
+    }
+    k_lr_front<<<nmat, LR_THREADS, sm_front, st>>>(gs, Bt, Zt, V, rank, b.U, b.Gv, b.W);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_lr_mid<<<nmat, LR_THREADS, 0, st>>>(gs, b.U, b.Gv, lam, rank, t, b.C11, b.M2, b.tpart);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_resolvent(gs, nmat, ea, b.W, b.Y, st)) != cudaSuccess) return e;
+    k_lr_back<<<nmat, LR_THREADS, sm_back, st>>>(gs, Bt, b.U, b.Gv, b.M2, b.Y, lam, rank, t, b.X, b.Ab);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 grid(nmat, (lmax + 31) / 32, (nmax + 7) / 8);
+    k_lr_out<<<grid, LR_THREADS, 0, st>>>(gs, b.U, b.Ab, V, b.X, lam, rank, t, Bbart, Zout_t);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_sum_partials<<<1, 256, 0, st>>>(nmat, b.tpart, tbar);
+    return cudaGetLastError();
+}

@@ -47,8 +47,10 @@ struct selr_plan {
     cudaGraphExec_t stage_graph[8];   // profiling: one graph per stage (NSTAGE <= 8)
     // reverse-mode workspaces (allocated on the first VJP call)
     cf *gw_Z, *gw_Bbar, *gw_S1, *gw_S2, *gw_S3, *gw_S4, *gw_V, *gw_aug, *gw_aug2, *gw_Gp;
+    cf *gw_U, *gw_Gv, *gw_W, *gw_Yv, *gw_C11, *gw_M2, *gw_X, *gw_Ab, *gw_Zo;
     float *gw_lam, *gw_tri, *gw_zs;
     int *gw_rank;
+    double *gw_tpart;
     double *gw_part;
 };
 
@@ -236,7 +238,8 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     if (!p) return SELR_OK;
     drop_graphs(p);
     void *gbufs[] = {p->gw_Z, p->gw_Bbar, p->gw_S1, p->gw_S2, p->gw_S3, p->gw_S4, p->gw_V, p->gw_aug, p->gw_aug2,
-                     p->gw_Gp, p->gw_lam, p->gw_tri, p->gw_zs, p->gw_rank, p->gw_part};
+                     p->gw_Gp, p->gw_U, p->gw_Gv, p->gw_W, p->gw_Yv, p->gw_C11, p->gw_M2, p->gw_X, p->gw_Ab,
+                     p->gw_Zo, p->gw_lam, p->gw_tri, p->gw_zs, p->gw_rank, p->gw_tpart, p->gw_part};
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
@@ -772,15 +775,22 @@ static selr_status grad_workspace(selr_plan *p) {
     // tridiagonal-basis eigenvectors (s x s floats per matrix).
     // Buffers already allocated by an earlier, partly failed call are kept.
     struct { void **ptr; size_t bytes; bool need; } req[] = {
-        {(void **)&p->gw_Bbar, lb, true}, {(void **)&p->gw_S1, lb, true}, {(void **)&p->gw_S2, lb, true},
-        {(void **)&p->gw_S3, lb, true},   {(void **)&p->gw_S4, lb, true}, {(void **)&p->gw_V, lb, true},
+        {(void **)&p->gw_Bbar, lb, true}, {(void **)&p->gw_S1, lb, true}, {(void **)&p->gw_V, lb, true},
+        {(void **)&p->gw_Zo, lb, true},
         {(void **)&p->gw_lam, sizeof(float) * (size_t)p->vec_elems, true},
         {(void **)&p->gw_part, sizeof(double) * 512, true},
+        // Jacobi path: batched s x s products and [B; I]
+        {(void **)&p->gw_S2, lb, jac}, {(void **)&p->gw_S3, lb, jac}, {(void **)&p->gw_S4, lb, jac},
         {(void **)&p->gw_aug, 2 * lb, jac}, {(void **)&p->gw_aug2, 2 * lb, jac},
+        // eigensolver path: eigen data and the low-rank slots
         {(void **)&p->gw_Gp, sizeof(cf) * (size_t)p->packed_elems, !jac},
         {(void **)&p->gw_tri, 4 * sizeof(float) * (size_t)p->vec_elems, !jac},
         {(void **)&p->gw_rank, sizeof(int) * (size_t)p->gs.total, !jac},
         {(void **)&p->gw_zs, sizeof(float) * (size_t)p->lift_elems, !jac},
+        {(void **)&p->gw_U, lb, !jac}, {(void **)&p->gw_Gv, lb, !jac}, {(void **)&p->gw_W, 2 * lb, !jac},
+        {(void **)&p->gw_Yv, 2 * lb, !jac}, {(void **)&p->gw_C11, lb, !jac}, {(void **)&p->gw_M2, lb, !jac},
+        {(void **)&p->gw_X, lb, !jac}, {(void **)&p->gw_Ab, lb, !jac},
+        {(void **)&p->gw_tpart, sizeof(double) * (size_t)p->gs.total, !jac},
         {(void **)&p->gw_Z, lb, true},     // last: marks the workspace as complete
     };
     for (auto &r : req) {
@@ -792,7 +802,8 @@ static selr_status grad_workspace(selr_plan *p) {
 }
 
 extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zbar, int32_t nmat, int32_t rows,
-                                    int32_t cols, float thresh, void *Abar, float *tbar, selr_stream stream) {
+                                    int32_t cols, float thresh, void *Abar, float *tbar, void *Z_out,
+                                    selr_stream stream) {
     if (!p || !A || !Zbar || !Abar || !tbar || nmat < 1 || rows < 1 || cols < 1 || !(thresh >= 0.f) ||
         !isfinite(thresh))
         return SELR_ERR_INVALID_ARG;
@@ -822,8 +833,8 @@ extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zba
     const long long sbl = (long long)n * len, ss = (long long)n * n;
     const cf one = mk(1.f, 0.f), zero = mk(0.f, 0.f);
     cf *Vt = p->gw_V;
-    long long sv;                       // batch stride of Vt (row stride n)
     if (p->d.svd_method == SELR_SVD_JACOBI) {
+        const long long sv = ss;        // batch stride of the compact Vt (row stride n)
         // every eigenpair of G = B^H B by one-sided Jacobi on [B; I]
         GroupSet ga = gs;
         ga.g[0].len = len + n;
@@ -846,10 +857,34 @@ extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zba
         CK(launch_cgemm(nmat, n, (int)La, n, one, p->gw_S2, 1, n, ss, p->gw_aug, 0, La, sa, zero, p->gw_aug2, La,
                         sa, st));
         CK(launch_split_aug(nmat, n, len, p->gw_aug2, Vt, p->gw_lam, st));
-        sv = ss;
+        cf *Bt = p->gw_S1;
+        // C = B^H Zbar = conj(Bt) Zt^T
+        CK(launch_cgemm(nmat, n, n, len, one, Bt, 3, len, sbl, p->gw_Z, 1, len, sbl, zero, p->gw_S2, n, ss, st));
+        // Ct = V^H C V = conj(Vt) C Vt^T
+        CK(launch_cgemm(nmat, n, n, n, one, Vt, 3, n, sv, p->gw_S2, 0, n, ss, zero, p->gw_S3, n, ss, st));
+        CK(launch_cgemm(nmat, n, n, n, one, p->gw_S3, 0, n, ss, Vt, 1, n, sv, zero, p->gw_S4, n, ss, st));
+        CK(launch_tbar(nmat, n, p->gw_lam, thresh, p->gw_S4, ss, n, tbar, st));
+        CK(launch_gamma(nmat, n, p->gw_lam, thresh, p->gw_S4, ss, n, st));
+        // Gbar = V (Gamma o Ct) V^H = Vt^T S4 conj(Vt); then Gbar + Gbar^H
+        CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, sv, p->gw_S4, 0, n, ss, zero, p->gw_S2, n, ss, st));
+        CK(launch_cgemm(nmat, n, n, n, one, p->gw_S2, 0, n, ss, Vt, 3, n, sv, zero, p->gw_S3, n, ss, st));
+        CK(launch_herm_sum(nmat, n, p->gw_S3, ss, st));
+        // h(G) = V h(Lambda) V^H = Vt^T conj(h o Vt)
+        CK(launch_scale_vecs(nmat, n, p->gw_lam, thresh, Vt, p->gw_S4, sv, n, 0, st));
+        CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, sv, p->gw_S4, 3, n, sv, zero, p->gw_S2, n, ss, st));
+        // Bbar^T = h(G)^T Zt + (Gbar + Gbar^H)^T Bt
+        CK(launch_cgemm(nmat, n, len, n, one, p->gw_S2, 1, n, ss, p->gw_Z, 0, len, sbl, zero, p->gw_Bbar, len, sbl, st));
+        CK(launch_cgemm(nmat, n, len, n, one, p->gw_S3, 1, n, ss, Bt, 0, len, sbl, one, p->gw_Bbar, len, sbl, st));
+        if (Z_out) {
+            // S_t(B)^T = h(G)^T Bt
+            CK(launch_cgemm(nmat, n, len, n, one, p->gw_S2, 1, n, ss, Bt, 0, len, sbl, zero, p->gw_Zo, len, sbl, st));
+            CK(launch_vm_to_natural(gs, p->gw_Zo, (cf *)Z_out, st));
+        }
+        CK(launch_vm_to_natural(gs, p->gw_Bbar, (cf *)Abar, st));
+        return SELR_OK;
     } else {
-        // every eigenpair of G = B^H B: Gram, Householder tridiagonalisation and inverse
-        // iteration with re-orthogonalisation across the whole of each eigenvalue cluster
+        // the eigenpairs above t^2 only (as in selr_svt), with their tridiagonal-basis
+        // vectors kept for the resolvent solves; then the low-rank form of the derivative
         if ((long long)nmat * n * (n + 1) / 2 > p->packed_elems) return SELR_ERR_SHAPE;
         EigArgs ea;
         memset(&ea, 0, sizeof(ea));
@@ -863,28 +898,15 @@ extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zba
         ea.zsave = p->gw_zs;
         CK(launch_gram(gs, 0, nmat, p->gw_S1, p->gw_Gp, nullptr, st));
         CK(launch_heig(gs, 0, nmat, ea, st));
-        sv = sbl;
+        LrBuffers lb2;
+        lb2.U = p->gw_U; lb2.Gv = p->gw_Gv; lb2.W = p->gw_W; lb2.Y = p->gw_Yv;
+        lb2.C11 = p->gw_C11; lb2.M2 = p->gw_M2; lb2.X = p->gw_X; lb2.Ab = p->gw_Ab; lb2.tpart = p->gw_tpart;
+        CK(launch_lowrank_vjp(gs, nmat, p->gw_S1, p->gw_Z, Vt, p->gw_lam, p->gw_rank, thresh, lb2, tbar, p->gw_Bbar,
+                              Z_out ? p->gw_Zo : nullptr, ea, st));
+        if (Z_out) CK(launch_vm_to_natural(gs, p->gw_Zo, (cf *)Z_out, st));
+        CK(launch_vm_to_natural(gs, p->gw_Bbar, (cf *)Abar, st));
+        return SELR_OK;
     }
-    cf *Bt = p->gw_S1;
-    // C = B^H Zbar = conj(Bt) Zt^T
-    CK(launch_cgemm(nmat, n, n, len, one, Bt, 3, len, sbl, p->gw_Z, 1, len, sbl, zero, p->gw_S2, n, ss, st));
-    // Ct = V^H C V = conj(Vt) C Vt^T
-    CK(launch_cgemm(nmat, n, n, n, one, Vt, 3, n, sv, p->gw_S2, 0, n, ss, zero, p->gw_S3, n, ss, st));
-    CK(launch_cgemm(nmat, n, n, n, one, p->gw_S3, 0, n, ss, Vt, 1, n, sv, zero, p->gw_S4, n, ss, st));
-    CK(launch_tbar(nmat, n, p->gw_lam, thresh, p->gw_S4, ss, n, tbar, st));
-    CK(launch_gamma(nmat, n, p->gw_lam, thresh, p->gw_S4, ss, n, st));
-    // Gbar = V (Gamma o Ct) V^H = Vt^T S4 conj(Vt); then Gbar + Gbar^H
-    CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, sv, p->gw_S4, 0, n, ss, zero, p->gw_S2, n, ss, st));
-    CK(launch_cgemm(nmat, n, n, n, one, p->gw_S2, 0, n, ss, Vt, 3, n, sv, zero, p->gw_S3, n, ss, st));
-    CK(launch_herm_sum(nmat, n, p->gw_S3, ss, st));
-    // h(G) = V h(Lambda) V^H = Vt^T conj(h o Vt)
-    CK(launch_scale_vecs(nmat, n, p->gw_lam, thresh, Vt, p->gw_S4, sv, n, 0, st));
-    CK(launch_cgemm(nmat, n, n, n, one, Vt, 1, n, sv, p->gw_S4, 3, n, sv, zero, p->gw_S2, n, ss, st));
-    // Bbar^T = h(G)^T Zt + (Gbar + Gbar^H)^T Bt
-    CK(launch_cgemm(nmat, n, len, n, one, p->gw_S2, 1, n, ss, p->gw_Z, 0, len, sbl, zero, p->gw_Bbar, len, sbl, st));
-    CK(launch_cgemm(nmat, n, len, n, one, p->gw_S3, 1, n, ss, Bt, 0, len, sbl, one, p->gw_Bbar, len, sbl, st));
-    CK(launch_vm_to_natural(gs, p->gw_Bbar, (cf *)Abar, st));
-    return SELR_OK;
 }
 
 extern "C" selr_status selr_dc_vjp(selr_plan *p, const uint8_t *mask, const void *Kbar, void *adj_out, void *Ybar,

@@ -156,14 +156,21 @@ struct EigArgs {
     float *tri;          // [mat][4 s]: tridiagonal d, reflector tau, complex sub-diagonal e
     const int *active;
     unsigned *status;
-    float *zsave;        // non-null: every eigenpair (not only those above t^2), with the
-                         // tridiagonal-basis vectors kept here ([mat] at g.off + mat s len)
+    float *zsave;        // non-null: keep the tridiagonal-basis eigenvectors of the computed
+                         // pairs here ([mat] at g.off + mat s len, row q = pair q)
+    int allp;            // compute every eigenpair, not only those above t^2 (needs zsave)
 };
 cudaError_t eig_init_attributes();
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,
                         const int *active, cudaStream_t st);
 cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, cudaStream_t st);
 cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, const SvtArgs &a,
+                             cudaStream_t st);
+// Resolvent solves of the reverse mode: for every computed pair q of every matrix,
+// Y[2q + c] = Q P Pi (lambda_q I - T_r)^{-1} Pi P^H Q^H W[2q + c] (c = 0, 1), with
+// Pi = I - sum_k z_k z_k^T over the computed pairs (zsave).  W, Y: per matrix at
+// 2 (g.off + mat s len), 2 rank vectors of length s.
+cudaError_t launch_resolvent(const GroupSet &gs, int mat_count, const EigArgs &ea, const cf *W, cf *Y,
                              cudaStream_t st);
 
 // grad.cu
@@ -181,6 +188,13 @@ cudaError_t launch_axpbypcz(long long n, float a, const cf *x, float b, const cf
                             cudaStream_t st);
 cudaError_t launch_dot_re(long long n, const cf *x, const cf *y, double *part, float *out, cudaStream_t st);
 cudaError_t launch_augment(int batch, int s, int len, const cf *Bt, cf *aug, cudaStream_t st);
+struct LrBuffers {
+    cf *U, *Gv, *W, *Y, *C11, *M2, *X, *Ab;   // see k_lr_front in grad.cu for the slots
+    double *tpart;                           // per-matrix threshold-cotangent partials
+};
+cudaError_t launch_lowrank_vjp(const GroupSet &gs, int nmat, const cf *Bt, const cf *Zt, const cf *V, const float *lam,
+                               const int *rank, float t, const LrBuffers &b, float *tbar, cf *Bbart, cf *Zout_t,
+                               const EigArgs &ea, cudaStream_t st);
 cudaError_t launch_split_aug(int batch, int s, int len, const cf *aug, cf *Vt, float *lam, cudaStream_t st);
 cudaError_t launch_add_diag(int batch, int s, cf *M, long long sm, float v, cudaStream_t st);
 

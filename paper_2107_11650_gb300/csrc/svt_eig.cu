@@ -21,12 +21,16 @@
 //               for their eigenvectors (one thread per vector) with modified
 //               Gram-Schmidt inside clusters of close eigenvalues, and
 //               back-transformation with batches of reflectors.
-//               With EigArgs::zsave set, every eigenpair is computed (the
-//               reverse-mode derivative needs them all): clusters of close
+//               EigArgs::zsave keeps the tridiagonal-basis eigenvectors.  With
+//               EigArgs::allp every eigenpair is computed: clusters of close
 //               eigenvalues then span several chunks of vectors, so each
 //               inverse-iteration pass also orthogonalises (twice, modified
 //               Gram-Schmidt) against the members of the same cluster found in
-//               earlier chunks, whose tridiagonal-basis vectors are kept in zsave.
+//               earlier chunks, read back from zsave.
+//   k_resolvent the resolvent solves of the reverse-mode derivative (see
+//               launch_resolvent in selr_internal.cuh): P^H Q^H, projection off
+//               the computed eigenvectors, a tridiagonal solve per right-hand
+//               side, projection, Q P.
 //   k_apply_eig Z = sum_i g_i (B v_i) v_i^H per tile of rows of B, fused with
 //               the multiplier update D <- D + tau (A - D/beta - Z) and
 //               E = Z - D/beta (Eqs. 13-14), or writing Z.
@@ -560,6 +564,106 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
     }
 }
 
+// ------------------------------------------------ real tridiagonal setup
+// T = P T_r P^H with T_r real symmetric: f_k = |e_k| and phases ph_0 = 1,
+// ph_{k+1} = ph_k e_k / |e_k| (warp 0 runs a product scan).  The caller
+// synchronises before using the outputs.
+__device__ __forceinline__ void tri_real_setup(const float *td, const float *ttau, const cf *te, int n, float *dd,
+                                               float *taus, float *ff, float *f2, cf *ph, int tid, int lane,
+                                               int warp) {
+    for (int k = tid; k < n; k += EIG_THREADS) {
+        dd[k] = td[k];
+        taus[k] = ttau[k];
+        const float ae = k + 1 < n ? sqrtf(cabs2(te[k])) : 0.f;
+        ff[k] = ae;
+        f2[k] = ae * ae;
+    }
+    if (warp == 0) {
+        const int per = (n + 31) / 32, k0 = lane * per, k1 = min(n, k0 + per);
+        cf loc = mk(1.f, 0.f);
+        for (int k = k0; k < k1; ++k) {
+            const cf e = k + 1 < n ? te[k] : mk(0.f, 0.f);
+            const float ae = sqrtf(cabs2(e));
+            if (ae > 0.f) loc = cmul(loc, mk(e.x / ae, e.y / ae));
+        }
+        // exclusive product scan of the lane products
+        cf incl = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const cf up = shfl_cf(incl, max(lane - o, 0));
+            if (lane >= o) incl = cmul(up, incl);
+        }
+        cf cur = shfl_cf(incl, max(lane - 1, 0));
+        if (lane == 0) cur = mk(1.f, 0.f);
+        for (int k = k0; k < k1; ++k) {
+            ph[k] = cur;
+            const cf e = k + 1 < n ? te[k] : mk(0.f, 0.f);
+            const float ae = sqrtf(cabs2(e));
+            if (ae > 0.f) cur = cmul(cur, mk(e.x / ae, e.y / ae));
+        }
+    }
+}
+
+// Gershgorin interval [gl, gu] of T_r and the pivot floor of its Sturm counts.
+__device__ __forceinline__ void gershgorin(const float *dd, const float *ff, const float *f2, int n, float *gl_,
+                                           float *gu_, float *pivmin_) {
+    float gl = FLT_MAX, gu = -FLT_MAX, fm2 = 0.f;
+    for (int k = 0; k < n; ++k) {
+        const float r0 = (k > 0 ? ff[k - 1] : 0.f) + (k + 1 < n ? ff[k] : 0.f);
+        gl = fminf(gl, dd[k] - r0);
+        gu = fmaxf(gu, dd[k] + r0);
+        fm2 = fmaxf(fm2, f2[k]);
+    }
+    *gl_ = gl;
+    *gu_ = gu;
+    *pivmin_ = FLT_MIN * fmaxf(1.f, fm2);
+}
+
+// Apply the Householder reflectors H_k = I - tau_k v_k v_k^H (v_k: entries
+// k+1..n-1, stored below the diagonal of packed column k) to nv vectors of
+// length n in shared memory (row stride n), warp per vector.  forward = true:
+// Q^H y = H_{n-3} ... H_0 y (k ascending); false: Q y (k descending).
+// Reflectors are staged EV_HB at a time in hb (EV_HB x n).
+__device__ void apply_reflectors(cf *Yc, int nv, int n, const cf *Gglob, const float *taus, cf *hb, bool forward,
+                                 int tid, int lane, int warp) {
+    const int kmax = n - 3;
+    for (int kb0 = 0; kb0 <= kmax; kb0 += EV_HB) {
+        const int nbat = min(EV_HB, kmax - kb0 + 1);
+        for (int b = 0; b < nbat; ++b) {
+            const int k = forward ? kb0 + b : kmax - kb0 - b;
+            const int m = n - k - 1;
+            const cf *hv = Gglob + colstart(k, n) + 1;
+            for (int i = tid; i < m; i += EIG_THREADS) hb[(long long)b * n + i] = hv[i];
+        }
+        __syncthreads();
+        for (int w = warp; w < nv; w += EIG_WARPS) {
+            for (int b = 0; b < nbat; ++b) {
+                const int k = forward ? kb0 + b : kmax - kb0 - b;
+                const float tau = taus[k];
+                if (tau == 0.f) continue;
+                const int m = n - k - 1;
+                const cf *vk = hb + (long long)b * n;
+                cf *y = Yc + (long long)w * n + k + 1;
+                float sr = 0.f, si = 0.f;
+                for (int i = lane; i < m; i += 32) {
+                    const cf v = vk[i], yy = y[i];
+                    sr += v.x * yy.x + v.y * yy.y;
+                    si += v.x * yy.y - v.y * yy.x;
+                }
+                sr = wsum(sr) * tau;
+                si = wsum(si) * tau;
+                for (int i = lane; i < m; i += 32) {
+                    const cf v = vk[i];
+                    y[i].x -= v.x * sr - v.y * si;
+                    y[i].y -= v.x * si + v.y * sr;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- eigvec
 // Shared-memory layout of k_eigvec (16-byte aligned regions).
 struct EvLayout {
@@ -602,8 +706,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
     const Group &g = gs.g[gi];
     if (is_frozen(g, mat, a.active)) return;
     const int n = g.s;
-    const bool allp = a.zsave != nullptr;
-    float *zs = allp ? a.zsave + g.off + (long long)mat * n * g.len : nullptr;
+    float *zs = a.zsave ? a.zsave + g.off + (long long)mat * n * g.len : nullptr;
+    const bool allp = a.allp != 0 && zs != nullptr;
     const long long pk = (long long)n * (n + 1) / 2;
     const cf *Gglob = a.Gp + g.poff + (long long)mat * pk;     // Householder vectors
     const EvLayout LY = ev_layout(n, IV_CHUNK, IV_ST);
@@ -623,48 +727,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
     float *lam_out = a.lam + g.soff + (long long)mat * n;
     cf *V = a.V + g.off + (long long)mat * n * g.len;
     int *rank_out = a.rank + g.moff + mat;
-    // T real: f_k = |e_k|; phases ph_0 = 1, ph_{k+1} = ph_k e_k / |e_k| (warp-0 product scan)
-    for (int k = tid; k < n; k += EIG_THREADS) {
-        dd[k] = td[k];
-        taus[k] = ttau[k];
-        const float ae = k + 1 < n ? sqrtf(cabs2(te[k])) : 0.f;
-        ff[k] = ae;
-        f2[k] = ae * ae;
-    }
-    if (warp == 0) {
-        const int per = (n + 31) / 32, k0 = lane * per, k1 = min(n, k0 + per);
-        cf loc = mk(1.f, 0.f);
-        for (int k = k0; k < k1; ++k) {
-            const cf e = k + 1 < n ? te[k] : mk(0.f, 0.f);
-            const float ae = sqrtf(cabs2(e));
-            if (ae > 0.f) loc = cmul(loc, mk(e.x / ae, e.y / ae));
-        }
-        // exclusive product scan of the lane products
-        cf incl = loc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const cf up = shfl_cf(incl, max(lane - o, 0));
-            if (lane >= o) incl = cmul(up, incl);
-        }
-        cf cur = shfl_cf(incl, max(lane - 1, 0));
-        if (lane == 0) cur = mk(1.f, 0.f);
-        for (int k = k0; k < k1; ++k) {
-            ph[k] = cur;
-            const cf e = k + 1 < n ? te[k] : mk(0.f, 0.f);
-            const float ae = sqrtf(cabs2(e));
-            if (ae > 0.f) cur = cmul(cur, mk(e.x / ae, e.y / ae));
-        }
-    }
+    tri_real_setup(td, ttau, te, n, dd, taus, ff, f2, ph, tid, lane, warp);
     __syncthreads();
     if (tid == 0) {
-        float gl = FLT_MAX, gu = -FLT_MAX, fm2 = 0.f;
-        for (int k = 0; k < n; ++k) {
-            const float r0 = (k > 0 ? ff[k - 1] : 0.f) + (k + 1 < n ? ff[k] : 0.f);
-            gl = fminf(gl, dd[k] - r0);
-            gu = fmaxf(gu, dd[k] + r0);
-            fm2 = fmaxf(fm2, f2[k]);
-        }
-        const float pivmin = FLT_MIN * fmaxf(1.f, fm2);
+        float gl, gu, pivmin;
+        gershgorin(dd, ff, f2, n, &gl, &gu, &pivmin);
         red[0] = gl; red[1] = gu; red[2] = pivmin;
         s_r = allp ? n : n - ((t2 >= gu) ? n : sturm_lt(dd, f2, n, t2, pivmin));
     }
@@ -762,7 +829,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
             }
             __syncthreads();
         }
-        if (allp) {
+        if (zs) {
             for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
                 const int w = idx / n, i = idx - w * n;
                 zs[(long long)(q0 + w) * n + i] = zv[i * IV_ST + w];
@@ -815,6 +882,137 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
             const cf y = Yc[idx];
             if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(a.status, (unsigned)ST_NONFINITE);
             V[(long long)(q0 + w) * n + i] = y;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------- resolvent
+// Shared-memory layout of k_resolvent (16-byte aligned regions); QC pairs per
+// pass give 2 QC complex right-hand sides and 4 QC real solves.
+struct RsLayout {
+    size_t ph, dd, ff, f2, taus, zr, lu0, lu1, lu2, llm, lpv, wc, hb, total;
+};
+__host__ __device__ inline RsLayout rs_layout(int n, int qc) {
+    const size_t st = 4 * (size_t)qc + 1;
+    RsLayout L;
+    size_t o = 0;
+    L.ph = o; o += al16((size_t)n * 8);
+    L.dd = o; o += al16((size_t)n * 4);
+    L.ff = o; o += al16((size_t)n * 4);
+    L.f2 = o; o += al16((size_t)n * 4);
+    L.taus = o; o += al16((size_t)n * 4);
+    L.zr = o; o += al16(st * n * 4);
+    L.lu0 = o; o += al16(st * n * 4);
+    L.lu1 = o; o += al16(st * n * 4);
+    L.lu2 = o; o += al16(st * n * 4);
+    L.llm = o; o += al16(st * n * 4);
+    L.lpv = o; o += al16(st * n);
+    L.wc = o; o += al16(2 * (size_t)qc * n * 8);
+    L.hb = o; o += al16((size_t)EV_HB * n * 8);
+    L.total = o;
+    return L;
+}
+
+// Remove from each of nv complex vectors (smem, row stride n) its components
+// along the r real orthonormal vectors zs (global, row stride n); warp per vector.
+__device__ void project_off(cf *Yc, int nv, int n, const float *zs, int r, int lane, int warp) {
+    for (int w = warp; w < nv; w += EIG_WARPS) {
+        cf *y = Yc + (long long)w * n;
+        for (int k = 0; k < r; ++k) {
+            const float *z = zs + (long long)k * n;
+            float cr = 0.f, ci = 0.f;
+            for (int i = lane; i < n; i += 32) {
+                cr = fmaf(z[i], y[i].x, cr);
+                ci = fmaf(z[i], y[i].y, ci);
+            }
+            cr = wsum(cr);
+            ci = wsum(ci);
+            for (int i = lane; i < n; i += 32) {
+                y[i].x -= cr * z[i];
+                y[i].y -= ci * z[i];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int QC>
+__global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs a, const cf *W, cf *Y) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    __shared__ float red[4];
+    constexpr int ST = 4 * QC + 1;
+    int mat;
+    const int gi = find_group(gs, blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    const int n = g.s;
+    const int r = a.rank[g.moff + mat];
+    if (r == 0) return;
+    const RsLayout LY = rs_layout(n, QC);
+    cf *ph = (cf *)(rsm + LY.ph);
+    float *dd = (float *)(rsm + LY.dd), *ff = (float *)(rsm + LY.ff), *f2 = (float *)(rsm + LY.f2);
+    float *taus = (float *)(rsm + LY.taus), *zr = (float *)(rsm + LY.zr);
+    float *lu0 = (float *)(rsm + LY.lu0), *lu1 = (float *)(rsm + LY.lu1), *lu2 = (float *)(rsm + LY.lu2);
+    float *llm = (float *)(rsm + LY.llm);
+    unsigned char *lpv = rsm + LY.lpv;
+    cf *wc = (cf *)(rsm + LY.wc), *hb = (cf *)(rsm + LY.hb);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long pk = (long long)n * (n + 1) / 2;
+    const cf *Gglob = a.Gp + g.poff + (long long)mat * pk;
+    const float *td = tri_d(a, g, mat), *ttau = td + n;
+    const cf *te = (const cf *)(td + 2 * n);
+    const float *lam = a.lam + g.soff + (long long)mat * n;
+    const float *zs = a.zsave + g.off + (long long)mat * n * g.len;
+    const long long wbase = 2 * (g.off + (long long)mat * n * g.len);
+    tri_real_setup(td, ttau, te, n, dd, taus, ff, f2, ph, tid, lane, warp);
+    __syncthreads();
+    if (tid == 0) {
+        float gl, gu, pivmin;
+        gershgorin(dd, ff, f2, n, &gl, &gu, &pivmin);
+        red[0] = FLT_EPSILON * fmaxf(fabsf(gl), fabsf(gu)) + pivmin;
+    }
+    __syncthreads();
+    const float tiny = red[0];
+    for (int q0 = 0; q0 < r; q0 += QC) {
+        const int qc = min(QC, r - q0), nv = 2 * qc;
+        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) wc[idx] = W[wbase + (long long)2 * q0 * n + idx];
+        __syncthreads();
+        apply_reflectors(wc, nv, n, Gglob, taus, hb, true, tid, lane, warp);     // Q^H (ends synchronised)
+        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
+            const int i = idx % n;
+            wc[idx] = cmulc(ph[i], wc[idx]);                                      // P^H
+        }
+        __syncthreads();
+        project_off(wc, nv, n, zs, r, lane, warp);
+        __syncthreads();
+        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
+            const int w = idx / n, i = idx - w * n;
+            zr[i * ST + 2 * w] = wc[idx].x;
+            zr[i * ST + 2 * w + 1] = wc[idx].y;
+        }
+        __syncthreads();
+        if (tid < 2 * nv)       // real system tid: pair q0 + tid / 4, right-hand side (tid / 2) % 2, re / im
+            tri_solve<ST>(dd, ff, n, lam[q0 + tid / 4], zr + tid, lu0 + tid, lu1 + tid, lu2 + tid, llm + tid,
+                          lpv + tid, tiny, true);
+        __syncthreads();
+        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
+            const int w = idx / n, i = idx - w * n;
+            // (lambda I - T_r)^{-1} = -(T_r - lambda I)^{-1}
+            wc[idx] = mk(-zr[i * ST + 2 * w], -zr[i * ST + 2 * w + 1]);
+        }
+        __syncthreads();
+        project_off(wc, nv, n, zs, r, lane, warp);
+        __syncthreads();
+        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
+            const int i = idx % n;
+            wc[idx] = cmul(ph[i], wc[idx]);                                       // P
+        }
+        __syncthreads();
+        apply_reflectors(wc, nv, n, Gglob, taus, hb, false, tid, lane, warp);    // Q
+        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
+            const cf y = wc[idx];
+            if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(a.status, (unsigned)ST_NONFINITE);
+            Y[wbase + (long long)2 * q0 * n + idx] = y;
         }
         __syncthreads();
     }
@@ -942,6 +1140,8 @@ cudaError_t eig_init_attributes() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag_g, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<16, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<8, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_apply_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
 }
@@ -1009,5 +1209,20 @@ cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, c
     const size_t smem = sizeof(cf) * ((size_t)maxn * AP_ET + (size_t)AP_CH * maxn + AP_ET * AP_CH);
     dim3 grid(mat_count, (maxlen + AP_ET - 1) / AP_ET);
     k_apply_eig<<<grid, AP_THREADS, smem, st>>>(gs, mat_begin, ea, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resolvent(const GroupSet &gs, int mat_count, const EigArgs &ea, const cf *W, cf *Y,
+                             cudaStream_t st) {
+    if (mat_count <= 0) return cudaSuccess;
+    if (g_eig_smem_max == 0) return cudaErrorNotReady;
+    int nmax = 0;
+    for (int k = 0; k < gs.n; ++k) nmax = max(nmax, gs.g[k].s);
+    const int qc = nmax <= 256 ? 4 : 2;
+    size_t smem = 0;
+    for (int k = 0; k < gs.n; ++k) smem = max(smem, rs_layout(gs.g[k].s, qc).total);
+    if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
+    if (qc == 4) k_resolvent<4><<<mat_count, EIG_THREADS, smem, st>>>(gs, ea, W, Y);
+    else k_resolvent<2><<<mat_count, EIG_THREADS, smem, st>>>(gs, ea, W, Y);
     return cudaGetLastError();
 }

@@ -12,8 +12,9 @@ output is the image X = F2D* K of the last X-update.
 
 Memory: per iteration only (K_k, D_row, D_col) are kept (the multipliers
 entering iteration k and the k-space iterate it produced); the lifted
-matrices, the SVT results and E = Z - D / beta are recomputed in the reverse
-pass from them.
+matrices are recomputed in the reverse pass from them, and the SVT result Z
+comes out of the SVT derivative call itself (selr_svt_vjp), so the reverse
+pass runs one eigensolve per lifted matrix, like the forward.
 
 Reverse, per iteration k from the last (cotangents Dbar_k, Ebar_k of the
 multiplier and of E_k = Z_k - D_k / beta):
@@ -70,19 +71,26 @@ class Unrolled2D:
         return vals
 
     # ---------------------------------------------------------------- forward
-    def _z_and_d(self, K, D, t, tau):
-        """A = lift(F* K) + D / beta, Z = S_t(A), D' = D + tau (A - D/beta - Z), E = Z - D'/beta."""
-        beta = self.desc.beta
+    def _lifts(self, K, D):
+        """A = lift(F* K) + D / beta for both families."""
         out = {}
         for ax in ("row", "col"):
             x = self._empty(self.shape)
             api.selr_transform(self.plan, self.dim[ax], True, K, x)
             A = self._empty(self.lift[ax])
             api.selr_lift(self.plan, ax, x, D[ax], A)
+            out[ax] = A
+        return out
+
+    def _z_and_d(self, K, D, t, tau):
+        """A = lift(F* K) + D / beta and Z = S_t(A) for both families."""
+        A = self._lifts(K, D)
+        out = {}
+        for ax in ("row", "col"):
             Z = self._empty(self.lift[ax])
-            api.selr_axpby(Z, 1.0, A)
+            api.selr_axpby(Z, 1.0, A[ax])
             api.selr_svt(self.plan, Z, t)
-            out[ax] = (A, Z)
+            out[ax] = (A[ax], Z)
         return out
 
     def _x_update(self, Y, E):
@@ -141,21 +149,21 @@ class Unrolled2D:
         for k in range(n - 1, -1, -1):
             K, D = ckpts[k]
             if k < n - 1:
-                zs = self._z_and_d(K, D, tv[k], tauv[k])
+                A = self._lifts(K, D)
                 Kbar = self._zeros(self.shape)
                 Dprev = {}
                 for f, ax in enumerate(("row", "col")):
-                    A, Z = zs[ax]
                     shp = self.lift[ax]
                     Dp = self._empty(shp)
                     api.selr_axpby(Dp, 1.0, Dbar[ax], -1.0 / beta, Ebar[ax])
                     Zb = self._empty(shp)
                     api.selr_axpby(Zb, 1.0, Ebar[ax], -tauv[k], Dp)
-                    R = self._empty(shp)
-                    api.selr_axpby(R, 1.0, A, -1.0 / beta, D[ax], -1.0, Z)
-                    api.selr_dot_re(self.plan, Dp, R, g_tau[k, f:f + 1])
                     Ab = self._empty(shp)
-                    api.selr_svt_vjp(self.plan, A, Zb, tv[k], Ab, g_t[k, f:f + 1])
+                    Z = self._empty(shp)
+                    api.selr_svt_vjp(self.plan, A[ax], Zb, tv[k], Ab, g_t[k, f:f + 1], Z_out=Z)
+                    R = self._empty(shp)
+                    api.selr_axpby(R, 1.0, A[ax], -1.0 / beta, D[ax], -1.0, Z)
+                    api.selr_dot_re(self.plan, Dp, R, g_tau[k, f:f + 1])
                     api.selr_axpby(Ab, 1.0, Ab, tauv[k], Dp)
                     Dprev[ax] = self._empty(shp)
                     api.selr_axpby(Dprev[ax], 1.0 - tauv[k] / beta, Dp, 1.0 / beta, Ab)

@@ -97,11 +97,13 @@ def test_svt_vjp_matches_oracle(nmat, rows, cols, decay, svd):
     plan = api.Plan(api.Desc(model="SHLR", J=12, M=256, N=256, window=16, svd=svd))
     dA, dZb = _dev(A), _dev(Zb)
     dAb = torch.empty_like(dA)
+    dZ = torch.empty_like(dA)
     dtb = torch.zeros(1, dtype=torch.float32, device="cuda")
-    api.selr_svt_vjp(plan, dA, dZb, t, dAb, dtb)
+    api.selr_svt_vjp(plan, dA, dZb, t, dAb, dtb, Z_out=dZ)
     assert api.selr_sync_status(plan) == 0
     err = rel_l2(_host(dAb), ref_Ab)
     assert err <= 2e-5, err
+    assert rel_l2(_host(dZ), osvt.svt(A, t)) <= 1e-5
     tb = float(dtb.cpu())
     assert abs(tb - ref_tb) <= 5e-5 * max(1.0, abs(ref_tb)), (tb, ref_tb)
     plan.close()
