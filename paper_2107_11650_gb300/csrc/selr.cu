@@ -478,17 +478,34 @@ static EigArgs eig_args(selr_plan *p, const int *active) {
 // S_t of every matrix of `gs` in [m0, m0 + mc): B0 (and W for Jacobi) already filled.
 static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, const SvtArgs &a, int part,
                              cudaStream_t st) {
-    cudaError_t e = cudaSuccess;
-    if (p->d.svd_method == SELR_SVD_JACOBI) {
-        if (part & 2) e = launch_jacobi(gs, m0, mc, a, st);
-        if (e == cudaSuccess && (part & 4)) e = launch_svt_apply(gs, m0, mc, a, st);
-        return e;
+    // one launch sequence per lift family: kernels are sized for their own family's
+    // matrices, and families of tiny matrices go to the warp-per-matrix kernel
+    for (int k = 0; k < gs.n; ++k) {
+        const int b = m0 > gs.start[k] ? m0 : gs.start[k];
+        const int e_ = (m0 + mc) < gs.start[k + 1] ? (m0 + mc) : gs.start[k + 1];
+        if (b >= e_) continue;
+        GroupSet v;
+        memset(&v, 0, sizeof(v));
+        v.n = 1;
+        v.g[0] = gs.g[k];
+        v.start[1] = gs.g[k].nmat;
+        v.total = gs.g[k].nmat;
+        const int lb = b - gs.start[k], lc = e_ - b;
+        cudaError_t e = cudaSuccess;
+        if (svt_small_fits(gs.g[k])) {
+            if (part & 4) e = launch_svt_small(v, lb, lc, a, st);
+        } else if (p->d.svd_method == SELR_SVD_JACOBI) {
+            if (part & 2) e = launch_jacobi(v, lb, lc, a, st);
+            if (e == cudaSuccess && (part & 4)) e = launch_svt_apply(v, lb, lc, a, st);
+        } else {
+            const EigArgs ea = eig_args(p, a.active);
+            if (part & 1) e = launch_gram(v, lb, lc, p->B0, p->Gp, a.active, st);
+            if (e == cudaSuccess && (part & 2)) e = launch_heig(v, lb, lc, ea, st);
+            if (e == cudaSuccess && (part & 4)) e = launch_apply_eig(v, lb, lc, ea, a, st);
+        }
+        if (e != cudaSuccess) return e;
     }
-    const EigArgs ea = eig_args(p, a.active);
-    if (part & 1) e = launch_gram(gs, m0, mc, p->B0, p->Gp, a.active, st);
-    if (e == cudaSuccess && (part & 2)) e = launch_heig(gs, m0, mc, ea, st);
-    if (e == cudaSuccess && (part & 4)) e = launch_apply_eig(gs, m0, mc, ea, a, st);
-    return e;
+    return cudaSuccess;
 }
 
 extern "C" selr_status selr_svt(selr_plan *p, void *A, int32_t nmat, int32_t rows, int32_t cols, float thresh,

@@ -146,6 +146,10 @@ cudaError_t svt_init_attributes();
 cudaError_t launch_jacobi(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
 cudaError_t launch_svt_apply(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
 
+// svt_small.cu: warp-per-matrix Jacobi SVT for s <= 8, len <= 64 (same SvtArgs epilogue)
+bool svt_small_fits(const Group &g);
+cudaError_t launch_svt_small(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
+
 // svt_eig.cu
 struct EigArgs {
     const cf *B0;
