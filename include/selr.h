@@ -82,6 +82,16 @@ typedef enum {
     SELR_SVD_JACOBI = 1   /* one-sided Jacobi on the lifted matrix (all singular pairs)          */
 } selr_svd_method;
 
+/* Arithmetic of the Gram matrices G = B^H B that feed the eigensolver
+ * (SELR_SVD_EIG; precision option of the SVT, not in the paper).  The
+ * tensor-core modes run on tcgen05 (TF32 operands, FP32 accumulation) for
+ * families with min(rows, cols) <= 256 and fall back to FP32 otherwise. */
+typedef enum {
+    SELR_GRAM_FP32 = 0,    /* FP32 FMA (default)                                              */
+    SELR_GRAM_TF32 = 1,    /* one TF32 product per term: ~1e-3 relative error in G             */
+    SELR_GRAM_3XTF32 = 3   /* x = x_hi + x_lo split, three TF32 products: about FP32 accuracy  */
+} selr_gram_precision;
+
 /* Problem description (Sec. III; Algorithms S1 and S2). */
 typedef struct {
     int32_t model;            /* selr_model                                               */
@@ -100,13 +110,14 @@ typedef struct {
     float jacobi_tol;         /* rotate a pair while |x^H y| > tol * ||x|| ||y||          */
     int32_t exec;             /* selr_exec                                                */
     int32_t svd_method;       /* selr_svd_method                                          */
+    int32_t gram_precision;   /* selr_gram_precision (SELR_SVD_EIG path)                   */
 } selr_desc;
 
 typedef struct selr_plan selr_plan;   /* opaque; owns its device workspace */
 
 /* Fill *desc with defaults (SHLR, weight 1, beta = tau = 20, lambda = 1e4,
  * lambda2 = 2, d_init = 1, max_iter = 30, tol = -1, 30 sweeps, tol 2e-6,
- * batched, SELR_SVD_EIG). */
+ * batched, SELR_SVD_EIG, SELR_GRAM_FP32). */
 void selr_desc_default(selr_desc *desc);
 
 /* Validate *desc and allocate the plan's device workspace on the current

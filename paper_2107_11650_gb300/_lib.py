@@ -20,6 +20,7 @@ MODELS = {"SHLR": 0, "SHLR_V": 1, "SHLR_P": 2, "SHLR_VP": 3}
 AXES = {"row": 0, "col": 1, "pe": 2, "param": 3}
 EXEC = {"batched": 0, "plain": 1}
 SVD = {"eig": 0, "jacobi": 1}
+GRAM = {"fp32": 0, "tf32": 1, "3xtf32": 3}
 
 # Every function declared in include/selr.h, with its ctypes signature.
 c_void_p, c_int32, c_float, c_size_t = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_size_t
@@ -31,7 +32,7 @@ class SelrDesc(ctypes.Structure):
                 ("lambda_", c_float), ("lambda2", c_float), ("beta", c_float), ("tau", c_float),
                 ("d_init", c_float), ("max_iter", c_int32), ("tol", c_float),
                 ("jacobi_max_sweeps", c_int32), ("jacobi_tol", c_float), ("exec_", c_int32),
-                ("svd_method", c_int32)]
+                ("svd_method", c_int32), ("gram_precision", c_int32)]
 
 
 SIGNATURES = {

@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import AXES, EXEC, MODELS, SVD, SelrDesc, check
+from ._lib import AXES, EXEC, GRAM, MODELS, SVD, SelrDesc, check
 
 
 @dataclass
@@ -39,6 +39,7 @@ class Desc:
     jacobi_tol: float = 2.0e-6
     exec: str = "batched"
     svd: str = "eig"
+    gram: str = "fp32"
 
     @classmethod
     def from_workload(cls, w, **over):
@@ -58,6 +59,7 @@ class Desc:
         d.jacobi_max_sweeps, d.jacobi_tol = self.jacobi_max_sweeps, self.jacobi_tol
         d.exec_ = EXEC[self.exec]
         d.svd_method = SVD[self.svd]
+        d.gram_precision = GRAM[self.gram]
         return d
 
 

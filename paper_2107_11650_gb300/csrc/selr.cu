@@ -97,6 +97,7 @@ extern "C" void selr_desc_default(selr_desc *d) {
     d->jacobi_tol = 2.0e-6f;
     d->exec = SELR_EXEC_BATCHED;
     d->svd_method = SELR_SVD_EIG;
+    d->gram_precision = SELR_GRAM_FP32;
 }
 
 extern "C" const char *selr_status_string(selr_status s) {
@@ -166,6 +167,9 @@ static selr_status validate(const selr_desc *d) {
     if (d->weight != 0 && d->weight != 1) return SELR_ERR_INVALID_ARG;
     if (d->exec != SELR_EXEC_BATCHED && d->exec != SELR_EXEC_PLAIN) return SELR_ERR_INVALID_ARG;
     if (d->svd_method != SELR_SVD_EIG && d->svd_method != SELR_SVD_JACOBI) return SELR_ERR_INVALID_ARG;
+    if (d->gram_precision != SELR_GRAM_FP32 && d->gram_precision != SELR_GRAM_TF32 &&
+        d->gram_precision != SELR_GRAM_3XTF32)
+        return SELR_ERR_INVALID_ARG;
     const bool two_d = d->model <= SELR_SHLR_V;
     if (two_d) {
         if (d->L != 1) return SELR_ERR_SHAPE;
@@ -499,7 +503,12 @@ static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, c
             if (e == cudaSuccess && (part & 4)) e = launch_svt_apply(v, lb, lc, a, st);
         } else {
             const EigArgs ea = eig_args(p, a.active);
-            if (part & 1) e = launch_gram(v, lb, lc, p->B0, p->Gp, a.active, st);
+            if (part & 1) {
+                if (p->d.gram_precision != SELR_GRAM_FP32 && gram_tc_fits(gs.g[k]))
+                    e = launch_gram_tc(v, lb, lc, p->B0, p->Gp, a.active, (int)p->d.gram_precision, p->status, st);
+                else
+                    e = launch_gram(v, lb, lc, p->B0, p->Gp, a.active, st);
+            }
             if (e == cudaSuccess && (part & 2)) e = launch_heig(v, lb, lc, ea, st);
             if (e == cudaSuccess && (part & 4)) e = launch_apply_eig(v, lb, lc, ea, a, st);
         }
@@ -995,6 +1004,7 @@ extern "C" selr_status selr_sync_status(selr_plan *p, selr_stream stream) {
     unsigned h = 0;
     if (cudaMemcpy(&h, p->status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return SELR_ERR_CUDA;
     if (cudaMemset(p->status, 0, sizeof(unsigned)) != cudaSuccess) return SELR_ERR_CUDA;
+    if (h & ST_TIMEOUT) return SELR_ERR_TIMEOUT;
     if (h & ST_NONFINITE) return SELR_ERR_NONFINITE;
     if (h & ST_NOCONV) return SELR_ERR_NO_CONVERGENCE;
     return SELR_OK;

@@ -99,7 +99,7 @@ __device__ __forceinline__ cf lift_value(const Group &g, int mat, int r, int c) 
 }
 
 // ---------------------------------------------------------- status words
-enum { ST_NOCONV = 1, ST_NONFINITE = 2 };
+enum { ST_NOCONV = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
 
 // --------------------------------------------------------------- launchers
 // fft.cu
@@ -145,6 +145,11 @@ struct SvtArgs {
 cudaError_t svt_init_attributes();
 cudaError_t launch_jacobi(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
 cudaError_t launch_svt_apply(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
+
+// gram_tc.cu: G = B^H B on tcgen05 tensor cores, mode 1 = TF32, mode 3 = 3xTF32 (s <= 256)
+bool gram_tc_fits(const Group &g);
+cudaError_t launch_gram_tc(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,
+                           const int *active, int mode, unsigned *status, cudaStream_t st);
 
 // svt_small.cu: warp-per-matrix Jacobi SVT for s <= 8, len <= 64 (same SvtArgs epilogue)
 bool svt_small_fits(const Group &g);
