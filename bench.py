@@ -158,7 +158,8 @@ def run_gpu(args, rank, world):
     model2d = wl.model in ("SHLR", "SHLR_V")
     modes = ["batched", "plain"] if args.exec == "both" else [args.exec]
     for mode in modes:
-        plan = api.Plan(api.Desc.from_workload(wl, exec=mode, max_iter=max(args.warmup, 1), svd=args.svd))
+        plan = api.Plan(api.Desc.from_workload(wl, exec=mode, max_iter=max(args.warmup, 1), svd=args.svd,
+                                               gram=args.gram))
         nmat = sum(plan.lift_shape(a)[0] for a in (("row", "col") if model2d else ("pe", "param")))
         with torch.cuda.stream(stream):
             api.selr_solve(plan, Y, mask, X, stream=stream)           # W warm-up iterations
@@ -210,7 +211,29 @@ def run_gpu(args, rank, world):
     e2e = time_e2e(plan, Yh, mh, stream, reps=2)
     e2e_ms = max_over_ranks(1000.0 * plan.desc.max_iter / e2e["value"], world)
     e2e["value"] = whole_job_value(world, plan.desc.max_iter, e2e_ms)
+    results["accuracy"] = accuracy_vs_oracle(plan, wl, Y, mask, stream) if rank == 0 else None
     return results, jac, e2e, wl
+
+
+def accuracy_vs_oracle(plan, wl, Y, mask, stream):
+    """Relative error of the reconstruction after the stored number of iterations
+    against FP64 oracle values at seeded sample positions (tests/golden, written by
+    an oracle-only script); None if no values are stored for the workload."""
+    import torch
+    from paper_2107_11650_gb300 import api
+    path = os.path.join(ROOT, "tests", "golden", f"{wl.name}_30it.npz")
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    plan.set_iterations(int(g["n_iter"]))
+    X = torch.empty_like(Y)
+    with torch.cuda.stream(stream):
+        api.selr_solve(plan, Y, mask, X, stream=stream)
+    st = api.selr_sync_status(plan, stream)
+    xs = X.cpu().numpy().ravel()[g["idx"]].astype(np.complex128)
+    err = float(np.linalg.norm(xs - g["values"]) / np.linalg.norm(g["values"]))
+    return {"rel_err_vs_fp64": err, "iterations": int(g["n_iter"]), "status": st,
+            "reference": f"FP64 oracle values at {len(g['idx'])} seeded positions, tests/golden/{wl.name}_30it.npz"}
 
 
 def time_e2e(plan, Yh, mh, stream, reps):
@@ -457,6 +480,7 @@ def main():
     ap.add_argument("--exec", default="both", choices=["both", "batched", "plain"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--svd", default="eig", choices=["eig", "jacobi"])
+    ap.add_argument("--gram", default="fp32", choices=["fp32", "tf32", "3xtf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -489,6 +513,7 @@ def main():
         "config": {"workload": wl.name, "coils": wl.J, "size": [wl.M, wl.N], "window": wl.window,
                    "model": wl.model, "mask": f"{wl.mask} R={wl.R} acs={wl.n_acs}",
                    "matrices_per_step": b["nmat"], "exec": "batched (graph-captured)", "svd": args.svd,
+                   "gram": args.gram,
                    "l2": "per-step state (D, E, work copies: 760 MB) exceeds L2; no flush"},
         "plain": ({"value": whole_job_value(world, results["plain"]["steps"], results["plain"]["ms"]),
                    "ms_per_step": results["plain"]["ms"] / results["plain"]["steps"],
@@ -506,6 +531,7 @@ def main():
         "gpu_launches": b["launches"],
         "clocks": b["clocks"],
         "status": b["status"],
+        "accuracy": results.get("accuracy"),
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)

@@ -21,7 +21,7 @@ import synth  # noqa: E402
 from oracle import admm  # noqa: E402
 
 N_SAMPLES = 4096
-RUNS = {"shlr_12c_256": 30}
+RUNS = {"shlr_12c_256": 30, "shlrv_12c_256": 30}
 
 
 def make(name, n_iter):
