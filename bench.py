@@ -98,15 +98,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- GPU arm
-def kernel_launches_per_iteration(model2d, exec_mode, nmat, svd="eig"):
-    """Kernels libselr launches per ADMM iteration (mirrors admm_stage in selr.cu):
-    adjoint, FFTs of the adjoints, DC + reduction, hybrid FFTs, lift, SVT kernels."""
-    svt = 3 if svd == "eig" else 2          # gram + heig + apply, or jacobi + apply
+def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
+    """Kernels libselr launches per ADMM iteration (mirrors admm_stage and svd_apply in
+    selr.cu): adjoint, FFTs of the adjoints, DC + reduction, hybrid FFTs, lift, and per
+    lift family either the warp-per-matrix SVT (s <= 8, len <= 64) or Gram, tridiagonal
+    reduction, eigenvectors and the two apply kernels (eig), Jacobi and apply (jacobi)."""
+    fams = [plan.lift_shape(a) for a in (("row", "col") if model2d else ("pe", "param"))]
     fft_a = 2 if model2d else 1
+
+    def svt_kernels(r, c):
+        s, l = min(r, c), max(r, c)
+        if s <= 8 and l <= 64:
+            return 1
+        return 5 if svd == "eig" else 2
+
     if exec_mode == "batched":
-        per = 1 + fft_a + 2 + fft_a + 1 + svt
+        per = 1 + fft_a + 2 + fft_a + 1 + sum(svt_kernels(r, c) for _, r, c in fams)
     else:
-        per = nmat + fft_a + 2 + fft_a + (1 + svt) * nmat
+        nmat = sum(nm for nm, _, _ in fams)
+        per = nmat + fft_a + 2 + fft_a + sum(nm * (1 + svt_kernels(r, c)) for nm, r, c in fams)
     return per + (0 if model2d else 1)
 
 
@@ -188,7 +198,7 @@ def run_gpu(args, rank, world):
         prof = plan.profile_read()
         st2 = api.selr_sync_status(plan, stream)
         results[mode] = dict(ms=ms, steps=steps, status=max(st, st2), nmat=nmat, clocks=clocks, stages=prof,
-                             launches=steps * kernel_launches_per_iteration(model2d, mode, nmat, args.svd) + 6)
+                             launches=steps * kernel_launches_per_iteration(plan, model2d, mode, args.svd) + 6)
         plan.profile(False)
         if mode == "batched":
             results["plan"] = plan

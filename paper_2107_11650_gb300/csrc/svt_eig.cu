@@ -1019,6 +1019,91 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
 }
 
 // ----------------------------------------------------------------- apply
+// k_apply_stream: the apply for matrices with r <= AS_CH pairs above t^2 (the
+// usual case on the lifted matrices).  CTA = (matrix, tile of AS_ET rows of B);
+// phase 1: Y[e][k] = h_k sum_c B[e][c] v_k[c] (thread = element e x two k),
+// phase 2: Z[e][c] = sum_k Y[e][k] conj(v_k[c]) streamed over c with the
+// epilogue (Z out, or D and E update) fused, B re-read from L1/L2.  No large
+// per-thread arrays, so occupancy (and with it memory parallelism) is high.
+#define AS_ET 32
+#define AS_CH 16
+#define AS_THREADS 256
+__global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int mat_begin, EigArgs ea, SvtArgs a) {
+    extern __shared__ cf ssm[];
+    __shared__ float gcoef[AS_CH];
+    int mat;
+    const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    if (is_frozen(g, mat, a.active)) return;
+    const int n = g.s, len = g.len;
+    const int e0 = blockIdx.y * AS_ET;
+    if (e0 >= len) return;
+    const int r = ea.rank[g.moff + mat];
+    if (r > AS_CH) return;                 // k_apply_eig handles the rest
+    const long long mb = g.off + (long long)mat * n * len;
+    if (blockIdx.y == 0 && threadIdx.x == 0 && a.rank_out) a.rank_out[g.moff + mat] = r;
+    const float t = g.thresh;
+    cf *Vs = ssm;                          // [AS_CH][n]
+    cf *Ys = ssm + (long long)AS_CH * n;   // [AS_ET][AS_CH + 1]
+    const cf *V = ea.V + mb;
+    const float *lam = ea.lam + g.soff + (long long)mat * n;
+    const int tid = threadIdx.x, e = tid & 31, w = tid >> 5;
+    for (int idx = tid; idx < r * n; idx += AS_THREADS) Vs[idx] = V[idx];
+    if (tid < r) {
+        const float sg = sqrtf(fmaxf(lam[tid], 0.f));
+        gcoef[tid] = sg > t ? 1.f - t / sg : 0.f;
+    }
+    __syncthreads();
+    const bool ein = e0 + e < len;
+    const cf *Bcol = a.B0 + mb + e0 + e;
+    {
+        const int k0 = 2 * w, k1 = k0 + 1;         // warp-uniform
+        if (k0 < r) {
+            float y0r = 0.f, y0i = 0.f, y1r = 0.f, y1i = 0.f;
+            if (ein) {
+                const cf *v0 = Vs + (long long)k0 * n, *v1 = Vs + (long long)(k1 < r ? k1 : k0) * n;
+                for (int c = 0; c < n; ++c) {
+                    const cf b = Bcol[(long long)c * len];
+                    const cf a0 = v0[c], a1 = v1[c];
+                    y0r = fmaf(b.x, a0.x, fmaf(-b.y, a0.y, y0r));
+                    y0i = fmaf(b.x, a0.y, fmaf(b.y, a0.x, y0i));
+                    y1r = fmaf(b.x, a1.x, fmaf(-b.y, a1.y, y1r));
+                    y1i = fmaf(b.x, a1.y, fmaf(b.y, a1.x, y1i));
+                }
+            }
+            Ys[e * (AS_CH + 1) + k0] = mk(gcoef[k0] * y0r, gcoef[k0] * y0i);
+            if (k1 < r) Ys[e * (AS_CH + 1) + k1] = mk(gcoef[k1] * y1r, gcoef[k1] * y1i);
+        }
+    }
+    __syncthreads();
+    if (!ein) return;
+    const float ib = 1.f / a.beta;
+    const cf *ye = Ys + e * (AS_CH + 1);
+    for (int c = w; c < n; c += AS_THREADS / 32) {
+        float zr = 0.f, zi = 0.f;
+        for (int k = 0; k < r; ++k) {
+            const cf y = ye[k], v = Vs[(long long)k * n + c];
+            zr = fmaf(y.x, v.x, fmaf(y.y, v.y, zr));
+            zi = fmaf(y.y, v.x, fmaf(-y.x, v.y, zi));
+        }
+        const long long vi = mb + (long long)c * len + e0 + e;
+        if (a.mode == 0) {
+            if (a.z_natural) {
+                const int rr = g.trans ? c : e0 + e, cc = g.trans ? e0 + e : c;
+                a.Zout[mb + (long long)rr * g.cols + cc] = mk(zr, zi);
+            } else {
+                a.Zout[vi] = mk(zr, zi);
+            }
+        } else {
+            const cf A = a.B0[vi];
+            const cf Dv = a.D[vi];
+            const cf Dn = mk(Dv.x + a.tau * (A.x - Dv.x * ib - zr), Dv.y + a.tau * (A.y - Dv.y * ib - zi));
+            a.D[vi] = Dn;
+            a.E[vi] = mk(zr - Dn.x * ib, zi - Dn.y * ib);
+        }
+    }
+}
+
 #define AP_ET 16
 #define AP_CH 16
 #define AP_THREADS 256
@@ -1034,6 +1119,7 @@ __global__ void __launch_bounds__(AP_THREADS) k_apply_eig(GroupSet gs, int mat_b
     const int et = min(AP_ET, len - e0);
     const long long mb = g.off + (long long)mat * n * len;
     const int r = ea.rank[g.moff + mat];
+    if (r <= AS_CH) return;                // k_apply_stream handled it
     const float t = g.thresh;
     cf *Bt = xsm;                          // [n][AP_ET]
     cf *Vc = Bt + (long long)n * AP_ET;    // [AP_CH][n]
@@ -1143,6 +1229,8 @@ cudaError_t eig_init_attributes() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_apply_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_apply_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
 }
 
@@ -1206,6 +1294,12 @@ cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, c
     int maxlen = 0, maxn = 0;
     for (int k = 0; k < gs.n; ++k) { maxlen = max(maxlen, gs.g[k].len); maxn = max(maxn, gs.g[k].s); }
     if (maxn > 512) return cudaErrorInvalidValue;
+    // matrices with at most AS_CH pairs above t^2: streaming kernel; the others: k_apply_eig
+    const size_t smem_s = sizeof(cf) * ((size_t)AS_CH * maxn + (size_t)AS_ET * (AS_CH + 1));
+    dim3 grid_s(mat_count, (maxlen + AS_ET - 1) / AS_ET);
+    k_apply_stream<<<grid_s, AS_THREADS, smem_s, st>>>(gs, mat_begin, ea, a);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
     const size_t smem = sizeof(cf) * ((size_t)maxn * AP_ET + (size_t)AP_CH * maxn + AP_ET * AP_CH);
     dim3 grid(mat_count, (maxlen + AP_ET - 1) / AP_ET);
     k_apply_eig<<<grid, AP_THREADS, smem, st>>>(gs, mat_begin, ea, a);
