@@ -1099,27 +1099,55 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
     if (!ein) return;
     const float ib = 1.f / a.beta;
     const cf *ye = Ys + e * (AS_CH + 1);
-    for (int c = w; c < n; c += AS_THREADS / 32) {
-        float zr = 0.f, zi = 0.f;
-        for (int k = 0; k < r; ++k) {
-            const cf y = ye[k], v = Vs[(long long)k * n + c];
-            zr = fmaf(y.x, v.x, fmaf(y.y, v.y, zr));
-            zi = fmaf(y.y, v.x, fmaf(-y.x, v.y, zi));
-        }
-        const long long vi = mb + (long long)c * len + e0 + e;
-        if (a.mode == 0) {
-            if (a.z_natural) {
-                const int rr = g.trans ? c : e0 + e, cc = g.trans ? e0 + e : c;
-                a.Zout[mb + (long long)rr * g.cols + cc] = mk(zr, zi);
-            } else {
-                a.Zout[vi] = mk(zr, zi);
+    // Z columns c = w, w + 8, ...; batches of AS_B rows so that their loads are in flight together
+    constexpr int AS_B = 4, NWS = AS_THREADS / 32;
+    const cf *__restrict__ B0 = a.B0;
+    cf *__restrict__ Dp = a.D;
+    cf *__restrict__ Ep = a.E;
+    for (int cb = w; cb < n; cb += AS_B * NWS) {
+        cf Av[AS_B], Dv[AS_B];
+        float zr[AS_B], zi[AS_B];
+#pragma unroll
+        for (int u = 0; u < AS_B; ++u) {
+            const int c = cb + u * NWS;
+            const long long vi = mb + (long long)c * len + e0 + e;
+            if (c < n && a.mode != 0) {
+                Av[u] = B0[vi];
+                Dv[u] = Dp[vi];
             }
-        } else {
-            const cf A = a.B0[vi];
-            const cf Dv = a.D[vi];
-            const cf Dn = mk(Dv.x + a.tau * (A.x - Dv.x * ib - zr), Dv.y + a.tau * (A.y - Dv.y * ib - zi));
-            a.D[vi] = Dn;
-            a.E[vi] = mk(zr - Dn.x * ib, zi - Dn.y * ib);
+            zr[u] = 0.f;
+            zi[u] = 0.f;
+        }
+        for (int k = 0; k < r; ++k) {
+            const cf y = ye[k];
+#pragma unroll
+            for (int u = 0; u < AS_B; ++u) {
+                const int c = cb + u * NWS;
+                if (c < n) {
+                    const cf v = Vs[(long long)k * n + c];
+                    zr[u] = fmaf(y.x, v.x, fmaf(y.y, v.y, zr[u]));
+                    zi[u] = fmaf(y.y, v.x, fmaf(-y.x, v.y, zi[u]));
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < AS_B; ++u) {
+            const int c = cb + u * NWS;
+            if (c >= n) continue;
+            const long long vi = mb + (long long)c * len + e0 + e;
+            if (a.mode == 0) {
+                if (a.z_natural) {
+                    const int rr = g.trans ? c : e0 + e, cc = g.trans ? e0 + e : c;
+                    a.Zout[mb + (long long)rr * g.cols + cc] = mk(zr[u], zi[u]);
+                } else {
+                    a.Zout[vi] = mk(zr[u], zi[u]);
+                }
+            } else {
+                const cf A = Av[u], D = Dv[u];
+                const cf Dn = mk(D.x + a.tau * (A.x - D.x * ib - zr[u]), D.y + a.tau * (A.y - D.y * ib - zi[u]));
+                Dp[vi] = Dn;
+                Ep[vi] = mk(zr[u] - Dn.x * ib, zi[u] - Dn.y * ib);
+            }
         }
     }
 }
