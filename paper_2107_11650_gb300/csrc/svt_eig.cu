@@ -619,51 +619,6 @@ __device__ __forceinline__ void gershgorin(const float *dd, const float *ff, con
     *pivmin_ = FLT_MIN * fmaxf(1.f, fm2);
 }
 
-// Apply the Householder reflectors H_k = I - tau_k v_k v_k^H (v_k: entries
-// k+1..n-1, stored below the diagonal of packed column k) to nv vectors of
-// length n in shared memory (row stride n), warp per vector.  forward = true:
-// Q^H y = H_{n-3} ... H_0 y (k ascending); false: Q y (k descending).
-// Reflectors are staged EV_HB at a time in hb (EV_HB x n).
-__device__ void apply_reflectors(cf *Yc, int nv, int n, const cf *Gglob, const float *taus, cf *hb, bool forward,
-                                 int tid, int lane, int warp) {
-    const int kmax = n - 3;
-    for (int kb0 = 0; kb0 <= kmax; kb0 += EV_HB) {
-        const int nbat = min(EV_HB, kmax - kb0 + 1);
-        for (int b = 0; b < nbat; ++b) {
-            const int k = forward ? kb0 + b : kmax - kb0 - b;
-            const int m = n - k - 1;
-            const cf *hv = Gglob + colstart(k, n) + 1;
-            for (int i = tid; i < m; i += EIG_THREADS) hb[(long long)b * n + i] = hv[i];
-        }
-        __syncthreads();
-        for (int w = warp; w < nv; w += EIG_WARPS) {
-            for (int b = 0; b < nbat; ++b) {
-                const int k = forward ? kb0 + b : kmax - kb0 - b;
-                const float tau = taus[k];
-                if (tau == 0.f) continue;
-                const int m = n - k - 1;
-                const cf *vk = hb + (long long)b * n;
-                cf *y = Yc + (long long)w * n + k + 1;
-                float sr = 0.f, si = 0.f;
-                for (int i = lane; i < m; i += 32) {
-                    const cf v = vk[i], yy = y[i];
-                    sr += v.x * yy.x + v.y * yy.y;
-                    si += v.x * yy.y - v.y * yy.x;
-                }
-                sr = wsum(sr) * tau;
-                si = wsum(si) * tau;
-                for (int i = lane; i < m; i += 32) {
-                    const cf v = vk[i];
-                    y[i].x -= v.x * sr - v.y * si;
-                    y[i].y -= v.x * si + v.y * sr;
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ---------------------------------------------------------------- eigvec
 // Shared-memory layout of k_eigvec (16-byte aligned regions).
 struct EvLayout {
@@ -891,7 +846,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
 // Shared-memory layout of k_resolvent (16-byte aligned regions); QC pairs per
 // pass give 2 QC complex right-hand sides and 4 QC real solves.
 struct RsLayout {
-    size_t ph, dd, ff, f2, taus, zr, lu0, lu1, lu2, llm, lpv, wc, hb, total;
+    size_t ph, dd, ff, f2, taus, zr, lu0, lu1, lu2, llm, lpv, wc, total;
 };
 __host__ __device__ inline RsLayout rs_layout(int n, int qc) {
     const size_t st = 4 * (size_t)qc + 1;
@@ -909,31 +864,92 @@ __host__ __device__ inline RsLayout rs_layout(int n, int qc) {
     L.llm = o; o += al16(st * n * 4);
     L.lpv = o; o += al16(st * n);
     L.wc = o; o += al16(2 * (size_t)qc * n * 8);
-    L.hb = o; o += al16((size_t)EV_HB * n * 8);
     L.total = o;
     return L;
 }
 
-// Remove from each of nv complex vectors (smem, row stride n) its components
-// along the r real orthonormal vectors zs (global, row stride n); warp per vector.
-__device__ void project_off(cf *Yc, int nv, int n, const float *zs, int r, int lane, int warp) {
-    for (int w = warp; w < nv; w += EIG_WARPS) {
-        cf *y = Yc + (long long)w * n;
-        for (int k = 0; k < r; ++k) {
-            const float *z = zs + (long long)k * n;
-            float cr = 0.f, ci = 0.f;
-            for (int i = lane; i < n; i += 32) {
-                cr = fmaf(z[i], y[i].x, cr);
-                ci = fmaf(z[i], y[i].y, ci);
+// One warp applies the reflectors H_k = I - tau_k v_k v_k^H (v_k: entries k+1..n-1,
+// stored below the diagonal of packed column k) to its own vector y (length n,
+// shared memory), reading each reflector from global memory into registers (lane
+// holds entries lane, lane + 32, ...) with the next one prefetched; no block
+// barrier.  forward: Q^H y = H_{n-3} ... H_0 y (k ascending); otherwise
+// Q y = H_0 ... H_{n-3} y (k descending).  n <= 32 * RS_MAXJ.
+#define RS_MAXJ 15
+__device__ void warp_reflectors(cf *y, int n, const cf *Gglob, const float *taus, bool forward, int lane) {
+    const int kmax = n - 3;
+    if (kmax < 0) return;
+    cf cur[RS_MAXJ], nxt[RS_MAXJ];
+    int k = forward ? 0 : kmax;
+    {
+        const int m = n - k - 1;
+        const cf *hv = Gglob + colstart(k, n) + 1;
+#pragma unroll
+        for (int j = 0; j < RS_MAXJ; ++j) {
+            const int i = lane + 32 * j;
+            cur[j] = i < m ? hv[i] : mk(0.f, 0.f);
+        }
+    }
+    for (int step = 0; step <= kmax; ++step) {
+        const int kn = forward ? k + 1 : k - 1;
+        if (step < kmax) {
+            const int m = n - kn - 1;
+            const cf *hv = Gglob + colstart(kn, n) + 1;
+#pragma unroll
+            for (int j = 0; j < RS_MAXJ; ++j) {
+                const int i = lane + 32 * j;
+                nxt[j] = i < m ? hv[i] : mk(0.f, 0.f);
             }
-            cr = wsum(cr);
-            ci = wsum(ci);
-            for (int i = lane; i < n; i += 32) {
-                y[i].x -= cr * z[i];
-                y[i].y -= ci * z[i];
+        }
+        const float tau = taus[k];
+        if (tau != 0.f) {
+            const int m = n - k - 1;
+            cf *yk = y + k + 1;
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int j = 0; j < RS_MAXJ; ++j) {
+                const int i = lane + 32 * j;
+                if (i < m) {
+                    const cf v = cur[j], yy = yk[i];
+                    sr += v.x * yy.x + v.y * yy.y;
+                    si += v.x * yy.y - v.y * yy.x;
+                }
+            }
+            sr = wsum(sr) * tau;
+            si = wsum(si) * tau;
+#pragma unroll
+            for (int j = 0; j < RS_MAXJ; ++j) {
+                const int i = lane + 32 * j;
+                if (i < m) {
+                    const cf v = cur[j];
+                    yk[i].x -= v.x * sr - v.y * si;
+                    yk[i].y -= v.x * si + v.y * sr;
+                }
             }
             __syncwarp();
         }
+#pragma unroll
+        for (int j = 0; j < RS_MAXJ; ++j) cur[j] = nxt[j];
+        k = kn;
+    }
+}
+
+// Remove from the complex vector y (shared memory, one warp) its components
+// along the r real orthonormal vectors zs (global, row stride n).
+__device__ void project_one(cf *y, int n, const float *zs, int r, int lane) {
+    for (int k = 0; k < r; ++k) {
+        const float *z = zs + (long long)k * n;
+        float cr = 0.f, ci = 0.f;
+        for (int i = lane; i < n; i += 32) {
+            cr = fmaf(z[i], y[i].x, cr);
+            ci = fmaf(z[i], y[i].y, ci);
+        }
+        cr = wsum(cr);
+        ci = wsum(ci);
+        for (int i = lane; i < n; i += 32) {
+            y[i].x -= cr * z[i];
+            y[i].y -= ci * z[i];
+        }
+        __syncwarp();
     }
 }
 
@@ -955,7 +971,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
     float *lu0 = (float *)(rsm + LY.lu0), *lu1 = (float *)(rsm + LY.lu1), *lu2 = (float *)(rsm + LY.lu2);
     float *llm = (float *)(rsm + LY.llm);
     unsigned char *lpv = rsm + LY.lpv;
-    cf *wc = (cf *)(rsm + LY.wc), *hb = (cf *)(rsm + LY.hb);
+    cf *wc = (cf *)(rsm + LY.wc);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long pk = (long long)n * (n + 1) / 2;
     const cf *Gglob = a.Gp + g.poff + (long long)mat * pk;
@@ -977,42 +993,39 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
         const int qc = min(QC, r - q0), nv = 2 * qc;
         for (int idx = tid; idx < nv * n; idx += EIG_THREADS) wc[idx] = W[wbase + (long long)2 * q0 * n + idx];
         __syncthreads();
-        apply_reflectors(wc, nv, n, Gglob, taus, hb, true, tid, lane, warp);     // Q^H (ends synchronised)
-        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
-            const int i = idx % n;
-            wc[idx] = cmulc(ph[i], wc[idx]);                                      // P^H
-        }
-        __syncthreads();
-        project_off(wc, nv, n, zs, r, lane, warp);
-        __syncthreads();
-        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
-            const int w = idx / n, i = idx - w * n;
-            zr[i * ST + 2 * w] = wc[idx].x;
-            zr[i * ST + 2 * w + 1] = wc[idx].y;
+        // each warp maps its own right-hand side to the tridiagonal basis: P^H Q^H w, projected
+        for (int w = warp; w < nv; w += EIG_WARPS) {
+            cf *y = wc + (long long)w * n;
+            warp_reflectors(y, n, Gglob, taus, true, lane);
+            for (int i = lane; i < n; i += 32) y[i] = cmulc(ph[i], y[i]);
+            __syncwarp();
+            project_one(y, n, zs, r, lane);
+            for (int i = lane; i < n; i += 32) {
+                zr[i * ST + 2 * w] = y[i].x;
+                zr[i * ST + 2 * w + 1] = y[i].y;
+            }
         }
         __syncthreads();
         if (tid < 2 * nv)       // real system tid: pair q0 + tid / 4, right-hand side (tid / 2) % 2, re / im
             tri_solve<ST>(dd, ff, n, lam[q0 + tid / 4], zr + tid, lu0 + tid, lu1 + tid, lu2 + tid, llm + tid,
                           lpv + tid, tiny, true);
         __syncthreads();
-        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
-            const int w = idx / n, i = idx - w * n;
+        for (int w = warp; w < nv; w += EIG_WARPS) {
+            cf *y = wc + (long long)w * n;
             // (lambda I - T_r)^{-1} = -(T_r - lambda I)^{-1}
-            wc[idx] = mk(-zr[i * ST + 2 * w], -zr[i * ST + 2 * w + 1]);
-        }
-        __syncthreads();
-        project_off(wc, nv, n, zs, r, lane, warp);
-        __syncthreads();
-        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
-            const int i = idx % n;
-            wc[idx] = cmul(ph[i], wc[idx]);                                       // P
-        }
-        __syncthreads();
-        apply_reflectors(wc, nv, n, Gglob, taus, hb, false, tid, lane, warp);    // Q
-        for (int idx = tid; idx < nv * n; idx += EIG_THREADS) {
-            const cf y = wc[idx];
-            if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(a.status, (unsigned)ST_NONFINITE);
-            Y[wbase + (long long)2 * q0 * n + idx] = y;
+            for (int i = lane; i < n; i += 32) y[i] = mk(-zr[i * ST + 2 * w], -zr[i * ST + 2 * w + 1]);
+            __syncwarp();
+            project_one(y, n, zs, r, lane);
+            for (int i = lane; i < n; i += 32) y[i] = cmul(ph[i], y[i]);
+            __syncwarp();
+            warp_reflectors(y, n, Gglob, taus, false, lane);
+            bool bad = false;
+            for (int i = lane; i < n; i += 32) {
+                const cf v = y[i];
+                if (!isfinite(v.x) || !isfinite(v.y)) bad = true;
+                Y[wbase + (long long)(2 * q0 + w) * n + i] = v;
+            }
+            if (bad) atomicOr(a.status, (unsigned)ST_NONFINITE);
         }
         __syncthreads();
     }
