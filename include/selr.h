@@ -127,6 +127,28 @@ void selr_desc_default(selr_desc *desc);
  * *out is set to NULL on failure. */
 selr_status selr_plan_create(const selr_desc *desc, selr_plan **out);
 
+/* One plan for n_inst independent reconstructions of uneven size (2D models
+ * only), batched: every step of an iteration runs for all instances at once,
+ * and all lifted matrices of one SVT size class (tiny / tridiagonal buckets
+ * n <= 32, 64, 128, 208, larger) across all instances go to one launch per
+ * kernel (the paper solves one problem at a time; batching is an engineering
+ * extension).  descs[i] may differ in J, M, N, window and lambda; every other
+ * field must equal descs[0] (SELR_ERR_INVALID_ARG otherwise;
+ * SELR_ERR_UNSUPPORTED for parameter models).  1 <= n_inst <= 32.
+ * selr_solve then takes packed arrays: instance i's Y / X [J][M][N] at
+ * element offset k_offset(i) and its mask [M][N] at mask_offset(i)
+ * (selr_plan_instance_layout).  With tol >= 0 the batch runs until every
+ * instance meets the stopping rule (rel_out: the largest change).  The
+ * single-operator entry points (selr_lift_shape, selr_transform, selr_lift,
+ * selr_adjoint, selr_dc, selr_dc_vjp) return SELR_ERR_UNSUPPORTED on a plan
+ * with more than one instance; selr_svt / selr_svt_vjp work on any plan. */
+selr_status selr_plan_create_batch(const selr_desc *descs, int32_t n_inst, selr_plan **out);
+
+/* Element offsets of instance inst in the packed k-space / image arrays and in
+ * the packed mask array of a plan (host outputs; either may be NULL). */
+selr_status selr_plan_instance_layout(const selr_plan *plan, int32_t inst, int64_t *k_offset,
+                                      int64_t *mask_offset);
+
 /* Free the plan and its workspace.  NULL is accepted. */
 selr_status selr_plan_destroy(selr_plan *plan);
 

@@ -57,6 +57,9 @@ SIGNATURES = {
     "selr_profile_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_float), ctypes.POINTER(c_int32)]),
     "selr_status_string": (ctypes.c_char_p, [c_int32]),
     "selr_last_error_string": (ctypes.c_char_p, []),
+    "selr_plan_create_batch": (c_int32, [ctypes.POINTER(SelrDesc), c_int32, ctypes.POINTER(c_void_p)]),
+    "selr_plan_instance_layout": (c_int32, [c_void_p, c_int32, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]),
     "selr_svt_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p,
                                c_void_p, c_void_p, c_void_p]),
     "selr_dc_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -139,6 +139,60 @@ class Plan:
         return n.value, r.value, c.value
 
 
+class BatchPlan(Plan):
+    """A ``selr_plan`` for several 2D instances of uneven size (selr_plan_create_batch)."""
+
+    def __init__(self, descs):
+        self.lib = _lib.load()
+        self.descs = list(descs)
+        self.desc = self.descs[0]
+        arr = (SelrDesc * len(self.descs))(*[d.to_c() for d in self.descs])
+        h = ctypes.c_void_p()
+        check(self.lib.selr_plan_create_batch(arr, len(self.descs), ctypes.byref(h)), "selr_plan_create_batch")
+        self.handle = h
+
+    @property
+    def nK(self):
+        return sum(d.L * d.J * d.M * d.N for d in self.descs)
+
+    @property
+    def n_mask(self):
+        return sum(d.L * d.M * d.N for d in self.descs)
+
+    def layout(self, i):
+        """(k_offset, mask_offset) of instance i in the packed arrays."""
+        k, m = ctypes.c_int64(), ctypes.c_int64()
+        check(self.lib.selr_plan_instance_layout(self.handle, int(i), ctypes.byref(k), ctypes.byref(m)),
+              "selr_plan_instance_layout")
+        return k.value, m.value
+
+    def pack(self, arrays, dtype, mask=False):
+        """Concatenate per-instance tensors in the plan's packed order."""
+        n = self.n_mask if mask else self.nK
+        out = torch.empty(n, dtype=dtype, device=arrays[0].device)
+        for i, a in enumerate(arrays):
+            off = self.layout(i)[1 if mask else 0]
+            out[off:off + a.numel()].copy_(a.reshape(-1))
+        return out
+
+    def unpack(self, packed, i):
+        """View of instance i in a packed k-space / image array."""
+        d = self.descs[i]
+        off = self.layout(i)[0]
+        return packed[off:off + d.L * d.J * d.M * d.N].view(d.J, d.M, d.N) if d.L == 1 else \
+            packed[off:off + d.L * d.J * d.M * d.N].view(d.L, d.J, d.M, d.N)
+
+
+def selr_solve_batch(plan: BatchPlan, Y, mask, X_out, stream=None):
+    """selr_solve on packed arrays of a batch plan; returns (iterations, largest relative change)."""
+    it, rel = ctypes.c_int32(), ctypes.c_float()
+    check(plan.lib.selr_solve(plan.handle, _ptr(Y, torch.complex64, "Y", plan.nK),
+                              _ptr(mask, torch.uint8, "mask", plan.n_mask),
+                              _ptr(X_out, torch.complex64, "X_out", plan.nK), ctypes.byref(it), ctypes.byref(rel),
+                              _stream(stream)), "selr_solve")
+    return it.value, rel.value
+
+
 def selr_transform(plan: Plan, dim: int, inverse: bool, x, out, stream=None):
     check(plan.lib.selr_transform(plan.handle, dim, 1 if inverse else 0,
                                   _ptr(x, torch.complex64, "x", plan.nK), _ptr(out, torch.complex64, "out", plan.nK),

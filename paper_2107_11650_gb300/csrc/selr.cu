@@ -8,11 +8,26 @@
 #include <string.h>
 #include <new>
 
+// One reconstruction problem of a plan: its sizes, its slices of the k-space
+// sized arrays and the mask, and its transform tables, weights and normal
+// diagonals (the lifted state of all instances shares the plan's arrays).
+struct Inst {
+    int J, M, N, L, p;
+    float lambda;
+    long long nK, koff, mkoff;   // k-space elements; offsets in K-sized arrays and in the mask
+    int poff;                    // offset of its [M][2] partial sums
+    FftTable ftM, ftN;
+    cf *twM, *twN, *wM, *wN;
+    float *da, *db;
+};
+
 struct selr_plan {
     selr_desc d;
     int model2d, vc;
-    int L, J, M, N;
-    long long nK;
+    int L, J, M, N;              // instance 0 (the only one unless created by selr_plan_create_batch)
+    long long nK;                // k-space elements of all instances
+    int n_inst;
+    Inst inst[SELR_MAX_INST];
     GroupSet gs;
     long long lift_elems, vec_elems;
     cf *K, *hybA, *hybB, *adjA, *adjB;
@@ -27,10 +42,6 @@ struct selr_plan {
     float *rel;
     int *active, *active_next;
     unsigned *status;
-    cf *twM, *twN;
-    FftTable ftM, ftN;
-    cf *wM, *wN;
-    float *da, *db;
     size_t bytes;
     float *h_rel;          // pinned host mirror
     int *h_active;         // pinned host mirror
@@ -248,10 +259,15 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
                     p->rank, p->sigma,
-                    p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status,
-                    p->twM, p->twN, p->wM, p->wN, p->da, p->db};
+                    p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (int i = 0; i < p->n_inst; ++i) {
+        Inst &I = p->inst[i];
+        void *ib[] = {I.twM, I.twN, I.wM, I.wN, I.da, I.db};
+        for (void *b : ib)
+            if (b) cudaFree(b);
+    }
     if (p->ev) {
         for (size_t i = 0; i < (size_t)p->prof_cap * NSTAGE * 2; ++i) cudaEventDestroy(p->ev[i]);
         free(p->ev);
@@ -262,34 +278,91 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     return SELR_OK;
 }
 
-extern "C" selr_status selr_plan_create(const selr_desc *d, selr_plan **out) {
+// SVT kernel class of a lift family: families of one class share one launch
+// sequence (0: warp-per-matrix SVT; eigensolver: tridiagonal template buckets).
+static int svt_class(const Group &g, int svd) {
+    if (svt_small_fits(g)) return 0;
+    if (svd == SELR_SVD_JACOBI) return 1;
+    if (g.s <= 32) return 1;
+    if (g.s <= 64) return 2;
+    if (g.s <= 128) return 3;
+    if (g.s <= 208) return 4;
+    return 5;
+}
+
+// Descriptions of a batch must agree on everything but the problem sizes and lambda.
+static selr_status check_batch(const selr_desc *ds, int n) {
+    for (int i = 0; i < n; ++i) {
+        const selr_status s = validate(&ds[i]);
+        if (s != SELR_OK) return s;
+    }
+    if (n == 1) return SELR_OK;
+    for (int i = 0; i < n; ++i) {
+        const selr_desc &a = ds[0], &b = ds[i];
+        if (b.model > SELR_SHLR_V) return SELR_ERR_UNSUPPORTED;
+        if (b.model != a.model || b.weight != a.weight || b.beta != a.beta || b.tau != a.tau ||
+            b.d_init != a.d_init || b.max_iter != a.max_iter || b.tol != a.tol || b.exec != a.exec ||
+            b.svd_method != a.svd_method || b.gram_precision != a.gram_precision ||
+            b.jacobi_max_sweeps != a.jacobi_max_sweeps || b.jacobi_tol != a.jacobi_tol)
+            return SELR_ERR_INVALID_ARG;
+    }
+    return SELR_OK;
+}
+
+static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out) {
     if (!out) return SELR_ERR_INVALID_ARG;
     *out = nullptr;
-    selr_status s = validate(d);
+    if (!ds || n_inst < 1 || n_inst > SELR_MAX_INST) return SELR_ERR_INVALID_ARG;
+    selr_status s = check_batch(ds, n_inst);
     if (s != SELR_OK) return s;
     selr_plan *p = new (std::nothrow) selr_plan;
     if (!p) return SELR_ERR_ALLOC;
     memset(p, 0, sizeof(*p));
+    const selr_desc *d = &ds[0];
     p->d = *d;
+    p->n_inst = n_inst;
     p->model2d = d->model <= SELR_SHLR_V;
     p->vc = d->model == SELR_SHLR_V || d->model == SELR_SHLR_VP;
     p->L = d->L; p->J = d->J; p->M = d->M; p->N = d->N;
-    p->nK = (long long)d->L * d->J * d->M * d->N;
     const float t1 = 1.0f / d->beta;
     GroupSet &gs = p->gs;
-    if (p->model2d) {
-        gs.n = 2;
-        gs.g[0] = make_group(G_ROW, d->M, d->N, d->window, d->J, p->vc, d->M, d->N, 1, t1);
-        gs.g[1] = make_group(G_COL, d->N, d->M, d->window, d->J, p->vc, d->M, d->N, 1, t1);
-    } else {
-        gs.n = 2;
-        gs.g[0] = make_group(G_PE, d->M * d->L, d->N, d->window, d->J, p->vc, d->M, d->N, d->L, t1);
-        gs.g[1] = make_group(G_PARAM, d->M * d->N, d->L, d->window_param, d->J, 0, d->M, d->N, d->L,
-                             d->lambda2 / d->beta);
+    gs.n = 0;
+    long long koff = 0, mkoff = 0;
+    int poff = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const selr_desc &di = ds[i];
+        Inst &I = p->inst[i];
+        I.J = di.J; I.M = di.M; I.N = di.N; I.L = di.L; I.p = di.window; I.lambda = di.lambda;
+        I.nK = (long long)di.L * di.J * di.M * di.N;
+        I.koff = koff; I.mkoff = mkoff; I.poff = poff;
+        koff += I.nK;
+        mkoff += (long long)di.L * di.M * di.N;
+        poff += 2 * di.M;
+        if (p->model2d) {
+            gs.g[gs.n] = make_group(G_ROW, di.M, di.N, di.window, di.J, p->vc, di.M, di.N, 1, t1);
+            gs.g[gs.n++].inst = i;
+            gs.g[gs.n] = make_group(G_COL, di.N, di.M, di.window, di.J, p->vc, di.M, di.N, 1, t1);
+            gs.g[gs.n++].inst = i;
+        } else {
+            gs.g[gs.n++] = make_group(G_PE, di.M * di.L, di.N, di.window, di.J, p->vc, di.M, di.N, di.L, t1);
+            gs.g[gs.n++] = make_group(G_PARAM, di.M * di.N, di.L, di.window_param, di.J, 0, di.M, di.N, di.L,
+                                      di.lambda2 / di.beta);
+        }
     }
+    p->nK = koff;
     for (int k = 0; k < gs.n; ++k) {
         if (gs.g[k].len > 512 || gs.g[k].s > 1024) { delete p; return SELR_ERR_SHAPE; }
         if (d->svd_method == SELR_SVD_EIG && gs.g[k].s > 480) { delete p; return SELR_ERR_SHAPE; }
+    }
+    if (n_inst > 1) {
+        // order the families by SVT class so that each class is one contiguous launch
+        for (int a = 1; a < gs.n; ++a) {
+            const Group g = gs.g[a];
+            const int c = svt_class(g, d->svd_method);
+            int b = a - 1;
+            while (b >= 0 && svt_class(gs.g[b], d->svd_method) > c) { gs.g[b + 1] = gs.g[b]; --b; }
+            gs.g[b + 1] = g;
+        }
     }
     finish_set(&gs);
     p->lift_elems = 0;
@@ -323,61 +396,88 @@ extern "C" selr_status selr_plan_create(const selr_desc *d, selr_plan **out) {
         AL(p->tri, 4 * sizeof(float) * (size_t)p->vec_elems);
         AL(p->rank, sizeof(int) * (size_t)gs.total);
     }
+    const size_t nrel = (size_t)(n_inst > 1 + d->M ? n_inst : 1 + d->M);
     AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
     AL(p->mat_status, sizeof(int) * (size_t)gs.total);
-    AL(p->partial, sizeof(double) * 2 * (size_t)d->M);
-    AL(p->rel, sizeof(float) * (1 + (size_t)d->M));
+    AL(p->partial, sizeof(double) * (size_t)poff);
+    AL(p->rel, sizeof(float) * nrel);
     AL(p->active, sizeof(int) * (size_t)d->M);
     AL(p->active_next, sizeof(int) * (size_t)d->M);
     AL(p->status, sizeof(unsigned));
-    AL(p->wN, sizeof(cf) * d->N);
-    AL(p->wM, sizeof(cf) * d->M);
-    AL(p->da, sizeof(float) * d->N);
-    AL(p->db, sizeof(float) * (p->model2d ? d->M : d->L));
+    for (int i = 0; i < n_inst; ++i) {
+        Inst &I = p->inst[i];
+        AL(I.wN, sizeof(cf) * I.N);
+        AL(I.wM, sizeof(cf) * I.M);
+        AL(I.da, sizeof(float) * I.N);
+        AL(I.db, sizeof(float) * (p->model2d ? I.M : I.L));
+    }
 #undef AL
     if (cudaMemset(p->status, 0, sizeof(unsigned)) != cudaSuccess) { selr_plan_destroy(p); return SELR_ERR_CUDA; }
-    // FFT tables (N always; M for the 2D models)
-    if (fft_table_build(d->N, &p->ftN, &p->twN) != cudaSuccess) { selr_plan_destroy(p); return SELR_ERR_SHAPE; }
-    if (p->model2d && fft_table_build(d->M, &p->ftM, &p->twM) != cudaSuccess) { selr_plan_destroy(p); return SELR_ERR_SHAPE; }
-    // weights and normal diagonals
-    {
-        const int nmax = d->M > d->N ? d->M : d->N;
+    for (int i = 0; i < n_inst; ++i) {
+        Inst &I = p->inst[i];
+        const selr_desc &di = ds[i];
+        // FFT tables (N always; M for the 2D models)
+        if (fft_table_build(I.N, &I.ftN, &I.twN) != cudaSuccess) { selr_plan_destroy(p); return SELR_ERR_SHAPE; }
+        if (p->model2d && fft_table_build(I.M, &I.ftM, &I.twM) != cudaSuccess) {
+            selr_plan_destroy(p);
+            return SELR_ERR_SHAPE;
+        }
+        // weights and normal diagonals
+        const int nmax = I.M > I.N ? I.M : I.N;
         cf *hw = (cf *)malloc(sizeof(cf) * nmax);
-        float *hd = (float *)malloc(sizeof(float) * (nmax > d->L ? nmax : d->L));
-        selr_status e = SELR_OK;
-        host_weights(d->N, d->weight, hw);
-        if (e == SELR_OK) e = upload(p->wN, hw, sizeof(cf) * d->N);
-        host_weights(d->M, d->weight, hw);
-        if (e == SELR_OK) e = upload(p->wM, hw, sizeof(cf) * d->M);
-        host_normal(d->N, d->window, d->weight, p->vc, hd);
-        if (e == SELR_OK) e = upload(p->da, hd, sizeof(float) * d->N);
-        if (p->model2d) {
-            host_normal(d->M, d->window, d->weight, p->vc, hd);
-            if (e == SELR_OK) e = upload(p->db, hd, sizeof(float) * d->M);
-        } else {
-            host_multiplicity(d->L, d->window_param, hd);
-            if (e == SELR_OK) e = upload(p->db, hd, sizeof(float) * d->L);
+        float *hd = (float *)malloc(sizeof(float) * (nmax > I.L ? nmax : I.L));
+        selr_status e = (hw && hd) ? SELR_OK : SELR_ERR_ALLOC;
+        if (e == SELR_OK) {
+            host_weights(I.N, di.weight, hw);
+            e = upload(I.wN, hw, sizeof(cf) * I.N);
+            host_weights(I.M, di.weight, hw);
+            if (e == SELR_OK) e = upload(I.wM, hw, sizeof(cf) * I.M);
+            host_normal(I.N, di.window, di.weight, p->vc, hd);
+            if (e == SELR_OK) e = upload(I.da, hd, sizeof(float) * I.N);
+            if (p->model2d) {
+                host_normal(I.M, di.window, di.weight, p->vc, hd);
+                if (e == SELR_OK) e = upload(I.db, hd, sizeof(float) * I.M);
+            } else {
+                host_multiplicity(I.L, di.window_param, hd);
+                if (e == SELR_OK) e = upload(I.db, hd, sizeof(float) * I.L);
+            }
         }
         free(hw);
         free(hd);
         if (e != SELR_OK) { selr_plan_destroy(p); return e; }
     }
-    const cf *wrow = d->weight ? p->wN : nullptr;
-    const cf *wcol = d->weight ? p->wM : nullptr;
-    if (p->model2d) {
-        gs.g[0].w = wrow; gs.g[0].src = p->hybA; gs.g[0].dst = p->adjA;
-        gs.g[1].w = wcol; gs.g[1].src = p->hybB; gs.g[1].dst = p->adjB;
-    } else {
-        gs.g[0].w = wrow; gs.g[0].src = p->K; gs.g[0].dst = p->adjA;
-        gs.g[1].w = nullptr; gs.g[1].src = p->hybB; gs.g[1].dst = p->adjB;
+    // sources and destinations of every family
+    for (int k = 0; k < gs.n; ++k) {
+        Group &g = gs.g[k];
+        const Inst &I = p->inst[g.inst];
+        switch (g.kind) {
+            case G_ROW: g.w = d->weight ? I.wN : nullptr; g.src = p->hybA + I.koff; g.dst = p->adjA + I.koff; break;
+            case G_COL: g.w = d->weight ? I.wM : nullptr; g.src = p->hybB + I.koff; g.dst = p->adjB + I.koff; break;
+            case G_PE: g.w = d->weight ? I.wN : nullptr; g.src = p->K + I.koff; g.dst = p->adjA + I.koff; break;
+            default: g.w = nullptr; g.src = p->hybB + I.koff; g.dst = p->adjB + I.koff; break;
+        }
     }
-    if (cudaMallocHost((void **)&p->h_rel, sizeof(float) * (1 + (size_t)d->M)) != cudaSuccess ||
+    if (cudaMallocHost((void **)&p->h_rel, sizeof(float) * nrel) != cudaSuccess ||
         cudaMallocHost((void **)&p->h_active, sizeof(int) * (size_t)d->M) != cudaSuccess) {
         cudaGetLastError();
         selr_plan_destroy(p);
         return SELR_ERR_ALLOC;
     }
     *out = p;
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_plan_create(const selr_desc *d, selr_plan **out) { return create_plan(d, 1, out); }
+
+extern "C" selr_status selr_plan_create_batch(const selr_desc *descs, int32_t n_inst, selr_plan **out) {
+    return create_plan(descs, n_inst, out);
+}
+
+extern "C" selr_status selr_plan_instance_layout(const selr_plan *p, int32_t inst, int64_t *k_offset,
+                                                 int64_t *mask_offset) {
+    if (!p || inst < 0 || inst >= p->n_inst) return SELR_ERR_INVALID_ARG;
+    if (k_offset) *k_offset = p->inst[inst].koff;
+    if (mask_offset) *mask_offset = p->inst[inst].mkoff;
     return SELR_OK;
 }
 
@@ -397,6 +497,7 @@ static int group_index(const selr_plan *p, int axis) {
 extern "C" selr_status selr_lift_shape(const selr_plan *p, int32_t axis, int32_t *nmat, int32_t *rows,
                                        int32_t *cols) {
     if (!p) return SELR_ERR_INVALID_ARG;
+    if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     const int gi = group_index(p, axis);
     if (gi < 0) return SELR_ERR_INVALID_ARG;
     if (nmat) *nmat = p->gs.g[gi].nmat;
@@ -405,17 +506,19 @@ extern "C" selr_status selr_lift_shape(const selr_plan *p, int32_t axis, int32_t
     return SELR_OK;
 }
 
-// Transform along M (dim 0) or N (dim 1) of an [L][J][M][N] array.
-static cudaError_t transform(selr_plan *p, int dim, int inverse, const cf *in, cf *out, cudaStream_t st) {
-    if (dim == 0) return launch_fft(in, out, p->ftM, (long long)p->L * p->J, p->N, inverse, st);
-    return launch_fft(in, out, p->ftN, (long long)p->L * p->J * p->M, 1, inverse, st);
+// Transform along M (dim 0) or N (dim 1) of instance i's [L][J][M][N] array.
+static cudaError_t transform(selr_plan *p, int i, int dim, int inverse, const cf *in, cf *out, cudaStream_t st) {
+    const Inst &I = p->inst[i];
+    if (dim == 0) return launch_fft(in, out, I.ftM, (long long)I.L * I.J, I.N, inverse, st);
+    return launch_fft(in, out, I.ftN, (long long)I.L * I.J * I.M, 1, inverse, st);
 }
 
 extern "C" selr_status selr_transform(selr_plan *p, int32_t dim, int32_t inverse, const void *in, void *out,
                                       selr_stream stream) {
     if (!p || !in || !out || (dim != 0 && dim != 1)) return SELR_ERR_INVALID_ARG;
+    if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     if (dim == 0 && !p->model2d) return SELR_ERR_SHAPE;
-    CK(transform(p, dim, inverse ? 1 : 0, (const cf *)in, (cf *)out, (cudaStream_t)stream));
+    CK(transform(p, 0, dim, inverse ? 1 : 0, (const cf *)in, (cf *)out, (cudaStream_t)stream));
     return SELR_OK;
 }
 
@@ -431,6 +534,7 @@ static GroupSet single_group(const selr_plan *p, int gi) {
 extern "C" selr_status selr_lift(selr_plan *p, int32_t axis, const void *x, const void *D, void *A_out,
                                  selr_stream stream) {
     if (!p || !x || !A_out) return SELR_ERR_INVALID_ARG;
+    if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     const int gi = group_index(p, axis);
     if (gi < 0) return SELR_ERR_INVALID_ARG;
     GroupSet s = single_group(p, gi);
@@ -442,6 +546,7 @@ extern "C" selr_status selr_lift(selr_plan *p, int32_t axis, const void *x, cons
 
 extern "C" selr_status selr_adjoint(selr_plan *p, int32_t axis, const void *E, void *x_out, selr_stream stream) {
     if (!p || !E || !x_out) return SELR_ERR_INVALID_ARG;
+    if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     const int gi = group_index(p, axis);
     if (gi < 0) return SELR_ERR_INVALID_ARG;
     GroupSet s = single_group(p, gi);
@@ -482,37 +587,46 @@ static EigArgs eig_args(selr_plan *p, const int *active) {
 // S_t of every matrix of `gs` in [m0, m0 + mc): B0 (and W for Jacobi) already filled.
 static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, const SvtArgs &a, int part,
                              cudaStream_t st) {
-    // one launch sequence per lift family: kernels are sized for their own family's
-    // matrices, and families of tiny matrices go to the warp-per-matrix kernel
-    for (int k = 0; k < gs.n; ++k) {
+    // one launch sequence per run of consecutive families of the same SVT class (the
+    // families of a batched plan are ordered by class): kernels are sized for their
+    // class, tiny matrices go to the warp-per-matrix kernel
+    const int svd = p->d.svd_method;
+    for (int k = 0; k < gs.n;) {
+        const int c = svt_class(gs.g[k], svd);
+        int k1 = k + 1;
+        while (k1 < gs.n && svt_class(gs.g[k1], svd) == c) ++k1;
         const int b = m0 > gs.start[k] ? m0 : gs.start[k];
-        const int e_ = (m0 + mc) < gs.start[k + 1] ? (m0 + mc) : gs.start[k + 1];
-        if (b >= e_) continue;
-        GroupSet v;
-        memset(&v, 0, sizeof(v));
-        v.n = 1;
-        v.g[0] = gs.g[k];
-        v.start[1] = gs.g[k].nmat;
-        v.total = gs.g[k].nmat;
-        const int lb = b - gs.start[k], lc = e_ - b;
-        cudaError_t e = cudaSuccess;
-        if (svt_small_fits(gs.g[k])) {
-            if (part & 4) e = launch_svt_small(v, lb, lc, a, st);
-        } else if (p->d.svd_method == SELR_SVD_JACOBI) {
-            if (part & 2) e = launch_jacobi(v, lb, lc, a, st);
-            if (e == cudaSuccess && (part & 4)) e = launch_svt_apply(v, lb, lc, a, st);
-        } else {
-            const EigArgs ea = eig_args(p, a.active);
-            if (part & 1) {
-                if (p->d.gram_precision != SELR_GRAM_FP32 && gram_tc_fits(gs.g[k]))
-                    e = launch_gram_tc(v, lb, lc, p->B0, p->Gp, a.active, (int)p->d.gram_precision, p->status, st);
-                else
-                    e = launch_gram(v, lb, lc, p->B0, p->Gp, a.active, st);
+        const int e_ = (m0 + mc) < gs.start[k1] ? (m0 + mc) : gs.start[k1];
+        if (b < e_) {
+            GroupSet v;
+            memset(&v, 0, sizeof(v));
+            v.n = k1 - k;
+            bool tc = p->d.gram_precision != SELR_GRAM_FP32;
+            for (int i = 0; i < v.n; ++i) {
+                v.g[i] = gs.g[k + i];
+                v.start[i] = gs.start[k + i] - gs.start[k];
+                tc = tc && gram_tc_fits(v.g[i]);
             }
-            if (e == cudaSuccess && (part & 2)) e = launch_heig(v, lb, lc, ea, st);
-            if (e == cudaSuccess && (part & 4)) e = launch_apply_eig(v, lb, lc, ea, a, st);
+            v.start[v.n] = gs.start[k1] - gs.start[k];
+            v.total = v.start[v.n];
+            const int lb = b - gs.start[k], lc = e_ - b;
+            cudaError_t e = cudaSuccess;
+            if (c == 0) {
+                if (part & 4) e = launch_svt_small(v, lb, lc, a, st);
+            } else if (svd == SELR_SVD_JACOBI) {
+                if (part & 2) e = launch_jacobi(v, lb, lc, a, st);
+                if (e == cudaSuccess && (part & 4)) e = launch_svt_apply(v, lb, lc, a, st);
+            } else {
+                const EigArgs ea = eig_args(p, a.active);
+                if (part & 1)
+                    e = tc ? launch_gram_tc(v, lb, lc, p->B0, p->Gp, a.active, (int)p->d.gram_precision, p->status, st)
+                           : launch_gram(v, lb, lc, p->B0, p->Gp, a.active, st);
+                if (e == cudaSuccess && (part & 2)) e = launch_heig(v, lb, lc, ea, st);
+                if (e == cudaSuccess && (part & 4)) e = launch_apply_eig(v, lb, lc, ea, a, st);
+            }
+            if (e != cudaSuccess) return e;
         }
-        if (e != cudaSuccess) return e;
+        k = k1;
     }
     return cudaSuccess;
 }
@@ -550,34 +664,43 @@ extern "C" selr_status selr_svt(selr_plan *p, void *A, int32_t nmat, int32_t row
     return SELR_OK;
 }
 
-// FFTs of the adjoints to k-space, the pointwise solve and the reduction.
+// FFTs of the adjoints to k-space, the pointwise solve and the reduction, per
+// instance (arrays are the packed ones; each instance works on its slices).
 static cudaError_t dc_step(selr_plan *p, const cf *Y, const uint8_t *mask, cf *adj_a, cf *adj_b, cf *K,
                            const int *active, int *active_next, cudaStream_t st) {
     cudaError_t e;
-    if (p->model2d) {
-        if ((e = transform(p, 0, 0, adj_a, adj_a, st)) != cudaSuccess) return e;
-        if ((e = transform(p, 1, 0, adj_b, adj_b, st)) != cudaSuccess) return e;
-    } else {
-        if ((e = transform(p, 1, 0, adj_b, adj_b, st)) != cudaSuccess) return e;
+    for (int i = 0; i < p->n_inst; ++i) {
+        const Inst &I = p->inst[i];
+        cf *aa = adj_a + I.koff, *ab = adj_b + I.koff;
+        if (p->model2d) {
+            if ((e = transform(p, i, 0, 0, aa, aa, st)) != cudaSuccess) return e;
+            if ((e = transform(p, i, 1, 0, ab, ab, st)) != cudaSuccess) return e;
+        } else {
+            if ((e = transform(p, i, 1, 0, ab, ab, st)) != cudaSuccess) return e;
+        }
+        DcArgs a;
+        memset(&a, 0, sizeof(a));
+        a.model2d = p->model2d;
+        a.L = I.L; a.J = I.J; a.M = I.M; a.N = I.N;
+        a.Y = Y + I.koff; a.mask = mask + I.mkoff; a.a = aa; a.b = ab; a.K = K + I.koff;
+        a.da = I.da; a.db = I.db;
+        a.lambda = I.lambda;
+        a.beta = p->d.beta;
+        a.partial = p->partial + I.poff;
+        a.active = active;
+        a.status = p->status;
+        if ((e = launch_dc(a, st)) != cudaSuccess) return e;
+        if ((e = launch_rel_finalize(p->partial + I.poff, I.M, !p->model2d, p->d.tol, p->rel + i, active_next, st)) !=
+            cudaSuccess)
+            return e;
     }
-    DcArgs a;
-    memset(&a, 0, sizeof(a));
-    a.model2d = p->model2d;
-    a.L = p->L; a.J = p->J; a.M = p->M; a.N = p->N;
-    a.Y = Y; a.mask = mask; a.a = adj_a; a.b = adj_b; a.K = K;
-    a.da = p->da; a.db = p->db;
-    a.lambda = p->d.lambda;
-    a.beta = p->d.beta;
-    a.partial = p->partial;
-    a.active = active;
-    a.status = p->status;
-    if ((e = launch_dc(a, st)) != cudaSuccess) return e;
-    return launch_rel_finalize(p->partial, p->M, !p->model2d, p->d.tol, p->rel, active_next, st);
+    return cudaSuccess;
 }
 
 extern "C" selr_status selr_dc(selr_plan *p, const void *Y, const uint8_t *mask, void *adj_a, void *adj_b,
                                void *K, float *rel_out, selr_stream stream) {
     if (!p || !Y || !mask || !adj_a || !adj_b || !K) return SELR_ERR_INVALID_ARG;
+    if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     CK(dc_step(p, (const cf *)Y, mask, (cf *)adj_a, (cf *)adj_b, (cf *)K, nullptr, nullptr, st));
     if (rel_out) CK(cudaMemcpyAsync(rel_out, p->rel, sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -614,11 +737,12 @@ static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_
         case 1:
             return dc_step(p, Y, mask, p->adjA, p->adjB, p->K, act, act_next, st);
         case 2:
-            if (p->model2d) {
-                if ((e = transform(p, 0, 1, p->K, p->hybA, st)) != cudaSuccess) return e;
-                return transform(p, 1, 1, p->K, p->hybB, st);
+            for (int i = 0; i < p->n_inst; ++i) {
+                const long long o = p->inst[i].koff;
+                if (p->model2d && (e = transform(p, i, 0, 1, p->K + o, p->hybA + o, st)) != cudaSuccess) return e;
+                if ((e = transform(p, i, 1, 1, p->K + o, p->hybB + o, st)) != cudaSuccess) return e;
             }
-            return transform(p, 1, 1, p->K, p->hybB, st);
+            return cudaSuccess;
         case 3:
             if (plain) {
                 for (int m = 0; m < total; ++m) {
@@ -703,11 +827,12 @@ static cudaError_t admm_init(selr_plan *p, const cf *Y, cudaStream_t st) {
 
 static cudaError_t output_image(selr_plan *p, cf *X, cudaStream_t st) {
     cudaError_t e;
-    if (p->model2d) {
-        if ((e = transform(p, 1, 1, p->K, X, st)) != cudaSuccess) return e;
-        return transform(p, 0, 1, X, X, st);
+    for (int i = 0; i < p->n_inst; ++i) {
+        const long long o = p->inst[i].koff;
+        if ((e = transform(p, i, 1, 1, p->K + o, X + o, st)) != cudaSuccess) return e;
+        if (p->model2d && (e = transform(p, i, 0, 1, X + o, X + o, st)) != cudaSuccess) return e;
     }
-    return transform(p, 1, 1, p->K, X, st);
+    return cudaSuccess;
 }
 
 extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *mask, void *X_out,
@@ -761,12 +886,13 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
             }
             ++iters;
             if (!fixed) {
-                CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float), cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float) * p->n_inst, cudaMemcpyDeviceToHost, st));
                 if (!p->model2d) CK(cudaMemcpyAsync(p->h_active, p->active, sizeof(int) * p->M, cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
                 last_rel = p->h_rel[0];
+                for (int i = 1; i < p->n_inst; ++i) last_rel = fmaxf(last_rel, p->h_rel[i]);
                 if (p->model2d) {
-                    if (last_rel < p->d.tol) break;
+                    if (last_rel < p->d.tol) break;      // every instance meets the criterion
                 } else {
                     int any = 0;
                     for (int m = 0; m < p->M; ++m) any |= p->h_active[m];
@@ -779,9 +905,10 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
     CK(output_image(p, (cf *)X_out, st));
     if (rel_out || iters_out) {
         if (rel_out && fixed) {
-            CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float) * p->n_inst, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             last_rel = p->h_rel[0];
+            for (int i = 1; i < p->n_inst; ++i) last_rel = fmaxf(last_rel, p->h_rel[i]);
         }
         if (rel_out) *rel_out = last_rel;
         if (iters_out) *iters_out = iters;
@@ -938,12 +1065,13 @@ extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zba
 extern "C" selr_status selr_dc_vjp(selr_plan *p, const uint8_t *mask, const void *Kbar, void *adj_out, void *Ybar,
                                    selr_stream stream) {
     if (!p || !mask || !Kbar || !adj_out) return SELR_ERR_INVALID_ARG;
+    if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     DcArgs a;
     memset(&a, 0, sizeof(a));
     a.model2d = p->model2d;
     a.L = p->L; a.J = p->J; a.M = p->M; a.N = p->N;
     a.mask = mask;
-    a.da = p->da; a.db = p->db;
+    a.da = p->inst[0].da; a.db = p->inst[0].db;
     a.lambda = p->d.lambda;
     a.beta = p->d.beta;
     CK(launch_dc_vjp(a, (const cf *)Kbar, (cf *)adj_out, (cf *)Ybar, (cudaStream_t)stream));

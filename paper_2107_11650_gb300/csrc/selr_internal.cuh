@@ -24,7 +24,8 @@ __host__ __device__ __forceinline__ float cabs2(cf a) { return a.x * a.x + a.y *
 
 // --------------------------------------------------------------- lift groups
 enum { G_ROW = 0, G_COL = 1, G_PE = 2, G_PARAM = 3 };
-#define SELR_MAX_GROUPS 4
+#define SELR_MAX_INST 32                     // instances of one batched plan (2D models)
+#define SELR_MAX_GROUPS (2 * SELR_MAX_INST)  // lift families: two per instance
 
 // One family of lifted matrices (all rows, all columns, all PE or all
 // parameter lifts).  A matrix is rows x cols = (nv - p + 1) x (C * p).
@@ -45,6 +46,7 @@ struct Group {
     long long soff;        // offset of matrix 0 in per-vector arrays (sigma)
     long long poff;        // offset of matrix 0 in packed Gram storage (s (s+1) / 2 per matrix)
     int moff;              // index of matrix 0 among all matrices (status words)
+    int inst;              // instance of a batched plan the family belongs to
     const cf *w;           // weights (length nv) or nullptr (identity)
     const cf *src;         // lift source array
     cf *dst;               // adjoint destination array
@@ -58,12 +60,14 @@ struct GroupSet {
 };
 
 __device__ __forceinline__ int find_group(const GroupSet &gs, int mat_global, int *local) {
-    int gi = 0;
-#pragma unroll
-    for (int k = 1; k < SELR_MAX_GROUPS; ++k)
-        if (k < gs.n && mat_global >= gs.start[k]) gi = k;
-    *local = mat_global - gs.start[gi];
-    return gi;
+    int lo = 0, hi = gs.n - 1;           // last group whose start <= mat_global
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mat_global >= gs.start[mid]) lo = mid;
+        else hi = mid - 1;
+    }
+    *local = mat_global - gs.start[lo];
+    return lo;
 }
 
 // Address of element `pos` of the vector of coil j belonging to matrix `mat`.

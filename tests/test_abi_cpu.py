@@ -70,6 +70,27 @@ def test_descriptor_defaults(lib):
     assert ctypes.sizeof(_lib.SelrDesc) == 20 * 4
 
 
+def test_batch_descriptor_validation(lib):
+    """Batched plans: sizes and lambda may differ; everything else must agree; 2D models only."""
+    def create(descs):
+        arr = (_lib.SelrDesc * len(descs))(*descs)
+        h = ctypes.c_void_p()
+        code = lib.selr_plan_create_batch(arr, len(descs), ctypes.byref(h))
+        assert not h.value
+        return code
+    a = _desc(lib, J=2, M=64, N=64, window=70)          # shape error reported per description
+    assert create([_desc(lib), a]) == 2
+    assert create([_desc(lib), _desc(lib, beta=10.0)]) == 1
+    assert create([_desc(lib), _desc(lib, svd_method=1)]) == 1
+    assert create([_desc(lib, model=2, L=8, window_param=4), _desc(lib, model=2, L=8, window_param=4)]) == 7
+    h = ctypes.c_void_p()
+    assert lib.selr_plan_create_batch(None, 2, ctypes.byref(h)) == 1
+    arr = (_lib.SelrDesc * 1)(_desc(lib))
+    assert lib.selr_plan_create_batch(arr, 0, ctypes.byref(h)) == 1
+    assert lib.selr_plan_create_batch(arr, 33, ctypes.byref(h)) == 1
+    assert lib.selr_plan_instance_layout(None, 0, None, None) == 1
+
+
 def test_null_arguments(lib):
     assert lib.selr_plan_create(None, None) == 1
     assert lib.selr_plan_destroy(None) == 0
