@@ -56,6 +56,31 @@ __device__ __forceinline__ float wsum(float v) {
     return v;
 }
 
+// Block-wide maximum of one non-negative float (all threads get the result).
+__device__ float bmax(float v, float *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (l < EIG_WARPS) t = red[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    return t;
+}
+
+// Squared norm below which a Householder column counts as already reduced:
+// (eps max_i G_ii)^2 (G is positive semidefinite, so |G_ij| <= max_i G_ii), and
+// never below 1e-36 so that tau = 1 / (|x|^2 + |x| |x_0|) stays finite.  Rank-
+// deficient Gram matrices leave trailing columns of ~1e-20 whose squared norms
+// are denormal; dropping them perturbs T by less than eps ||G||.
+__device__ __forceinline__ float reflector_floor(float gmax) {
+    const float f = FLT_EPSILON * gmax;
+    return fmaxf(f * f, 1e-36f);
+}
+
 // Block-wide sum of one float (all threads get the result).
 __device__ float bsum(float v, float *red) {
     v = wsum(v);
@@ -280,6 +305,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     }
     for (long long i = tid; i < pk; i += EIG_THREADS) Gs[i] = Gglob[i];
     __syncthreads();
+    float gmax = 0.f;
+    for (int j = tid; j < n; j += EIG_THREADS) gmax = fmaxf(gmax, Gs[cst[j]].x);
+    const float floor2 = reflector_floor(bmax(gmax, red));
     cf vo[RPL], wo[RPL], vn[RPL];
 #pragma unroll
     for (int t = 0; t < RPL; ++t) vo[t] = wo[t] = vn[t] = mk(0.f, 0.f);
@@ -313,7 +341,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             const float rest = xn2 - ax0 * ax0;
             float tau = 0.f;
             cf alpha = x0, v0 = mk(0.f, 0.f);
-            if (rest > 1e-30f * xn2 && xn2 > 0.f) {
+            if (rest > 1e-30f * xn2 && xn2 > floor2) {
                 const float xnorm = sqrtf(xn2);
                 const cf phs = ax0 > 0.f ? mk(x0.x / ax0, x0.y / ax0) : mk(1.f, 0.f);
                 alpha = mk(-phs.x * xnorm, -phs.y * xnorm);
@@ -468,6 +496,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j = tid; j < n; j += EIG_THREADS) cst[j] = (int)colstart(j, n);
     __syncthreads();
+    float gmax = 0.f;
+    for (int j = tid; j < n; j += EIG_THREADS) gmax = fmaxf(gmax, Gs[cst[j]].x);
+    const float floor2 = reflector_floor(bmax(gmax, red));
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
         cf *col = Gs + cst[k] + 1;
@@ -479,7 +510,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
         const float rest = xn2 - ax0 * ax0;
         if (tid == 0) {
             td[k] = Gs[cst[k]].x;
-            if (!(rest > 1e-30f * xn2) || xn2 == 0.f) {
+            if (!(rest > 1e-30f * xn2) || !(xn2 > floor2)) {
                 s_tau = 0.f;
                 s_alpha = x0;
             } else {
