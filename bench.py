@@ -460,9 +460,11 @@ def run_unrolled(args, rank, world):
         out = torch.cat([loss.reshape(1), net.ts.grad, net.taus.grad]).cpu()
     e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0), world)
     units = len(wls) * n_iter
+    status = max(api.selr_sync_status(e.plan) for e in net.engines)
     if rank != 0:
         return None
     line = {
+        "status": status,
         "metric": "instance-iterations/s, forward + backward, 16 uneven unrolled SHLR instances",
         "value": whole_job_value(world, args.steps * units, ms), "unit": "instance-iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -541,7 +543,10 @@ def run_batch(args, rank, world):
     e1.record(stream)
     e1.synchronize()
     ms_single = max_over_ranks(e0.elapsed_time(e1), world)
-    diff = max(float((plan.unpack(Xp, i) - Xs[i]).abs().max() / Xs[i].abs().max()) for i in range(len(wls)))
+    # torch.max propagates NaN (a Python max over floats would not)
+    diff = float(torch.stack([(plan.unpack(Xp, i) - Xs[i]).abs().max() / Xs[i].abs().max()
+                              for i in range(len(wls))]).max())
+    st = max(st, max(api.selr_sync_status(sp, stream) for sp in singles))
     units = len(wls) * args.steps
     if rank != 0:
         return None
