@@ -14,15 +14,18 @@
 // and a.b ~ a_h.b_h + a_h.b_l + a_l.b_h, which recovers about FP32 accuracy
 // (the dropped a_l.b_l term is 2^-22 relative).
 //
-// Kernel.  One CTA (4 warps) per matrix, s <= 256.  Accumulators: D_re and
-// D_im, 128 lanes x N columns each (N = s rounded up to 16), in 2N <= 512
-// tensor-memory columns.  Rows are processed in M-tiles of 128; K in chunks of
-// 16 real elements, double-buffered in shared memory in the canonical K-major
-// layout without swizzle (core matrices of 8 rows x 16 bytes; LBO = 128 bytes
-// between core matrices along K, SBO = 512 bytes between 8-row groups).  All
-// threads convert and store a chunk; one thread issues the MMAs (M = 128,
-// N, K = 8) and commits them to the stage's mbarrier, which the threads wait on
-// before refilling that stage.  Every wait is bounded: on expiry the kernel
+// Kernel.  One CTA (4 warps) per matrix, s <= 256, N = s rounded up to 16.
+// s <= 192: one pass over K with two accumulator pairs in tensor memory,
+// rows 0..127 x N columns and rows 128.. x columns 128..N-1 (the block below
+// tile 0 is the conjugate transpose of tile 0's right part), 2N + 2(N - 128) <=
+// 512 columns.  s > 192: two passes (rows 0..127, then 128..255) against all N
+// columns.  K in chunks of 16 real elements, double-buffered in shared memory
+// in the canonical K-major layout without swizzle (core matrices of 8 rows x 16
+// bytes; LBO = 128 bytes between core matrices along K, SBO = 512 bytes between
+// 8-row groups).  Each thread converts 4-element quads (one 16-byte store per
+// tile) while its loads of the next chunk are in flight; one thread issues
+// the MMAs (M = 128, K = 8) and commits them to the stage's mbarrier, which
+// the threads wait on before refilling that stage.  Every wait is bounded: on expiry the kernel
 // sets ST_TIMEOUT, waits (bounded) for its MMAs in flight, frees its tensor
 // memory and returns.
 #include "selr_internal.cuh"
@@ -99,6 +102,42 @@ __device__ __forceinline__ bool gt_wait(uint32_t bar, uint32_t parity) {
     }
 }
 
+// 16-byte shared store of four 32-bit words.
+__device__ __forceinline__ void st4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// Reads 16 tensor-memory columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+// Issue the products of one K = 8 step into accumulator pair (dre, dim):
+// A rows at byte offset arow, B rows at brow, both tiles at k-offset ko.
+template <int MODE>
+__device__ __forceinline__ void gt_step(uint32_t dre, uint32_t dim, uint32_t idesc, uint32_t bxh, uint32_t bxl,
+                                        uint32_t byh, uint32_t byl, uint32_t arow, uint32_t brow, uint32_t ko,
+                                        uint32_t first) {
+    const uint64_t ah = gt_desc(bxh + arow + ko);
+    gt_mma(dre, ah, gt_desc(bxh + brow + ko), idesc, first);
+    gt_mma(dim, ah, gt_desc(byh + brow + ko), idesc, first);
+    if (MODE == 3) {
+        const uint64_t al = gt_desc(bxl + arow + ko);
+        gt_mma(dre, ah, gt_desc(bxl + brow + ko), idesc, 1u);
+        gt_mma(dim, ah, gt_desc(byl + brow + ko), idesc, 1u);
+        gt_mma(dre, al, gt_desc(bxh + brow + ko), idesc, 1u);
+        gt_mma(dim, al, gt_desc(byh + brow + ko), idesc, 1u);
+    }
+}
+
+#define GT_QPR (GT_KC / 4)                                   // 4-element quads per row and chunk
+#define GT_QPT (GT_TILE_ROWS * GT_QPR / GT_THREADS)          // quads per thread (8)
+
 template <int MODE>
 __global__ void __launch_bounds__(GT_THREADS, 1)
 k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, unsigned *status) {
@@ -116,7 +155,14 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
     const int n = g.s, len = g.len, K = 2 * len;
     const int N = (n + 15) & ~15;                  // MMA N (multiple of 16 for M = 128)
     const int nk = (K + GT_KC - 1) / GT_KC;
-    const int mtiles = (n + 127) / 128;
+    // N <= 192: one pass over K; tile 0 = rows 0..127 x all N columns, tile 1 = rows
+    // 128.. x columns 128..N-1 (its columns < 128 are the conjugates of tile 0's).
+    // N > 192: two passes, rows 0..127 then 128..255, each against all N columns.
+    const bool single = N <= 192;
+    const int npass = single ? 1 : 2;
+    const int N1 = (single && N > 128) ? N - 128 : 0;
+    const int rows = N > 128 ? 256 : 128;          // rows staged per chunk (zero beyond n)
+    const int nq = rows * GT_QPR;
     const float *X = (const float *)(B0 + g.off + (long long)mat * n * len);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
@@ -133,12 +179,31 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tm = tmem_base_s;
-    const uint32_t d_re = tm, d_im = tm + (uint32_t)N;
-    const uint32_t idesc = gt_idesc(128, N);
-    uint32_t waits[2] = {0u, 0u};                 // completed waits per stage (parity)
+    const uint32_t d0_re = tm, d0_im = tm + (uint32_t)N;
+    const uint32_t d1_re = tm + 2u * N, d1_im = tm + 2u * N + (uint32_t)N1;
+    const uint32_t idesc0 = gt_idesc(128, N), idesc1 = N1 ? gt_idesc(128, N1) : 0u;
+    const uint32_t rowgrp = GT_KC / 4 * 128;       // bytes per 8-row group (SBO)
+    uint32_t waits[2] = {0u, 0u};                  // completed waits per stage (parity)
     bool ok = true;
     cf *G = Gp + g.poff + (long long)mat * ((long long)n * (n + 1) / 2);
-    for (int mt = 0; mt < mtiles && ok; ++mt) {
+    float2 pa[GT_QPT], pb[GT_QPT];                 // prefetched quads of the next chunk
+    auto gload = [&](int kc) {
+#pragma unroll
+        for (int u = 0; u < GT_QPT; ++u) {
+            const int idx = tid + GT_THREADS * u;
+            const int r = idx / GT_QPR, q = idx - r * GT_QPR;
+            const int k = kc * GT_KC + 4 * q;
+            pa[u] = make_float2(0.f, 0.f);
+            pb[u] = make_float2(0.f, 0.f);
+            if (idx < nq && r < n) {
+                const float *xr = X + (long long)r * K;
+                if (k < K) pa[u] = *(const float2 *)(xr + k);
+                if (k + 2 < K) pb[u] = *(const float2 *)(xr + k + 2);
+            }
+        }
+    };
+    for (int pass = 0; pass < npass && ok; ++pass) {
+        gload(0);
         for (int kc = 0; kc < nk && ok; ++kc) {
             const int st = kc & 1;
             unsigned char *stage = gsm + st * GT_STAGE_BYTES;
@@ -148,55 +213,55 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
                 ++waits[st];
                 if (!__syncthreads_and(w_ok)) { ok = false; break; }
             }
-            // load, split and rotate chunk kc: complex pairs (k even)
-            uint32_t *xh = (uint32_t *)stage, *xl = (uint32_t *)(stage + GT_TILE_BYTES);
-            uint32_t *yh = (uint32_t *)(stage + 2 * GT_TILE_BYTES), *yl = (uint32_t *)(stage + 3 * GT_TILE_BYTES);
-            const int rows = mtiles * 128 > N ? mtiles * 128 : N;     // rows referenced by A and B
-            for (int idx = tid; idx < rows * (GT_KC / 2); idx += GT_THREADS) {
-                const int r = idx / (GT_KC / 2), kp = idx - r * (GT_KC / 2);
-                const int k = kc * GT_KC + 2 * kp;
-                float re = 0.f, im = 0.f;
-                if (r < n && k < K) {
-                    const float2 v = *(const float2 *)(X + (long long)r * K + k);
-                    re = v.x;
-                    im = v.y;
-                }
-                const uint32_t hre = to_tf32(re), him = to_tf32(im);
-                const uint32_t lre = MODE == 3 ? to_tf32(re - __uint_as_float(hre)) : 0u;
-                const uint32_t lim = MODE == 3 ? to_tf32(im - __uint_as_float(him)) : 0u;
-                const uint32_t o0 = gt_off(r, 2 * kp) >> 2, o1 = gt_off(r, 2 * kp + 1) >> 2;
-                xh[o0] = hre; xh[o1] = him;
-                yh[o0] = him; yh[o1] = hre ^ 0x80000000u;              // (Im, -Re)
+            float2 ca[GT_QPT], cb[GT_QPT];
+#pragma unroll
+            for (int u = 0; u < GT_QPT; ++u) { ca[u] = pa[u]; cb[u] = pb[u]; }
+            if (kc + 1 < nk) gload(kc + 1);            // next chunk's loads in flight meanwhile
+            const uint32_t bxh = smem_u32(stage), bxl = bxh + GT_TILE_BYTES;
+            const uint32_t byh = bxh + 2 * GT_TILE_BYTES, byl = bxh + 3 * GT_TILE_BYTES;
+#pragma unroll
+            for (int u = 0; u < GT_QPT; ++u) {
+                const int idx = tid + GT_THREADS * u;
+                if (idx >= nq) continue;
+                const int r = idx / GT_QPR, q = idx - r * GT_QPR;
+                const uint32_t off = gt_off(r, 4 * q);
+                // (re0, im0, re1, im1) and the rotation (im0, -re0, im1, -re1)
+                const uint32_t h0 = to_tf32(ca[u].x), h1 = to_tf32(ca[u].y);
+                const uint32_t h2 = to_tf32(cb[u].x), h3 = to_tf32(cb[u].y);
+                st4(bxh + off, h0, h1, h2, h3);
+                st4(byh + off, h1, h0 ^ 0x80000000u, h3, h2 ^ 0x80000000u);
                 if (MODE == 3) {
-                    xl[o0] = lre; xl[o1] = lim;
-                    yl[o0] = lim; yl[o1] = lre ^ 0x80000000u;
+                    const uint32_t l0 = to_tf32(ca[u].x - __uint_as_float(h0));
+                    const uint32_t l1 = to_tf32(ca[u].y - __uint_as_float(h1));
+                    const uint32_t l2 = to_tf32(cb[u].x - __uint_as_float(h2));
+                    const uint32_t l3 = to_tf32(cb[u].y - __uint_as_float(h3));
+                    st4(bxl + off, l0, l1, l2, l3);
+                    st4(byl + off, l1, l0 ^ 0x80000000u, l3, l2 ^ 0x80000000u);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t bxh = smem_u32(xh), bxl = smem_u32(xl), byh = smem_u32(yh), byl = smem_u32(yl);
-                const uint32_t arow = (uint32_t)(mt * 128 / 8) * (GT_KC / 4 * 128);   // A rows mt*128..
 #pragma unroll
                 for (int k8 = 0; k8 < GT_KC / 8; ++k8) {
-                    const uint32_t ko = (uint32_t)k8 * 2 * 128;                   // two core matrices
+                    const uint32_t ko = (uint32_t)k8 * 2 * 128;              // two core matrices along K
                     const uint32_t first = (kc == 0 && k8 == 0) ? 0u : 1u;
-                    const uint64_t ah = gt_desc(bxh + arow + ko), al = gt_desc(bxl + arow + ko);
-                    gt_mma(d_re, ah, gt_desc(bxh + ko), idesc, first);
-                    gt_mma(d_im, ah, gt_desc(byh + ko), idesc, first);
-                    if (MODE == 3) {
-                        gt_mma(d_re, ah, gt_desc(bxl + ko), idesc, 1u);
-                        gt_mma(d_im, ah, gt_desc(byl + ko), idesc, 1u);
-                        gt_mma(d_re, al, gt_desc(bxh + ko), idesc, 1u);
-                        gt_mma(d_im, al, gt_desc(byh + ko), idesc, 1u);
+                    if (single) {
+                        gt_step<MODE>(d0_re, d0_im, idesc0, bxh, bxl, byh, byl, 0u, 0u, ko, first);
+                        if (N1)
+                            gt_step<MODE>(d1_re, d1_im, idesc1, bxh, bxl, byh, byl, 16u * rowgrp, 16u * rowgrp, ko,
+                                          first);
+                    } else {
+                        gt_step<MODE>(d0_re, d0_im, idesc0, bxh, bxl, byh, byl, (uint32_t)pass * 16u * rowgrp, 0u,
+                                      ko, first);
                     }
                 }
                 gt_commit(smem_u32(&bars[st]));
             }
         }
         if (!ok) break;
-        // drain: the last one or two chunks of this M-tile
+        // drain: the last one or two chunks of this pass
         bool d_ok = true;
         for (int kc = nk >= 2 ? nk - 2 : 0; kc < nk; ++kc) {
             const int st = kc & 1;
@@ -205,33 +270,43 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
         }
         if (!__syncthreads_and(d_ok)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // accumulators -> packed lower triangle; thread owns row i, 16 columns per load
-        const int i = mt * 128 + warp * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
-        const int jmax = min(N, mt * 128 + 128);
-        for (int j0 = 0; j0 < jmax; j0 += 16) {
-            uint32_t vr[16], vi[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
-                  "=r"(vr[7]), "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]),
-                  "=r"(vr[14]), "=r"(vr[15])
-                : "r"(d_re + lane_addr + (uint32_t)j0));
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
-                  "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]),
-                  "=r"(vi[14]), "=r"(vi[15])
-                : "r"(d_im + lane_addr + (uint32_t)j0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (i < n) {
+        {
+            // tile 0 (single pass) or this pass's rows (two passes)
+            const int a = (single ? 0 : pass * 128) + warp * 32 + lane;
+            const int jmax = single ? N : min(N, pass * 128 + 128);
+            for (int j0 = 0; j0 < jmax; j0 += 16) {
+                uint32_t vr[16], vi[16];
+                tm_ld16(d0_re + lane_addr + (uint32_t)j0, vr);
+                tm_ld16(d0_im + lane_addr + (uint32_t)j0, vi);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (a < n) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int j = j0 + u;
-                    if (j <= i) G[(long long)j * (2 * n - j + 1) / 2 + (i - j)] =
-                        mk(__uint_as_float(vr[u]), __uint_as_float(vi[u]));
+                    for (int u = 0; u < 16; ++u) {
+                        const int c = j0 + u;                          // value = G(a, c)
+                        if (c >= n) continue;
+                        const float re = __uint_as_float(vr[u]), im = __uint_as_float(vi[u]);
+                        if (c <= a) G[(long long)c * (2 * n - c + 1) / 2 + (a - c)] = mk(re, im);
+                        else if (single) G[(long long)a * (2 * n - a + 1) / 2 + (c - a)] = mk(re, -im);
+                    }
+                }
+            }
+        }
+        if (single && N1) {
+            const int a = 128 + warp * 32 + lane;
+            for (int j0 = 0; j0 < N1; j0 += 16) {
+                uint32_t vr[16], vi[16];
+                tm_ld16(d1_re + lane_addr + (uint32_t)j0, vr);
+                tm_ld16(d1_im + lane_addr + (uint32_t)j0, vi);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (a < n) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int c = 128 + j0 + u;                    // value = G(a, c)
+                        if (c < n && c <= a)
+                            G[(long long)c * (2 * n - c + 1) / 2 + (a - c)] =
+                                mk(__uint_as_float(vr[u]), __uint_as_float(vi[u]));
+                    }
                 }
             }
         }
