@@ -174,6 +174,9 @@ def run_gpu(args, rank, world):
         with torch.cuda.stream(stream):
             api.selr_solve(plan, Y, mask, X, stream=stream)           # W warm-up iterations
         st = api.selr_sync_status(plan, stream)
+        if mode == "batched" and not args.no_autotune:
+            with torch.cuda.stream(stream):
+                results["tuning"] = plan.autotune(Y, mask, allow_tf32=args.allow_tf32, stream=stream)
         steps = args.steps if mode == "batched" else max(1, min(args.steps, args.plain_steps))
         plan.set_iterations(steps)
         plan.profile(True)
@@ -576,8 +579,10 @@ def main():
     ap.add_argument("--exec", default="both", choices=["both", "batched", "plain"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--svd", default="eig", choices=["eig", "jacobi"])
-    ap.add_argument("--gram", default="fp32", choices=["fp32", "tf32", "3xtf32"])
+    ap.add_argument("--gram", default="3xtf32", choices=["fp32", "tf32", "3xtf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--allow-tf32", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -612,7 +617,7 @@ def main():
         "config": {"workload": wl.name, "coils": wl.J, "size": [wl.M, wl.N], "window": wl.window,
                    "model": wl.model, "mask": f"{wl.mask} R={wl.R} acs={wl.n_acs}",
                    "matrices_per_step": b["nmat"], "exec": "batched (graph-captured)", "svd": args.svd,
-                   "gram": args.gram,
+                   "gram": (results.get("tuning") or {}).get("gram", args.gram),
                    "l2": "per-step state (D, E, work copies: 760 MB) exceeds L2; no flush"},
         "plain": ({"value": whole_job_value(world, results["plain"]["steps"], results["plain"]["ms"]),
                    "ms_per_step": results["plain"]["ms"] / results["plain"]["steps"],
@@ -631,6 +636,7 @@ def main():
         "clocks": b["clocks"],
         "status": b["status"],
         "accuracy": results.get("accuracy"),
+        "tuning": results.get("tuning"),
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)

@@ -241,6 +241,25 @@ selr_status selr_dc(selr_plan *plan, const void *Y, const uint8_t *mask, void *a
 selr_status selr_solve(selr_plan *plan, const void *Y, const uint8_t *mask, void *X_out,
                        int32_t *iters_out, float *rel_out, selr_stream stream);
 
+/* Autotuner (engineering extension, not in the paper): runs short solves
+ * (2 iterations each) of the caller's problem Y / mask (as for selr_solve;
+ * X_scratch receives throw-away images) and keeps the fastest settings in the
+ * plan: with SELR_SVD_EIG the Gram precision among the modes of FP32-level
+ * accuracy (SELR_GRAM_FP32, SELR_GRAM_3XTF32; also SELR_GRAM_TF32 when
+ * flags & 1) and the number of eigenvectors refined per inverse-iteration
+ * pass (8 or 16); with SELR_SVD_JACOBI the sweep cap (twice the largest
+ * number of sweeps a matrix needed, + 2, if below the current cap and no
+ * matrix reached it).
+ * max_iter, tol and profiling are restored afterwards; cached CUDA graphs are
+ * dropped.  Synchronises the stream. */
+selr_status selr_plan_autotune(selr_plan *plan, const void *Y, const uint8_t *mask, void *X_scratch,
+                               int32_t flags, selr_stream stream);
+
+/* Settings in force (host outputs, any may be NULL): Gram precision, inverse-
+ * iteration chunk (0 = chosen by order), Jacobi sweep cap. */
+selr_status selr_plan_tuning(const selr_plan *plan, int32_t *gram_precision, int32_t *ev_chunk,
+                             int32_t *jacobi_max_sweeps);
+
 /* Change the iteration cap and stopping tolerance of an existing plan
  * (same meaning as selr_desc.max_iter / tol).  SELR_ERR_INVALID_ARG if
  * max_iter < 1. */

@@ -118,6 +118,23 @@ class Plan:
         check(self.lib.selr_set_iterations(self.handle, int(max_iter), float(tol)), "selr_set_iterations")
         self.desc.max_iter, self.desc.tol = int(max_iter), float(tol)
 
+    def autotune(self, Y, mask, allow_tf32=False, stream=None):
+        """selr_plan_autotune on (Y, mask); returns the settings in force."""
+        X = torch.empty_like(Y)
+        nm = mask.numel()
+        check(self.lib.selr_plan_autotune(self.handle, _ptr(Y, torch.complex64, "Y", self.nK),
+                                          _ptr(mask, torch.uint8, "mask", nm),
+                                          _ptr(X, torch.complex64, "X", self.nK), 1 if allow_tf32 else 0,
+                                          _stream(stream)), "selr_plan_autotune")
+        return self.tuning()
+
+    def tuning(self):
+        g, c, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(self.lib.selr_plan_tuning(self.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(w)),
+              "selr_plan_tuning")
+        names = {v: k for k, v in GRAM.items()}
+        return {"gram": names.get(g.value, g.value), "ev_chunk": c.value, "jacobi_max_sweeps": w.value}
+
     STAGES = ("adjoint", "dc", "hybrid_fft", "lift", "gram", "svd", "apply")
 
     def profile(self, on=True):

@@ -62,6 +62,8 @@ struct selr_plan {
     float *gw_lam, *gw_tri, *gw_zs;
     int *gw_rank;
     double *gw_tpart;
+    int ev_chunk;              // tuned inverse-iteration chunk (0: by order)
+    int tuned;                 // selr_plan_autotune ran
     double *gw_part;
 };
 
@@ -581,6 +583,7 @@ static EigArgs eig_args(selr_plan *p, const int *active) {
     e.tri = p->tri;
     e.active = active;
     e.status = p->status;
+    e.ev_chunk = p->ev_chunk;
     return e;
 }
 
@@ -1091,6 +1094,105 @@ extern "C" selr_status selr_dot_re(selr_plan *p, int64_t n, const void *x, const
     selr_status ws = grad_workspace(p);
     if (ws != SELR_OK) return ws;
     CK(launch_dot_re(n, (const cf *)x, (const cf *)y, p->gw_part, out, (cudaStream_t)stream));
+    return SELR_OK;
+}
+
+// ---------------------------------------------------------------- autotuning
+// Times a short solve (2 iterations, graph-captured when the plan is batched and
+// the stream is not the legacy default stream) for every candidate setting on
+// the caller's own data and keeps the fastest: the Gram precision among those
+// with FP32-level accuracy (FP32, 3xTF32; one-pass TF32 only if flags bit 0),
+// the inverse-iteration chunk (8 or 16 vectors per pass), and for the Jacobi
+// method the sweep cap (twice the largest number of sweeps any matrix needed, + 2).
+static selr_status time_solve(selr_plan *p, const void *Y, const uint8_t *mask, void *X, cudaStream_t st,
+                              float *ms) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SELR_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return SELR_ERR_CUDA; }
+    selr_status s = selr_solve(p, Y, mask, X, nullptr, nullptr, (selr_stream)st);       // warm / capture
+    float best = 3.4e38f;
+    for (int rep = 0; rep < 2 && s == SELR_OK; ++rep) {
+        if (cudaEventRecord(e0, st) != cudaSuccess) { s = SELR_ERR_CUDA; break; }
+        s = selr_solve(p, Y, mask, X, nullptr, nullptr, (selr_stream)st);
+        if (s != SELR_OK) break;
+        float t = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) { s = SELR_ERR_CUDA; break; }
+        best = t < best ? t : best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return s;
+}
+
+extern "C" selr_status selr_plan_autotune(selr_plan *p, const void *Y, const uint8_t *mask, void *X_scratch,
+                                          int32_t flags, selr_stream stream) {
+    if (!p || !Y || !mask || !X_scratch) return SELR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int max_iter = p->d.max_iter;
+    const float tol = p->d.tol;
+    const int prof = p->prof_on;
+    p->d.max_iter = 2;
+    p->d.tol = -1.f;
+    p->prof_on = 0;
+    drop_graphs(p);
+    selr_status s = SELR_OK;
+    if (p->d.svd_method == SELR_SVD_JACOBI) {
+        // sweep cap from the sweeps the matrices actually needed in two iterations
+        s = selr_solve(p, Y, mask, X_scratch, nullptr, nullptr, stream);
+        if (s == SELR_OK) {
+            int *h = (int *)malloc(sizeof(int) * (size_t)p->gs.total);
+            if (!h) s = SELR_ERR_ALLOC;
+            else {
+                if (cudaMemcpy(h, p->mat_status, sizeof(int) * (size_t)p->gs.total, cudaMemcpyDeviceToHost) !=
+                    cudaSuccess)
+                    s = SELR_ERR_CUDA;
+                int mx = 0;
+                bool capped = false;
+                for (int i = 0; s == SELR_OK && i < p->gs.total; ++i) {
+                    if (h[i] < 0) capped = true;
+                    mx = h[i] > mx ? h[i] : mx;
+                }
+                // later iterations start further from convergence than none, but keep a margin
+                if (s == SELR_OK && !capped && mx > 0 && 2 * mx + 2 < p->d.jacobi_max_sweeps)
+                    p->d.jacobi_max_sweeps = 2 * mx + 2;
+                free(h);
+            }
+        }
+    } else {
+        int grams[3] = {SELR_GRAM_FP32, SELR_GRAM_3XTF32, SELR_GRAM_TF32};
+        const int ngram = (flags & 1) ? 3 : 2;
+        const int chunks[2] = {16, 8};
+        float best = 3.4e38f;
+        int bg = p->d.gram_precision, bc = p->ev_chunk;
+        for (int gi = 0; gi < ngram && s == SELR_OK; ++gi) {
+            for (int ci = 0; ci < 2 && s == SELR_OK; ++ci) {
+                p->d.gram_precision = grams[gi];
+                p->ev_chunk = chunks[ci];
+                drop_graphs(p);
+                float ms = 0.f;
+                s = time_solve(p, Y, mask, X_scratch, st, &ms);
+                if (s == SELR_OK && ms < best) { best = ms; bg = grams[gi]; bc = chunks[ci]; }
+            }
+        }
+        p->d.gram_precision = bg;
+        p->ev_chunk = bc;
+    }
+    drop_graphs(p);
+    p->d.max_iter = max_iter;
+    p->d.tol = tol;
+    p->prof_on = prof;
+    if (s == SELR_OK) p->tuned = 1;
+    return s;
+}
+
+extern "C" selr_status selr_plan_tuning(const selr_plan *p, int32_t *gram_precision, int32_t *ev_chunk,
+                                        int32_t *jacobi_max_sweeps) {
+    if (!p) return SELR_ERR_INVALID_ARG;
+    if (gram_precision) *gram_precision = p->d.gram_precision;
+    if (ev_chunk) *ev_chunk = p->ev_chunk;
+    if (jacobi_max_sweeps) *jacobi_max_sweeps = p->d.jacobi_max_sweeps;
     return SELR_OK;
 }
 

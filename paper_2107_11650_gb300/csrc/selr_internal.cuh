@@ -172,6 +172,7 @@ struct EigArgs {
     float *zsave;        // non-null: keep the tridiagonal-basis eigenvectors of the computed
                          // pairs here ([mat] at g.off + mat s len, row q = pair q)
     int allp;            // compute every eigenpair, not only those above t^2 (needs zsave)
+    int ev_chunk;        // inverse-iteration vectors per pass: 16 or 8 (0: by order)
 };
 cudaError_t eig_init_attributes();
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,

@@ -1370,7 +1370,8 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // 2. eigenpairs above t^2 and back-transformation
-    const int chunk = ev_chunk(nmax);
+    int chunk = ea.ev_chunk == 8 || ea.ev_chunk == 16 ? ea.ev_chunk : ev_chunk(nmax);
+    if (chunk == 16 && nmax > 352) chunk = 8;         // the 16-vector layout exceeds shared memory
     size_t smem = 0;
     for (int k = 0; k < gs.n; ++k) smem = max(smem, ev_layout(gs.g[k].s, chunk, chunk + 1).total);
     if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;

@@ -87,3 +87,30 @@ def test_solve_gram_precision(gram):
     err = rel_l2(X.cpu().numpy().astype(np.complex128), ref)
     assert err <= (1e-4 if gram == "3xtf32" else 5e-3), err
     plan.close()
+
+
+@pytest.mark.parametrize("svd", ["eig", "jacobi"])
+def test_autotune_keeps_accuracy(svd):
+    """The autotuner only chooses among settings of FP32-level accuracy (unless
+    TF32 is allowed): after tuning, a 30-iteration solve still meets 1e-4."""
+    api = _api()
+    cfg = get_config("shlr_4c_64")
+    inp = synth.make_inputs(cfg)
+    plan = api.Plan(api.Desc.from_workload(cfg, svd=svd))
+    Y = torch.from_numpy(inp["Y"].astype(np.complex64)).cuda()
+    mask = torch.from_numpy(inp["mask"]).cuda()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        t = plan.autotune(Y, mask, stream=s)
+    if svd == "eig":
+        assert t["gram"] in ("fp32", "3xtf32") and t["ev_chunk"] in (8, 16)
+    else:
+        assert 2 <= t["jacobi_max_sweeps"] <= 30
+    assert plan.desc.max_iter == 30
+    X = torch.empty_like(Y)
+    with torch.cuda.stream(s):
+        it, _ = api.selr_solve(plan, Y, mask, X, stream=s)
+    assert it == 30 and api.selr_sync_status(plan, s) == 0
+    ref = oadmm.shlr(inp["Y"], inp["mask"], cfg, n_iter=30)[0]
+    assert rel_l2(X.cpu().numpy().astype(np.complex128), ref) <= 1e-4
+    plan.close()
