@@ -45,6 +45,7 @@
 #define EIG_SMEM_MAX_N 208       // packed G of order <= 208 stays in shared memory
 #define INV_ITERS 4
 #define EV_HB 8                  // Householder reflectors staged per back-transformation batch
+#define TB 4                     // trailing columns per pass of the tridiagonal sweep (8 sums per reduction)
 
 __device__ __forceinline__ long long colstart(int j, int n) { return (long long)j * (2 * n - j + 1) / 2; }
 
@@ -381,33 +382,71 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
         cf pa[RPL];
 #pragma unroll
         for (int t = 0; t < RPL; ++t) pa[t] = mk(0.f, 0.f);
-        for (int j = k + 1 + warp; j < n; j += EIG_WARPS) {
-            const cf voj = vp[j], woj = wp[j], vnj = vb[j];
-            const int base = cst[j] - j;
-            float cr = 0.f, ci = 0.f;
+        // TB columns per pass (j, j + 16, ...): their 2 TB column sums are reduced together
+        // by a transpose-reduce butterfly (9 shuffles instead of 10 TB)
+        for (int j0 = k + 1 + warp; j0 < n; j0 += TB * EIG_WARPS) {
+            float acc[2 * TB];
 #pragma unroll
-            for (int t = 0; t < RPL; ++t) {
-                if (32 * t + 31 >= j && 32 * t < n) {           // warp-uniform: slot t has rows >= j
-                    const int i = lane + 32 * t;
-                    if (i >= j && i < n) {
-                        cf gv = Gs[base + i];
-                        if (upd) {
-                            gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
-                            gv.y -= vo[t].y * woj.x - vo[t].x * woj.y + wo[t].y * voj.x - wo[t].x * voj.y;
-                            Gs[base + i] = gv;
-                        }
-                        pa[t].x += gv.x * vnj.x - gv.y * vnj.y;
-                        pa[t].y += gv.x * vnj.y + gv.y * vnj.x;
-                        if (i > j) {                           // conj(G(i,j)) v_i -> p_j
-                            cr += gv.x * vn[t].x + gv.y * vn[t].y;
-                            ci += gv.x * vn[t].y - gv.y * vn[t].x;
+            for (int c = 0; c < TB; ++c) {
+                const int j = j0 + c * EIG_WARPS;
+                float cr = 0.f, ci = 0.f;
+                if (j < n) {                                       // warp-uniform
+                    const cf voj = vp[j], woj = wp[j], vnj = vb[j];
+                    const int base = cst[j] - j;
+#pragma unroll
+                    for (int t = 0; t < RPL; ++t) {
+                        if (32 * t + 31 >= j && 32 * t < n) {       // warp-uniform: slot t has rows >= j
+                            const int i = lane + 32 * t;
+                            if (i >= j && i < n) {
+                                cf gv = Gs[base + i];
+                                if (upd) {
+                                    gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
+                                    gv.y -= vo[t].y * woj.x - vo[t].x * woj.y + wo[t].y * voj.x - wo[t].x * voj.y;
+                                    Gs[base + i] = gv;
+                                }
+                                pa[t].x += gv.x * vnj.x - gv.y * vnj.y;
+                                pa[t].y += gv.x * vnj.y + gv.y * vnj.x;
+                                if (i > j) {                       // conj(G(i,j)) v_i -> p_j
+                                    cr += gv.x * vn[t].x + gv.y * vn[t].y;
+                                    ci += gv.x * vn[t].y - gv.y * vn[t].x;
+                                }
+                            }
                         }
                     }
                 }
+                acc[2 * c] = cr;
+                acc[2 * c + 1] = ci;
             }
-            cr = wsum(cr);
-            ci = wsum(ci);
-            if (lane == 0) Cs[j] = mk(cr, ci);
+            // butterfly: after the halving steps lane L holds value 4 b4 + 2 b3 + b2 (bits of L)
+            // summed over its 8-lane group; the last two steps complete the sum
+            float b4v[4], b3v[2], s1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool hi = lane & 16;
+                const float send = hi ? acc[q] : acc[q + 4];
+                const float keep = hi ? acc[q + 4] : acc[q];
+                b4v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const bool hi = lane & 8;
+                const float send = hi ? b4v[q] : b4v[q + 2];
+                const float keep = hi ? b4v[q + 2] : b4v[q];
+                b3v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+            {
+                const bool hi = lane & 4;
+                const float send = hi ? b3v[0] : b3v[1];
+                const float keep = hi ? b3v[1] : b3v[0];
+                s1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+            if ((lane & 3) == 0) {
+                const int v = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                const int j = j0 + (v >> 1) * EIG_WARPS;
+                if (j < n) ((float *)Cs)[2 * j + (v & 1)] = s1;
+            }
         }
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
