@@ -471,7 +471,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
         float kv = 0.f;
 #pragma unroll
         for (int w2 = 0; w2 < EIG_WARPS; ++w2) kv += red[w2];
-        const float K = 0.5f * tau * tau * kv;
+        // tau kv = Re(v^H p) <= 2 ||G|| is bounded; tau alone can be ~1e36 for tiny columns,
+        // so tau^2 must not be formed
+        const float K = 0.5f * tau * (tau * kv);
         const int i3 = k + 1 + tid;
         if (i3 < n) {
             float sr = Cs[i3].x, si = Cs[i3].y;
