@@ -315,10 +315,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     float tau_old = 0.f;
     cf *vb = vbuf0, *vp = vbuf1, *wb = wbuf0, *wp = wbuf1;
     for (int k = 0; k + 2 < n; ++k) {
-        // ---- 1. column k and the reflector, computed identically by every warp (registers
-        //         only: column k is not written back, nobody reads it again); warp 0 publishes
-        float tau;
-        {
+        // ---- 1. column k and the reflector (warp 0)
+        if (warp == 0) {
             const cf vk = vp[k], wk = wp[k];
             cf colv[RPL];
             float xn2 = 0.f;
@@ -332,6 +330,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                     if (tau_old != 0.f) {
                         gv.x -= vo[t].x * wk.x + vo[t].y * wk.y + wo[t].x * vk.x + wo[t].y * vk.y;
                         gv.y -= vo[t].y * wk.x - vo[t].x * wk.y + wo[t].y * vk.x - wo[t].x * vk.y;
+                        Gs[ck + i - k] = gv;
                     }
                     colv[t] = gv;
                     if (i > k) xn2 += cabs2(gv);
@@ -339,10 +338,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             }
             xn2 = wsum(xn2);
             const cf x0 = shfl_cf(pick(colv, (k + 1) >> 5), (k + 1) & 31);
-            const cf dk = shfl_cf(pick(colv, k >> 5), k & 31);
             const float ax0 = sqrtf(cabs2(x0));
             const float rest = xn2 - ax0 * ax0;
-            tau = 0.f;
+            float tau = 0.f;
             cf alpha = x0, v0 = mk(0.f, 0.f);
             if (rest > 1e-30f * xn2 && xn2 > floor2) {
                 const float xnorm = sqrtf(xn2);
@@ -355,41 +353,45 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
 #pragma unroll
             for (int t = 0; t < RPL; ++t) {
                 const int i = lane + 32 * t;
-                cf v = mk(0.f, 0.f);
-                if (32 * t < n && i >= k + 1 && i < n) v = tau == 0.f ? mk(0.f, 0.f) : (i == k + 1 ? v0 : colv[t]);
-                vn[t] = v;
-                if (warp == 0 && 32 * t < n) {
-                    if (i >= k + 1 && i < n) hv[i - k - 1] = v;
-                    if (i < n) vb[i] = v;                     // read in phase 3 only
+                if (32 * t < n) {
+                    cf v = mk(0.f, 0.f);
+                    if (i >= k + 1 && i < n) {
+                        v = tau == 0.f ? mk(0.f, 0.f) : (i == k + 1 ? v0 : colv[t]);
+                        hv[i - k - 1] = v;
+                    }
+                    if (i < n) vb[i] = v;
                 }
             }
-            if (warp == 0 && lane == 0) {
+            __syncwarp();
+            if (lane == 0) {
+                s_tau = tau;
                 ttau[k] = tau;
                 te[k] = alpha;
-                td[k] = dk.x;
+                td[k] = Gs[ck].x;
             }
         }
-        // ---- 2. fused update + symv over the trailing columns; each warp also forms its
-        //         share of v^H p (its row partials and its column sums) for K
+        __syncthreads();
+        const float tau = s_tau;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            vn[t] = (i < n) ? vb[i] : mk(0.f, 0.f);
+        }
+        // ---- 2. fused update + symv over the trailing columns
         const bool upd = tau_old != 0.f;
         cf pa[RPL];
 #pragma unroll
         for (int t = 0; t < RPL; ++t) pa[t] = mk(0.f, 0.f);
-        float kcol = 0.f;                                      // sum over this warp's columns of Re(conj(v_j) C_j)
         // TB columns per pass (j, j + 16, ...): their 2 TB column sums are reduced together
         // by a transpose-reduce butterfly (9 shuffles instead of 10 TB)
         for (int j0 = k + 1 + warp; j0 < n; j0 += TB * EIG_WARPS) {
             float acc[2 * TB];
-            cf vnjs[TB];
 #pragma unroll
             for (int c = 0; c < TB; ++c) {
                 const int j = j0 + c * EIG_WARPS;
                 float cr = 0.f, ci = 0.f;
-                vnjs[c] = mk(0.f, 0.f);
                 if (j < n) {                                       // warp-uniform
-                    const cf voj = vp[j], woj = wp[j];
-                    const cf vnj = shfl_cf(pick(vn, j >> 5), j & 31);
-                    vnjs[c] = vnj;
+                    const cf voj = vp[j], woj = wp[j], vnj = vb[j];
                     const int base = cst[j] - j;
 #pragma unroll
                     for (int t = 0; t < RPL; ++t) {
@@ -442,38 +444,19 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
             if ((lane & 3) == 0) {
                 const int v = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                const int c = v >> 1;
-                const int j = j0 + c * EIG_WARPS;
-                if (j < n) {
-                    ((float *)Cs)[2 * j + (v & 1)] = s1;
-                    // Re(conj(v_j) C_j) = v_j.x C_j.x + v_j.y C_j.y: this lane holds one of the two parts
-                    cf vj = vnjs[0];
-#pragma unroll
-                    for (int u = 1; u < TB; ++u)
-                        if (u == c) vj = vnjs[u];
-                    kcol += (v & 1) ? vj.y * s1 : vj.x * s1;
-                }
+                const int j = j0 + (v >> 1) * EIG_WARPS;
+                if (j < n) ((float *)Cs)[2 * j + (v & 1)] = s1;
             }
         }
-        float kpart = kcol;
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
-            if (32 * t < n && i >= k + 1 && i < n) {
-                Pw[(long long)warp * n + i] = pa[t];
-                kpart += vn[t].x * pa[t].x + vn[t].y * pa[t].y;
-            }
+            if (32 * t < n && i >= k + 1 && i < n) Pw[(long long)warp * n + i] = pa[t];
         }
-        kpart = wsum(kpart);
-        if (lane == 0) red[warp] = kpart;
         __syncthreads();
-        // ---- 3. p = tau * (row partials + column sum), K = tau/2 Re(v^H p), w = p - K v
+        // ---- 3. p = tau * (row partials + column sum), K, w (all threads)
+        cf pi = mk(0.f, 0.f), vi = mk(0.f, 0.f);
         float kv = 0.f;
-#pragma unroll
-        for (int w2 = 0; w2 < EIG_WARPS; ++w2) kv += red[w2];
-        // tau kv = Re(v^H p) <= 2 ||G|| is bounded; tau alone can be ~1e36 for tiny columns,
-        // so tau^2 must not be formed
-        const float K = 0.5f * tau * (tau * kv);
         const int i3 = k + 1 + tid;
         if (i3 < n) {
             float sr = Cs[i3].x, si = Cs[i3].y;
@@ -482,9 +465,13 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                 sr += q.x;
                 si += q.y;
             }
-            const cf vi = vb[i3];
-            wb[i3] = mk(tau * sr - K * vi.x, tau * si - K * vi.y);
+            pi = mk(tau * sr, tau * si);
+            vi = vb[i3];
+            kv = vi.x * pi.x + vi.y * pi.y;
         }
+        kv = bsum(kv, red);
+        const float K = 0.5f * tau * kv;
+        if (i3 < n) wb[i3] = mk(pi.x - K * vi.x, pi.y - K * vi.y);
         if (tid <= k && tid < n) wb[tid] = mk(0.f, 0.f);
         __syncthreads();
 #pragma unroll
