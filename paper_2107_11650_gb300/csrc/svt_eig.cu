@@ -640,8 +640,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
 // synchronises before using the outputs.
 __device__ __forceinline__ void tri_real_setup(const float *td, const float *ttau, const cf *te, int n, float *dd,
                                                float *taus, float *ff, float *f2, cf *ph, int tid, int lane,
-                                               int warp) {
-    for (int k = tid; k < n; k += EIG_THREADS) {
+                                               int warp, int nthreads = EIG_THREADS) {
+    for (int k = tid; k < n; k += nthreads) {
         dd[k] = td[k];
         taus[k] = ttau[k];
         const float ae = k + 1 < n ? sqrtf(cabs2(te[k])) : 0.f;
@@ -721,8 +721,9 @@ __host__ __device__ inline EvLayout ev_layout(int n, int chunk, int st) {
 // are interleaved with the odd stride IV_ST (> IV_CHUNK) so that both the
 // thread-per-vector solves and the warp-per-vector reductions avoid bank
 // conflicts.
-template <int IV_CHUNK, int IV_ST>
-__global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_begin, EigArgs a) {
+template <int IV_CHUNK, int IV_ST, int NT>
+__global__ void __launch_bounds__(NT) k_eigvec(GroupSet gs, int mat_begin, EigArgs a) {
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char vsm[];
     __shared__ float red[4];
     __shared__ int s_r, s_cst, s_wend;
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
     float *lam_out = a.lam + g.soff + (long long)mat * n;
     cf *V = a.V + g.off + (long long)mat * n * g.len;
     int *rank_out = a.rank + g.moff + mat;
-    tri_real_setup(td, ttau, te, n, dd, taus, ff, f2, ph, tid, lane, warp);
+    tri_real_setup(td, ttau, te, n, dd, taus, ff, f2, ph, tid, lane, warp, NT);
     __syncthreads();
     if (tid == 0) {
         float gl, gu, pivmin;
@@ -766,7 +767,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
     const int r = s_r;
     if (tid == 0) *rank_out = r;
     if (r == 0) return;
-    for (int q = warp; q < r; q += EIG_WARPS) {
+    for (int q = warp; q < r; q += NW) {
         const int j = n - 1 - q;
         float lo = fmaxf(gl, t2), hi = gu;
         hi = hi + 2.f * FLT_EPSILON * fabsf(hi) + pivmin;
@@ -793,10 +794,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
         }
     }
     __syncthreads();
-    for (int q = tid; q < r; q += EIG_THREADS) lam_out[q] = lamv[q];
+    for (int q = tid; q < r; q += NT) lam_out[q] = lamv[q];
     for (int q0 = 0; q0 < r; q0 += IV_CHUNK) {
         const int qc = min(IV_CHUNK, r - q0);
-        for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
+        for (int idx = tid; idx < qc * n; idx += NT) {
             const int q = idx / n, i = idx - q * n;
             zv[i * IV_ST + q] = 1.f + 0.25f * (float)(((i * 7919 + (q0 + q) * 104729) % 997) - 498) / 498.f;
         }
@@ -818,7 +819,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
                                  lpv + tid, FLT_EPSILON * tnorm + pivmin, it == 0);
             __syncthreads();
             if (allp && s_cst < q0) {
-                for (int w = warp; w < s_wend; w += EIG_WARPS) {
+                for (int w = warp; w < s_wend; w += NW) {
                     for (int pass = 0; pass < 2; ++pass) {
                         for (int o = s_cst; o < q0; ++o) {
                             const float *zo = zs + (long long)o * n;
@@ -832,7 +833,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
                 }
                 __syncthreads();
             }
-            for (int w = warp; w < qc; w += EIG_WARPS) {
+            for (int w = warp; w < qc; w += NW) {
                 if (!(w == 0 || clu[q0 + w])) continue;
                 int end = w + 1;
                 while (end < qc && !clu[q0 + end]) ++end;
@@ -855,13 +856,13 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
             __syncthreads();
         }
         if (zs) {
-            for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
+            for (int idx = tid; idx < qc * n; idx += NT) {
                 const int w = idx / n, i = idx - w * n;
                 zs[(long long)(q0 + w) * n + i] = zv[i * IV_ST + w];
             }
         }
         // back-transformation y = Q P z, reflectors applied for k = n-3 .. 0 in batches of EV_HB
-        for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
+        for (int idx = tid; idx < qc * n; idx += NT) {
             const int w = idx / n, i = idx - w * n;
             Yc[idx] = cscale(ph[i], zv[i * IV_ST + w]);
         }
@@ -873,10 +874,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
                 const int k = kb - b;
                 const int m = n - k - 1;
                 const cf *hv = Gglob + colstart(k, n) + 1;
-                for (int i = tid; i < m; i += EIG_THREADS) hb[(long long)b * n + i] = hv[i];
+                for (int i = tid; i < m; i += NT) hb[(long long)b * n + i] = hv[i];
             }
             __syncthreads();
-            for (int w = warp; w < qc; w += EIG_WARPS) {
+            for (int w = warp; w < qc; w += NW) {
                 for (int b = 0; b < nbat; ++b) {
                     const int k = kb - b;
                     const float tau = taus[k];
@@ -902,7 +903,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigvec(GroupSet gs, int mat_beg
             }
             __syncthreads();
         }
-        for (int idx = tid; idx < qc * n; idx += EIG_THREADS) {
+        for (int idx = tid; idx < qc * n; idx += NT) {
             const int w = idx / n, i = idx - w * n;
             const cf y = Yc[idx];
             if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(a.status, (unsigned)ST_NONFINITE);
@@ -1355,8 +1356,8 @@ cudaError_t eig_init_attributes() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag_g, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<16, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<8, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<16, 17, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<8, 9, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e != cudaSuccess) return e;
@@ -1414,8 +1415,9 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
     size_t smem = 0;
     for (int k = 0; k < gs.n; ++k) smem = max(smem, ev_layout(gs.g[k].s, chunk, chunk + 1).total);
     if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
-    if (chunk == 16) k_eigvec<16, 17><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea);
-    else k_eigvec<8, 9><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea);
+    // chunk 16: 512 threads; chunk 8: 256 threads (smaller CTAs, more matrices in flight per SM)
+    if (chunk == 16) k_eigvec<16, 17, 512><<<mat_count, 512, smem, st>>>(gs, mat_begin, ea);
+    else k_eigvec<8, 9, 256><<<mat_count, 256, smem, st>>>(gs, mat_begin, ea);
     return cudaGetLastError();
 }
 
