@@ -1105,14 +1105,15 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
 // ----------------------------------------------------------------- apply
 // k_apply_stream: the apply for matrices with r <= AS_CH pairs above t^2 (the
 // usual case on the lifted matrices).  CTA = (matrix, tile of AS_ET rows of B);
-// phase 1: Y[e][k] = h_k sum_c B[e][c] v_k[c] (warp = slice of c, lane = e, 16 pairs at
-// a time, partial sums over the slices added in shared memory),
+// phase 1: Y[e][k] = h_k sum_c B[e][c] v_k[c], lane = e; for r <= AS_SMALL the warps
+// split the rows c (partial sums reduced in a fixed order), otherwise they split the
+// pairs k (one writer per entry), so the result is bitwise reproducible;
 // phase 2: Z[e][c] = sum_k Y[e][k] conj(v_k[c]) streamed over c with the
 // epilogue (Z out, or D and E update) fused, B re-read from L1/L2.  No large
 // per-thread arrays, so occupancy (and with it memory parallelism) is high.
 #define AS_ET 32
-#define AS_CH 32          // pairs handled by the streaming apply (phase 1 in halves of 16)
-#define AS_HALF 16
+#define AS_CH 32          // pairs handled by the streaming apply
+#define AS_SMALL 8        // up to this many pairs phase 1 splits the rows of B over the warps
 #define AS_THREADS 256
 __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int mat_begin, EigArgs ea, SvtArgs a) {
     extern __shared__ cf ssm[];
@@ -1129,64 +1130,84 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
     const long long mb = g.off + (long long)mat * n * len;
     if (blockIdx.y == 0 && threadIdx.x == 0 && a.rank_out) a.rank_out[g.moff + mat] = r;
     const float t = g.thresh;
-    cf *Vs = ssm;                          // [AS_CH][n]
-    cf *Ys = ssm + (long long)AS_CH * n;   // [AS_ET][AS_CH + 1]
-    const cf *V = ea.V + mb;
+    cf *Ys = ssm;                          // [AS_ET][AS_CH + 1]
+    cf *P = Ys + AS_ET * (AS_CH + 1);      // [warps][AS_ET][AS_SMALL + 1] partials (r <= AS_SMALL)
+    const cf *__restrict__ Vs = ea.V + mb; // eigenvectors (rows), read through L1
     const float *lam = ea.lam + g.soff + (long long)mat * n;
     const int tid = threadIdx.x, e = tid & 31, w = tid >> 5;
-    for (int idx = tid; idx < r * n; idx += AS_THREADS) Vs[idx] = V[idx];
+    constexpr int NWS = AS_THREADS / 32;
     if (tid < r) {
         const float sg = sqrtf(fmaxf(lam[tid], 0.f));
         gcoef[tid] = sg > t ? 1.f - t / sg : 0.f;
     }
-    __syncthreads();
     const bool ein = e0 + e < len;
     const cf *Bcol = a.B0 + mb + e0 + e;
-    for (int idx = tid; idx < AS_ET * (AS_CH + 1); idx += AS_THREADS) Ys[idx] = mk(0.f, 0.f);
-    __syncthreads();
-    {
-        // warp w accumulates rows c in its slice for AS_HALF pairs at a time (the slice of B is
-        // re-read from L1 for the second half) and adds its partial sums into Ys (shared atomics)
-        const int nw = AS_THREADS / 32, c0 = (n * w) / nw, c1 = (n * (w + 1)) / nw;
-        for (int k0 = 0; k0 < r; k0 += AS_HALF) {
-            float yr[AS_HALF], yi[AS_HALF];
+    if (r <= AS_SMALL) {
+        // few pairs: warp w takes a slice of the rows c for every pair; fixed-order reduction
+        const int c0 = (n * w) / NWS, c1 = (n * (w + 1)) / NWS;
+        float yr[AS_SMALL], yi[AS_SMALL];
 #pragma unroll
-            for (int k = 0; k < AS_HALF; ++k) yr[k] = yi[k] = 0.f;
-            if (ein) {
-                for (int c = c0; c < c1; ++c) {
-                    const cf b = Bcol[(long long)c * len];
+        for (int k = 0; k < AS_SMALL; ++k) yr[k] = yi[k] = 0.f;
+        if (ein) {
+            for (int c = c0; c < c1; ++c) {
+                const cf b = Bcol[(long long)c * len];
 #pragma unroll
-                    for (int k = 0; k < AS_HALF; ++k) {
-                        if (k0 + k < r) {
-                            const cf v = Vs[(long long)(k0 + k) * n + c];
-                            yr[k] = fmaf(b.x, v.x, fmaf(-b.y, v.y, yr[k]));
-                            yi[k] = fmaf(b.x, v.y, fmaf(b.y, v.x, yi[k]));
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < AS_HALF; ++k) {
-                    if (k0 + k < r) {
-                        float *y = (float *)&Ys[e * (AS_CH + 1) + k0 + k];
-                        atomicAdd(y, yr[k]);
-                        atomicAdd(y + 1, yi[k]);
+                for (int k = 0; k < AS_SMALL; ++k) {
+                    if (k < r) {
+                        const cf v = Vs[(long long)k * n + c];
+                        yr[k] = fmaf(b.x, v.x, fmaf(-b.y, v.y, yr[k]));
+                        yi[k] = fmaf(b.x, v.y, fmaf(b.y, v.x, yi[k]));
                     }
                 }
             }
         }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < AS_ET * r; idx += AS_THREADS) {
-        const int ee = idx / r, k = idx - ee * r;
-        const cf y = Ys[ee * (AS_CH + 1) + k];
-        Ys[ee * (AS_CH + 1) + k] = mk(gcoef[k] * y.x, gcoef[k] * y.y);
+#pragma unroll
+        for (int k = 0; k < AS_SMALL; ++k)
+            if (k < r) P[((long long)w * AS_ET + e) * (AS_SMALL + 1) + k] = mk(yr[k], yi[k]);
+        __syncthreads();
+        for (int idx = tid; idx < AS_ET * r; idx += AS_THREADS) {
+            const int ee = idx / r, k = idx - ee * r;
+            float sr = 0.f, si = 0.f;
+            for (int ww = 0; ww < NWS; ++ww) {
+                const cf pv = P[((long long)ww * AS_ET + ee) * (AS_SMALL + 1) + k];
+                sr += pv.x;
+                si += pv.y;
+            }
+            Ys[ee * (AS_CH + 1) + k] = mk(gcoef[k] * sr, gcoef[k] * si);
+        }
+    } else {
+        // more pairs: warp w takes pairs w, w + 8, ... over all rows; one writer per entry
+        __syncthreads();                   // gcoef
+        constexpr int KPW = AS_CH / NWS;
+        float yr[KPW], yi[KPW];
+#pragma unroll
+        for (int u = 0; u < KPW; ++u) yr[u] = yi[u] = 0.f;
+        if (ein) {
+            for (int c = 0; c < n; ++c) {
+                const cf b = Bcol[(long long)c * len];
+#pragma unroll
+                for (int u = 0; u < KPW; ++u) {
+                    const int k = w + NWS * u;
+                    if (k < r) {
+                        const cf v = Vs[(long long)k * n + c];
+                        yr[u] = fmaf(b.x, v.x, fmaf(-b.y, v.y, yr[u]));
+                        yi[u] = fmaf(b.x, v.y, fmaf(b.y, v.x, yi[u]));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < KPW; ++u) {
+            const int k = w + NWS * u;
+            if (k < r) Ys[e * (AS_CH + 1) + k] = mk(gcoef[k] * yr[u], gcoef[k] * yi[u]);
+        }
     }
     __syncthreads();
     if (!ein) return;
     const float ib = 1.f / a.beta;
     const cf *ye = Ys + e * (AS_CH + 1);
     // Z columns c = w, w + 8, ...; batches of AS_B rows so that their loads are in flight together
-    constexpr int AS_B = 4, NWS = AS_THREADS / 32;
+    constexpr int AS_B = 4;
     const cf *__restrict__ B0 = a.B0;
     cf *__restrict__ Dp = a.D;
     cf *__restrict__ Ep = a.E;
@@ -1431,7 +1452,7 @@ cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, c
     for (int k = 0; k < gs.n; ++k) { maxlen = max(maxlen, gs.g[k].len); maxn = max(maxn, gs.g[k].s); }
     if (maxn > 512) return cudaErrorInvalidValue;
     // matrices with at most AS_CH pairs above t^2: streaming kernel; the others: k_apply_eig
-    const size_t smem_s = sizeof(cf) * ((size_t)AS_CH * maxn + (size_t)AS_ET * (AS_CH + 1));
+    const size_t smem_s = sizeof(cf) * ((size_t)AS_ET * (AS_CH + 1) + (size_t)(AS_THREADS / 32) * AS_ET * (AS_SMALL + 1));
     dim3 grid_s(mat_count, (maxlen + AS_ET - 1) / AS_ET);
     k_apply_stream<<<grid_s, AS_THREADS, smem_s, st>>>(gs, mat_begin, ea, a);
     cudaError_t e0 = cudaGetLastError();
