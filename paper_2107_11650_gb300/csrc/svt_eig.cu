@@ -1112,7 +1112,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
 // epilogue (Z out, or D and E update) fused, B re-read from L1/L2.  No large
 // per-thread arrays, so occupancy (and with it memory parallelism) is high.
 #define AS_ET 32
-#define AS_CH 32          // pairs handled by the streaming apply
+#define AS_CH 64          // pairs handled by the streaming apply
 #define AS_SMALL 8        // up to this many pairs phase 1 splits the rows of B over the warps
 #define AS_THREADS 256
 __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int mat_begin, EigArgs ea, SvtArgs a) {
