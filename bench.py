@@ -102,7 +102,8 @@ def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
     """Kernels libselr launches per ADMM iteration (mirrors admm_stage and svd_apply in
     selr.cu): adjoint, FFTs of the adjoints, DC + reduction, hybrid FFTs, lift, and per
     lift family either the warp-per-matrix SVT (s <= 8, len <= 64) or Gram, tridiagonal
-    reduction, eigenvectors and the two apply kernels (eig), Jacobi and apply (jacobi)."""
+    reduction, eigenvectors and the three apply kernels (streaming for r <= 32 and
+    32 < r <= 64 pairs, general above) (eig), Jacobi and apply (jacobi)."""
     fams = [plan.lift_shape(a) for a in (("row", "col") if model2d else ("pe", "param"))]
     fft_a = 2 if model2d else 1
 
@@ -110,7 +111,7 @@ def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
         s, l = min(r, c), max(r, c)
         if s <= 8 and l <= 64:
             return 1
-        return 5 if svd == "eig" else 2
+        return 6 if svd == "eig" else 2
 
     if exec_mode == "batched":
         per = 1 + fft_a + 2 + fft_a + 1 + sum(svt_kernels(r, c) for _, r, c in fams)

@@ -1112,12 +1112,13 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
 // epilogue (Z out, or D and E update) fused, B re-read from L1/L2.  No large
 // per-thread arrays, so occupancy (and with it memory parallelism) is high.
 #define AS_ET 32
-#define AS_CH 64          // pairs handled by the streaming apply
+#define AS_CH 64          // pairs handled by the streaming apply (variants for r <= 32 and 32 < r <= 64)
 #define AS_SMALL 8        // up to this many pairs phase 1 splits the rows of B over the warps
 #define AS_THREADS 256
+template <int CH>
 __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int mat_begin, EigArgs ea, SvtArgs a) {
     extern __shared__ cf ssm[];
-    __shared__ float gcoef[AS_CH];
+    __shared__ float gcoef[CH];
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
@@ -1126,12 +1127,12 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
     const int e0 = blockIdx.y * AS_ET;
     if (e0 >= len) return;
     const int r = ea.rank[g.moff + mat];
-    if (r > AS_CH) return;                 // k_apply_eig handles the rest
+    if (r > CH || (CH > 32 && r <= CH / 2)) return;   // the other variant / k_apply_eig
     const long long mb = g.off + (long long)mat * n * len;
     if (blockIdx.y == 0 && threadIdx.x == 0 && a.rank_out) a.rank_out[g.moff + mat] = r;
     const float t = g.thresh;
-    cf *Ys = ssm;                          // [AS_ET][AS_CH + 1]
-    cf *P = Ys + AS_ET * (AS_CH + 1);      // [warps][AS_ET][AS_SMALL + 1] partials (r <= AS_SMALL)
+    cf *Ys = ssm;                          // [AS_ET][CH + 1]
+    cf *P = Ys + AS_ET * (CH + 1);      // [warps][AS_ET][AS_SMALL + 1] partials (r <= AS_SMALL)
     const cf *__restrict__ Vs = ea.V + mb; // eigenvectors (rows), read through L1
     const float *lam = ea.lam + g.soff + (long long)mat * n;
     const int tid = threadIdx.x, e = tid & 31, w = tid >> 5;
@@ -1173,12 +1174,12 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
                 sr += pv.x;
                 si += pv.y;
             }
-            Ys[ee * (AS_CH + 1) + k] = mk(gcoef[k] * sr, gcoef[k] * si);
+            Ys[ee * (CH + 1) + k] = mk(gcoef[k] * sr, gcoef[k] * si);
         }
     } else {
         // more pairs: warp w takes pairs w, w + 8, ... over all rows; one writer per entry
         __syncthreads();                   // gcoef
-        constexpr int KPW = AS_CH / NWS;
+        constexpr int KPW = CH / NWS;
         float yr[KPW], yi[KPW];
 #pragma unroll
         for (int u = 0; u < KPW; ++u) yr[u] = yi[u] = 0.f;
@@ -1199,13 +1200,13 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
 #pragma unroll
         for (int u = 0; u < KPW; ++u) {
             const int k = w + NWS * u;
-            if (k < r) Ys[e * (AS_CH + 1) + k] = mk(gcoef[k] * yr[u], gcoef[k] * yi[u]);
+            if (k < r) Ys[e * (CH + 1) + k] = mk(gcoef[k] * yr[u], gcoef[k] * yi[u]);
         }
     }
     __syncthreads();
     if (!ein) return;
     const float ib = 1.f / a.beta;
-    const cf *ye = Ys + e * (AS_CH + 1);
+    const cf *ye = Ys + e * (CH + 1);
     // Z columns c = w, w + 8, ...; batches of AS_B rows so that their loads are in flight together
     constexpr int AS_B = 4;
     const cf *__restrict__ B0 = a.B0;
@@ -1384,7 +1385,9 @@ cudaError_t eig_init_attributes() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_apply_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
+    e = cudaFuncSetAttribute(k_apply_stream<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_stream<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_apply_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, g_eig_smem_max);
 }
@@ -1452,10 +1455,14 @@ cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, c
     for (int k = 0; k < gs.n; ++k) { maxlen = max(maxlen, gs.g[k].len); maxn = max(maxn, gs.g[k].s); }
     if (maxn > 512) return cudaErrorInvalidValue;
     // matrices with at most AS_CH pairs above t^2: streaming kernel; the others: k_apply_eig
-    const size_t smem_s = sizeof(cf) * ((size_t)AS_ET * (AS_CH + 1) + (size_t)(AS_THREADS / 32) * AS_ET * (AS_SMALL + 1));
+    const size_t smem32 = sizeof(cf) * ((size_t)AS_ET * (32 + 1) + (size_t)(AS_THREADS / 32) * AS_ET * (AS_SMALL + 1));
+    const size_t smem64 = sizeof(cf) * ((size_t)AS_ET * (64 + 1) + (size_t)(AS_THREADS / 32) * AS_ET * (AS_SMALL + 1));
     dim3 grid_s(mat_count, (maxlen + AS_ET - 1) / AS_ET);
-    k_apply_stream<<<grid_s, AS_THREADS, smem_s, st>>>(gs, mat_begin, ea, a);
+    k_apply_stream<32><<<grid_s, AS_THREADS, smem32, st>>>(gs, mat_begin, ea, a);
     cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
+    k_apply_stream<64><<<grid_s, AS_THREADS, smem64, st>>>(gs, mat_begin, ea, a);
+    e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     const size_t smem = sizeof(cf) * ((size_t)maxn * AP_ET + (size_t)AP_CH * maxn + AP_ET * AP_CH);
     dim3 grid(mat_count, (maxlen + AP_ET - 1) / AP_ET);
