@@ -279,8 +279,21 @@ __device__ __forceinline__ cf shfl_cf(cf v, int src) {
 //   3. all threads: p = tau (sum of partials), K = tau/2 Re(v^H p), w = p - K v.
 // Reflector: x = G[k+1:, k], alpha = -e^{i arg x0} ||x||, v = x - alpha e1,
 // tau = 2 / v^H v, so (I - tau v v^H) x = alpha e1.
-template <int RPL>
-__global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat_begin, EigArgs a) {
+// Columns [0, c0) of the packed matrix stay in global memory and [c0, n) are held in
+// shared memory: the smallest c0 for which the shared part, the work arrays of
+// k_tridiag and alignment fit in `budget` bytes (0 when everything fits).
+__host__ __device__ inline size_t tridiag_smem_c0(int n, int c0) {
+    const long long pk = (long long)n * (n + 1) / 2, c0s = (long long)c0 * (2 * n - c0 + 1) / 2;
+    return al16((size_t)(pk - c0s) * 8) + (size_t)(EIG_WARPS + 5) * n * 8 + (size_t)n * 4 + 16;
+}
+__host__ __device__ inline int tridiag_c0(int n, size_t budget) {
+    int c0 = 0;
+    while (c0 < n && tridiag_smem_c0(n, c0) > budget) ++c0;
+    return c0;
+}
+
+template <int RPL, bool HYB>
+__global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat_begin, EigArgs a, int budget) {
     extern __shared__ __align__(16) unsigned char tsm[];
     __shared__ float s_tau;
     __shared__ float red[EIG_WARPS];
@@ -290,24 +303,28 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     if (is_frozen(g, mat, a.active)) return;
     const int n = g.s;
     const long long pk = (long long)n * (n + 1) / 2;
+    const int c0 = HYB ? tridiag_c0(n, (size_t)budget) : 0;   // columns kept in global memory
+    const long long c0s = (long long)c0 * (2 * n - c0 + 1) / 2;
     cf *Gglob = a.Gp + g.poff + (long long)mat * pk;
-    cf *Gs = (cf *)tsm;                                   // [pk]
-    cf *Pw = Gs + al16((size_t)pk * 8) / 8;              // [EIG_WARPS][n] row-sum partials
+    cf *Gs = (cf *)tsm;                                   // packed columns c0..n-1
+    cf *Pw = Gs + al16((size_t)(pk - c0s) * 8) / 8;      // [EIG_WARPS][n] row-sum partials
     cf *Cs = Pw + (long long)EIG_WARPS * n;               // [n] column sums
     cf *vbuf0 = Cs + n, *vbuf1 = vbuf0 + n;               // v of this / previous step
     cf *wbuf0 = vbuf1 + n, *wbuf1 = wbuf0 + n;            // w of this / previous step
-    int *cst = (int *)(wbuf1 + n);                        // [n]
+    int *cst = (int *)(wbuf1 + n);                        // [n] column offsets (global for j < c0)
     float *td = tri_d(a, g, mat), *ttau = td + n;
     cf *te = (cf *)(td + 2 * n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // pointer to element (j, j) of packed column j
+    auto colp = [&](int j) -> cf * { return (HYB && j < c0) ? Gglob + cst[j] : Gs + cst[j]; };
     for (int j = tid; j < n; j += EIG_THREADS) {
-        cst[j] = (int)colstart(j, n);
+        cst[j] = (int)(colstart(j, n) - (j >= c0 ? c0s : 0));
         vbuf1[j] = wbuf1[j] = mk(0.f, 0.f);
     }
-    for (long long i = tid; i < pk; i += EIG_THREADS) Gs[i] = Gglob[i];
+    for (long long i = c0s + tid; i < pk; i += EIG_THREADS) Gs[i - c0s] = Gglob[i];
     __syncthreads();
     float gmax = 0.f;
-    for (int j = tid; j < n; j += EIG_THREADS) gmax = fmaxf(gmax, Gs[cst[j]].x);
+    for (int j = tid; j < n; j += EIG_THREADS) gmax = fmaxf(gmax, colp(j)[0].x);
     const float floor2 = reflector_floor(bmax(gmax, red));
     cf vo[RPL], wo[RPL], vn[RPL];
 #pragma unroll
@@ -320,17 +337,17 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             const cf vk = vp[k], wk = wp[k];
             cf colv[RPL];
             float xn2 = 0.f;
-            const int ck = cst[k];
+            cf *colk = colp(k) - k;
 #pragma unroll
             for (int t = 0; t < RPL; ++t) {
                 const int i = lane + 32 * t;
                 colv[t] = mk(0.f, 0.f);
                 if (32 * t + 31 >= k && 32 * t < n && i >= k && i < n) {
-                    cf gv = Gs[ck + i - k];
+                    cf gv = colk[i];
                     if (tau_old != 0.f) {
                         gv.x -= vo[t].x * wk.x + vo[t].y * wk.y + wo[t].x * vk.x + wo[t].y * vk.y;
                         gv.y -= vo[t].y * wk.x - vo[t].x * wk.y + wo[t].y * vk.x - wo[t].x * vk.y;
-                        Gs[ck + i - k] = gv;
+                        colk[i] = gv;
                     }
                     colv[t] = gv;
                     if (i > k) xn2 += cabs2(gv);
@@ -349,7 +366,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                 tau = 1.f / (xn2 + xnorm * ax0);
                 v0 = mk(phs.x * (ax0 + xnorm), phs.y * (ax0 + xnorm));
             }
-            cf *hv = Gglob + ck + 1;                          // Householder vector k (global)
+            cf *hv = Gglob + colstart(k, n) + 1;              // Householder vector k (global)
 #pragma unroll
             for (int t = 0; t < RPL; ++t) {
                 const int i = lane + 32 * t;
@@ -367,7 +384,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                 s_tau = tau;
                 ttau[k] = tau;
                 te[k] = alpha;
-                td[k] = Gs[ck].x;
+                td[k] = colk[k].x;
             }
         }
         __syncthreads();
@@ -392,17 +409,17 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                 float cr = 0.f, ci = 0.f;
                 if (j < n) {                                       // warp-uniform
                     const cf voj = vp[j], woj = wp[j], vnj = vb[j];
-                    const int base = cst[j] - j;
+                    cf *colj = colp(j) - j;
 #pragma unroll
                     for (int t = 0; t < RPL; ++t) {
                         if (32 * t + 31 >= j && 32 * t < n) {       // warp-uniform: slot t has rows >= j
                             const int i = lane + 32 * t;
                             if (i >= j && i < n) {
-                                cf gv = Gs[base + i];
+                                cf gv = colj[i];
                                 if (upd) {
                                     gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
                                     gv.y -= vo[t].y * woj.x - vo[t].x * woj.y + wo[t].y * voj.x - wo[t].x * voj.y;
-                                    Gs[base + i] = gv;
+                                    colj[i] = gv;
                                 }
                                 pa[t].x += gv.x * vnj.x - gv.y * vnj.y;
                                 pa[t].y += gv.x * vnj.y + gv.y * vnj.x;
@@ -492,21 +509,22 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             for (int t = 0; t < RPL; ++t) {
                 const int i = lane + 32 * t;
                 if (tau_old != 0.f && 32 * t < n && i >= j && i < n) {
-                    cf gv = Gs[cst[j] + i - j];
+                    cf *cj = colp(j) - j;
+                    cf gv = cj[i];
                     gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
                     gv.y -= vo[t].y * woj.x - vo[t].x * woj.y + wo[t].y * voj.x - wo[t].x * voj.y;
-                    Gs[cst[j] + i - j] = gv;
+                    cj[i] = gv;
                 }
             }
         }
         __syncwarp();
         if (lane == 0) {
             if (n >= 2) {
-                td[n - 2] = Gs[cst[n - 2]].x;
-                te[n - 2] = Gs[cst[n - 2] + 1];
+                td[n - 2] = colp(n - 2)[0].x;
+                te[n - 2] = colp(n - 2)[1];
                 ttau[n - 2] = 0.f;
             }
-            td[n - 1] = Gs[cst[n - 1]].x;
+            td[n - 1] = colp(n - 1)[0].x;
             te[n - 1] = mk(0.f, 0.f);
             ttau[n - 1] = 0.f;
         }
@@ -1375,10 +1393,11 @@ cudaError_t eig_init_attributes() {
     if (e != cudaSuccess) return e;
     g_eig_smem_max = optin - 2048;
     const int mx = g_eig_smem_max;
-    e = cudaFuncSetAttribute(k_tridiag<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    e = cudaFuncSetAttribute(k_tridiag<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<7, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag_g, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<16, 17, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<8, 9, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -1411,10 +1430,10 @@ cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const 
     return cudaGetLastError();
 }
 
-template <int RPL>
+template <int RPL, bool HYB>
 static void tridiag_launch(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, size_t smem,
                            cudaStream_t st) {
-    k_tridiag<RPL><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea);
+    k_tridiag<RPL, HYB><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea, (int)smem);
 }
 
 cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, cudaStream_t st) {
@@ -1426,10 +1445,19 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
     if (nmax <= EIG_SMEM_MAX_N) {
         const size_t smem = tridiag_smem(nmax);
         if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
-        if (nmax <= 32) tridiag_launch<1>(gs, mat_begin, mat_count, ea, smem, st);
-        else if (nmax <= 64) tridiag_launch<2>(gs, mat_begin, mat_count, ea, smem, st);
-        else if (nmax <= 128) tridiag_launch<4>(gs, mat_begin, mat_count, ea, smem, st);
-        else tridiag_launch<7>(gs, mat_begin, mat_count, ea, smem, st);
+        if (nmax <= 32) tridiag_launch<1, false>(gs, mat_begin, mat_count, ea, smem, st);
+        else if (nmax <= 64) tridiag_launch<2, false>(gs, mat_begin, mat_count, ea, smem, st);
+        else if (nmax <= 128) tridiag_launch<4, false>(gs, mat_begin, mat_count, ea, smem, st);
+        else tridiag_launch<7, false>(gs, mat_begin, mat_count, ea, smem, st);
+    } else if (nmax <= 256) {
+        // the first columns of the packed matrix stay in global memory (L2), the rest in smem
+        size_t smem = 0;
+        for (int k = 0; k < gs.n; ++k) {
+            const int n = gs.g[k].s;
+            smem = max(smem, tridiag_smem_c0(n, tridiag_c0(n, (size_t)g_eig_smem_max)));
+        }
+        tridiag_launch<8, true>(gs, mat_begin, mat_count, ea, (size_t)g_eig_smem_max, st);
+        (void)smem;
     } else {
         k_tridiag_g<<<mat_count, EIG_THREADS, tridiag_g_smem(nmax), st>>>(gs, mat_begin, ea);
     }
