@@ -288,8 +288,10 @@ static int svt_class(const Group &g, int svd) {
     if (g.s <= 32) return 1;
     if (g.s <= 64) return 2;
     if (g.s <= 128) return 3;
-    if (g.s <= 208) return 4;
-    return 5;
+    if (g.s <= 192) return 4;
+    if (g.s <= 208) return 5;
+    if (g.s <= 256) return 6;
+    return 7;
 }
 
 // Descriptions of a batch must agree on everything but the problem sizes and lambda.

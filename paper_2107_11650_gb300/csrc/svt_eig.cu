@@ -1396,6 +1396,7 @@ cudaError_t eig_init_attributes() {
     e = cudaFuncSetAttribute(k_tridiag<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<7, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag_g, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -1448,6 +1449,7 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
         if (nmax <= 32) tridiag_launch<1, false>(gs, mat_begin, mat_count, ea, smem, st);
         else if (nmax <= 64) tridiag_launch<2, false>(gs, mat_begin, mat_count, ea, smem, st);
         else if (nmax <= 128) tridiag_launch<4, false>(gs, mat_begin, mat_count, ea, smem, st);
+        else if (nmax <= 192) tridiag_launch<6, false>(gs, mat_begin, mat_count, ea, smem, st);
         else tridiag_launch<7, false>(gs, mat_begin, mat_count, ea, smem, st);
     } else if (nmax <= 256) {
         // the first columns of the packed matrix stay in global memory (L2), the rest in smem
