@@ -292,7 +292,7 @@ __host__ __device__ inline int tridiag_c0(int n, size_t budget) {
     return c0;
 }
 
-template <int RPL, bool HYB>
+template <int RPL, bool HYB, bool FULL>
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat_begin, EigArgs a, int budget) {
     extern __shared__ __align__(16) unsigned char tsm[];
     __shared__ float s_tau;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             for (int t = 0; t < RPL; ++t) {
                 const int i = lane + 32 * t;
                 colv[t] = mk(0.f, 0.f);
-                if (32 * t + 31 >= k && 32 * t < n && i >= k && i < n) {
+                if (32 * t + 31 >= k && (FULL || 32 * t < n) && i >= k && (FULL || i < n)) {
                     cf gv = colk[i];
                     if (tau_old != 0.f) {
                         gv.x -= vo[t].x * wk.x + vo[t].y * wk.y + wo[t].x * vk.x + wo[t].y * vk.y;
@@ -370,13 +370,13 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
 #pragma unroll
             for (int t = 0; t < RPL; ++t) {
                 const int i = lane + 32 * t;
-                if (32 * t < n) {
+                if ((FULL || 32 * t < n)) {
                     cf v = mk(0.f, 0.f);
-                    if (i >= k + 1 && i < n) {
+                    if (i >= k + 1 && (FULL || i < n)) {
                         v = tau == 0.f ? mk(0.f, 0.f) : (i == k + 1 ? v0 : colv[t]);
                         hv[i - k - 1] = v;
                     }
-                    if (i < n) vb[i] = v;
+                    if ((FULL || i < n)) vb[i] = v;
                 }
             }
             __syncwarp();
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
-            vn[t] = (i < n) ? vb[i] : mk(0.f, 0.f);
+            vn[t] = ((FULL || i < n)) ? vb[i] : mk(0.f, 0.f);
         }
         // ---- 2. fused update + symv over the trailing columns
         const bool upd = tau_old != 0.f;
@@ -412,9 +412,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                     cf *colj = colp(j) - j;
 #pragma unroll
                     for (int t = 0; t < RPL; ++t) {
-                        if (32 * t + 31 >= j && 32 * t < n) {       // warp-uniform: slot t has rows >= j
+                        if (32 * t + 31 >= j && (FULL || 32 * t < n)) {       // warp-uniform: slot t has rows >= j
                             const int i = lane + 32 * t;
-                            if (i >= j && i < n) {
+                            if (i >= j && (FULL || i < n)) {
                                 cf gv = colj[i];
                                 if (upd) {
                                     gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
-            if (32 * t < n && i >= k + 1 && i < n) Pw[(long long)warp * n + i] = pa[t];
+            if ((FULL || 32 * t < n) && i >= k + 1 && (FULL || i < n)) Pw[(long long)warp * n + i] = pa[t];
         }
         __syncthreads();
         // ---- 3. p = tau * (row partials + column sum), K, w (all threads)
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
-            wo[t] = (i < n) ? wb[i] : mk(0.f, 0.f);
+            wo[t] = ((FULL || i < n)) ? wb[i] : mk(0.f, 0.f);
             vo[t] = vn[t];
         }
         tau_old = tau;
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
 #pragma unroll
             for (int t = 0; t < RPL; ++t) {
                 const int i = lane + 32 * t;
-                if (tau_old != 0.f && 32 * t < n && i >= j && i < n) {
+                if (tau_old != 0.f && (FULL || 32 * t < n) && i >= j && (FULL || i < n)) {
                     cf *cj = colp(j) - j;
                     cf gv = cj[i];
                     gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
@@ -1393,12 +1393,12 @@ cudaError_t eig_init_attributes() {
     if (e != cudaSuccess) return e;
     g_eig_smem_max = optin - 2048;
     const int mx = g_eig_smem_max;
-    e = cudaFuncSetAttribute(k_tridiag<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<7, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    e = cudaSuccess;
+#define TRI_ATTR(R, H)                                                                                      \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<R, H, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag<R, H, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    TRI_ATTR(1, false) TRI_ATTR(2, false) TRI_ATTR(4, false) TRI_ATTR(6, false) TRI_ATTR(7, false) TRI_ATTR(8, true)
+#undef TRI_ATTR
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag_g, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<16, 17, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<8, 9, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -1434,7 +1434,10 @@ cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const 
 template <int RPL, bool HYB>
 static void tridiag_launch(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, size_t smem,
                            cudaStream_t st) {
-    k_tridiag<RPL, HYB><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea, (int)smem);
+    bool full = true;                  // every order equals 32 * RPL: no bound checks against n
+    for (int k = 0; k < gs.n; ++k) full = full && gs.g[k].s == 32 * RPL;
+    if (full) k_tridiag<RPL, HYB, true><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea, (int)smem);
+    else k_tridiag<RPL, HYB, false><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea, (int)smem);
 }
 
 cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, cudaStream_t st) {
