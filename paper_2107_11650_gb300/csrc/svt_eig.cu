@@ -414,9 +414,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                     for (int t = 0; t < RPL; ++t) {
                         if (32 * t + 31 >= j && (FULL || 32 * t < n)) {       // warp-uniform: slot t has rows >= j
                             const int i = lane + 32 * t;
-                            // only the slot holding row j needs i >= j and i > j; the others have i > j
-                            const bool edge = 32 * t <= j;                   // warp-uniform
-                            if ((edge ? i >= j : true) && (FULL || i < n)) {
+                            if (i >= j && (FULL || i < n)) {
                                 cf gv = colj[i];
                                 if (upd) {
                                     gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
@@ -425,7 +423,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                                 }
                                 pa[t].x += gv.x * vnj.x - gv.y * vnj.y;
                                 pa[t].y += gv.x * vnj.y + gv.y * vnj.x;
-                                if (!edge || i > j) {              // conj(G(i,j)) v_i -> p_j
+                                if (i > j) {                       // conj(G(i,j)) v_i -> p_j
                                     cr += gv.x * vn[t].x + gv.y * vn[t].y;
                                     ci += gv.x * vn[t].y - gv.y * vn[t].x;
                                 }
