@@ -168,14 +168,18 @@ __global__ void __launch_bounds__(256) k_gram(GroupSet gs, int mat_begin, const 
 }
 
 // ------------------------------------------------------- tridiagonal tools
-// Number of eigenvalues of the real symmetric tridiagonal (d, f) below x.
+// Number of eigenvalues of the real symmetric tridiagonal (d, f) below x.  The
+// recurrence divides once per step along a chain of n dependent steps, so it uses
+// the fast division (2 ulp): a count can only change where |q| is within rounding
+// of the pivot floor, which moves the bisection point by O(eps |T|), well inside
+// the bisection's own stopping width.
 __device__ __forceinline__ int sturm_lt(const float *d, const float *f2, int n, float x, float pivmin) {
     int cnt = 0;
     float q = d[0] - x;
     if (fabsf(q) < pivmin) q = -pivmin;
     if (q < 0.f) ++cnt;
     for (int k = 1; k < n; ++k) {
-        q = (d[k] - x) - f2[k - 1] / q;
+        q = (d[k] - x) - __fdividef(f2[k - 1], q);
         if (fabsf(q) < pivmin) q = -pivmin;
         if (q < 0.f) ++cnt;
     }
@@ -203,19 +207,20 @@ __device__ void tri_solve(const float *d, const float *f, int n, float lam, floa
             const float fn = k + 1 < n - 1 ? f[k + 1] : 0.f;
             if (fabsf(c0) >= fabsf(fk)) {
                 if (c0 == 0.f) c0 = tiny;
-                const float l = fk / c0;
-                u0[k * ST] = c0; u1[k * ST] = c1; u2[k * ST] = 0.f; lm[k * ST] = l; piv[k * ST] = 0;
+                const float rc = 1.f / c0;
+                const float l = fk * rc;
+                u0[k * ST] = rc; u1[k * ST] = c1; u2[k * ST] = 0.f; lm[k * ST] = l; piv[k * ST] = 0;
                 c0 = an - l * c1;
                 c1 = fn;
             } else {
                 const float l = c0 / fk;
-                u0[k * ST] = fk; u1[k * ST] = an; u2[k * ST] = fn; lm[k * ST] = l; piv[k * ST] = 1;
+                u0[k * ST] = 1.f / fk; u1[k * ST] = an; u2[k * ST] = fn; lm[k * ST] = l; piv[k * ST] = 1;
                 c0 = c1 - l * an;
                 c1 = -l * fn;
             }
         }
         if (c0 == 0.f) c0 = tiny;
-        u0[(n - 1) * ST] = c0; u1[(n - 1) * ST] = 0.f; u2[(n - 1) * ST] = 0.f;
+        u0[(n - 1) * ST] = 1.f / c0; u1[(n - 1) * ST] = 0.f; u2[(n - 1) * ST] = 0.f;
     }
     float zk = z[0];
     for (int k = 0; k < n - 1; ++k) {
@@ -229,13 +234,13 @@ __device__ void tri_solve(const float *d, const float *f, int n, float lam, floa
         }
     }
     z[(n - 1) * ST] = zk;
-    float x2 = z[(n - 1) * ST] / u0[(n - 1) * ST];
+    float x2 = z[(n - 1) * ST] * u0[(n - 1) * ST];
     z[(n - 1) * ST] = x2;
     if (n > 1) {
-        float x1 = (z[(n - 2) * ST] - u1[(n - 2) * ST] * x2) / u0[(n - 2) * ST];
+        float x1 = (z[(n - 2) * ST] - u1[(n - 2) * ST] * x2) * u0[(n - 2) * ST];
         z[(n - 2) * ST] = x1;
         for (int k = n - 3; k >= 0; --k) {
-            const float x0 = (z[k * ST] - u1[k * ST] * x1 - u2[k * ST] * x2) / u0[k * ST];
+            const float x0 = (z[k * ST] - u1[k * ST] * x1 - u2[k * ST] * x2) * u0[k * ST];
             z[k * ST] = x0;
             x2 = x1;
             x1 = x0;
