@@ -56,8 +56,6 @@ struct selr_plan {
     cudaEvent_t *ev;          // [prof_cap][NSTAGE][2]
     int prof_count;           // iterations timed by the last solve
     cudaGraphExec_t stage_graph[8];   // profiling: one graph per stage (NSTAGE <= 8)
-    cudaStream_t side;                // second stream of the split SVT stages
-    cudaEvent_t ev_fork, ev_join;
     // reverse-mode workspaces (allocated on the first VJP call)
     cf *gw_Z, *gw_Bbar, *gw_S1, *gw_S2, *gw_S3, *gw_S4, *gw_V, *gw_aug, *gw_aug2, *gw_Gp;
     cf *gw_U, *gw_Gv, *gw_W, *gw_Yv, *gw_C11, *gw_M2, *gw_X, *gw_Ab, *gw_Zo;
@@ -278,9 +276,6 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     }
     if (p->h_rel) cudaFreeHost(p->h_rel);
     if (p->h_active) cudaFreeHost(p->h_active);
-    if (p->side) cudaStreamDestroy(p->side);
-    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-    if (p->ev_join) cudaEventDestroy(p->ev_join);
     delete p;
     return SELR_OK;
 }
@@ -471,13 +466,6 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
         cudaGetLastError();
         selr_plan_destroy(p);
         return SELR_ERR_ALLOC;
-    }
-    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        selr_plan_destroy(p);
-        return SELR_ERR_CUDA;
     }
     *out = p;
     return SELR_OK;
@@ -783,30 +771,11 @@ static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_
     }
 }
 
-// One iteration.  Batched plans run the three SVT stages (Gram, eigensolver, apply) for
-// the two halves of the lifted matrices on two streams (fork and join by events, so a
-// captured graph gets two parallel branches): the first half's eigenvector and apply
-// kernels fill SMs left idle by the last wave of the second half's tridiagonalisation.
 static cudaError_t admm_iteration(selr_plan *p, const cf *Y, const uint8_t *mask, cudaStream_t st) {
-    cudaError_t e;
-    const bool split = p->d.exec == SELR_EXEC_BATCHED && p->gs.total >= 2;
-    for (int s = 0; s < (split ? 4 : NSTAGE); ++s)
-        if ((e = admm_stage(p, s, Y, mask, st)) != cudaSuccess) return e;
-    if (!split) return cudaSuccess;
-    const int *act = p->model2d ? nullptr : p->active;
-    SvtArgs a = svt_args(p);
-    a.mode = 1;
-    a.D = p->D;
-    a.E = p->E;
-    a.active = act;
-    const int total = p->gs.total, half = total / 2;
-    if ((e = cudaEventRecord(p->ev_fork, st)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(p->side, p->ev_fork, 0)) != cudaSuccess) return e;
-    if ((e = svd_apply(p, p->gs, half, total - half, a, 7, p->side)) != cudaSuccess) return e;
-    if ((e = svd_apply(p, p->gs, 0, half, a, 7, st)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(p->ev_join, p->side)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(st, p->ev_join, 0)) != cudaSuccess) return e;
-    if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->M, st);
+    for (int s = 0; s < NSTAGE; ++s) {
+        cudaError_t e = admm_stage(p, s, Y, mask, st);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
@@ -841,9 +810,7 @@ static cudaError_t capture(selr_plan *p, int s0, int s1, const cf *Y, const uint
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    if (s0 == 0 && s1 == NSTAGE) e = admm_iteration(p, Y, mask, st);      // whole iteration (split SVT)
-    else
-        for (int s = s0; s < s1 && e == cudaSuccess; ++s) e = admm_stage(p, s, Y, mask, st);
+    for (int s = s0; s < s1 && e == cudaSuccess; ++s) e = admm_stage(p, s, Y, mask, st);
     cudaError_t e2 = cudaStreamEndCapture(st, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (e2 == cudaSuccess) cudaGraphDestroy(g);
