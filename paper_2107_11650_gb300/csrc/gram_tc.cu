@@ -14,13 +14,13 @@
 // and a.b ~ a_h.b_h + a_h.b_l + a_l.b_h, which recovers about FP32 accuracy
 // (the dropped a_l.b_l term is 2^-22 relative).
 //
-// Kernel.  One CTA (4 warps) per matrix, s <= 256, N = s rounded up to 16.
+// Kernel.  One CTA (8 warps) per matrix, s <= 256, N = s rounded up to 16.
 // s <= 192: one pass over K with two accumulator pairs in tensor memory,
 // rows 0..127 x N columns and rows 128.. x columns 128..N-1 (the block below
 // tile 0 is the conjugate transpose of tile 0's right part), 2N + 2(N - 128) <=
 // 512 columns.  s > 192: two passes (rows 0..127, then 128..255) against all N
 // columns.  K in chunks of 16 real elements, double-buffered in shared memory
-// in the canonical K-major layout without swizzle (core matrices of 8 rows x 16
+// in three stages in the canonical K-major layout without swizzle (core matrices of 8 rows x 16
 // bytes; LBO = 128 bytes between core matrices along K, SBO = 512 bytes between
 // 8-row groups).  Each thread converts 4-element quads (one 16-byte store per
 // tile) while its loads of the next chunk are in flight; one thread issues
@@ -30,12 +30,13 @@
 // memory and returns.
 #include "selr_internal.cuh"
 
-#define GT_THREADS 128
+#define GT_THREADS 256           // 8 warps convert; warp w reads TMEM lane quarter w % 4
+#define GT_NS 3                  // shared-memory stages
 #define GT_KC 16                  // real K elements per chunk (64 bytes per row)
 #define GT_TILE_ROWS 256          // rows held per operand tile (s <= 256)
 #define GT_TILE_BYTES (GT_TILE_ROWS * GT_KC * 4)   // 16 KB
 #define GT_STAGE_BYTES (4 * GT_TILE_BYTES)         // Xh, Xl, Yh, Yl
-#define GT_SMEM (2 * GT_STAGE_BYTES + 1024)        // two stages + alignment slack
+#define GT_SMEM (GT_NS * GT_STAGE_BYTES + 1024)    // stages + alignment slack
 #define GT_WAIT_NS 2000000000ull   // 2 s bound on any single wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -136,13 +137,13 @@ __device__ __forceinline__ void gt_step(uint32_t dre, uint32_t dim, uint32_t ide
 }
 
 #define GT_QPR (GT_KC / 4)                                   // 4-element quads per row and chunk
-#define GT_QPT (GT_TILE_ROWS * GT_QPR / GT_THREADS)          // quads per thread (8)
+#define GT_QPT (GT_TILE_ROWS * GT_QPR / GT_THREADS)          // quads per thread (4)
 
 template <int MODE>
 __global__ void __launch_bounds__(GT_THREADS, 1)
 k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, unsigned *status) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[GT_NS];
     __shared__ uint32_t tmem_base_s;
     unsigned char *gsm = (unsigned char *)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
     int mat;
@@ -171,8 +172,8 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
+        for (int b = 0; b < GT_NS; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[b])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -183,7 +184,7 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
     const uint32_t d1_re = tm + 2u * N, d1_im = tm + 2u * N + (uint32_t)N1;
     const uint32_t idesc0 = gt_idesc(128, N), idesc1 = N1 ? gt_idesc(128, N1) : 0u;
     const uint32_t rowgrp = GT_KC / 4 * 128;       // bytes per 8-row group (SBO)
-    uint32_t waits[2] = {0u, 0u};                  // completed waits per stage (parity)
+    uint32_t waits[GT_NS] = {};                    // completed waits per stage (parity)
     bool ok = true;
     cf *G = Gp + g.poff + (long long)mat * ((long long)n * (n + 1) / 2);
     float2 pa[GT_QPT], pb[GT_QPT];                 // prefetched quads of the next chunk
@@ -205,9 +206,9 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
     for (int pass = 0; pass < npass && ok; ++pass) {
         gload(0);
         for (int kc = 0; kc < nk && ok; ++kc) {
-            const int st = kc & 1;
+            const int st = kc % GT_NS;
             unsigned char *stage = gsm + st * GT_STAGE_BYTES;
-            if (kc >= 2) {
+            if (kc >= GT_NS) {
                 // every thread waits, then the block agrees on the outcome (no divergent exits)
                 const bool w_ok = gt_wait(smem_u32(&bars[st]), waits[st] & 1);
                 ++waits[st];
@@ -261,21 +262,23 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
             }
         }
         if (!ok) break;
-        // drain: the last one or two chunks of this pass
+        // drain: the chunks of this pass not waited for yet
         bool d_ok = true;
-        for (int kc = nk >= 2 ? nk - 2 : 0; kc < nk; ++kc) {
-            const int st = kc & 1;
+        for (int kc = nk >= GT_NS ? nk - GT_NS : 0; kc < nk; ++kc) {
+            const int st = kc % GT_NS;
             d_ok = gt_wait(smem_u32(&bars[st]), waits[st] & 1) && d_ok;
             ++waits[st];
         }
         if (!__syncthreads_and(d_ok)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+        // warp w reads lane quarter w % 4 (rows) and every other group of 16 columns
+        const int wq = warp & 3, wh = warp >> 2;
+        const uint32_t lane_addr = (uint32_t)(wq * 32) << 16;
         {
             // tile 0 (single pass) or this pass's rows (two passes)
-            const int a = (single ? 0 : pass * 128) + warp * 32 + lane;
+            const int a = (single ? 0 : pass * 128) + wq * 32 + lane;
             const int jmax = single ? N : min(N, pass * 128 + 128);
-            for (int j0 = 0; j0 < jmax; j0 += 16) {
+            for (int j0 = 16 * wh; j0 < jmax; j0 += 32) {
                 uint32_t vr[16], vi[16];
                 tm_ld16(d0_re + lane_addr + (uint32_t)j0, vr);
                 tm_ld16(d0_im + lane_addr + (uint32_t)j0, vi);
@@ -293,8 +296,8 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
             }
         }
         if (single && N1) {
-            const int a = 128 + warp * 32 + lane;
-            for (int j0 = 0; j0 < N1; j0 += 16) {
+            const int a = 128 + wq * 32 + lane;
+            for (int j0 = 16 * wh; j0 < N1; j0 += 32) {
                 uint32_t vr[16], vi[16];
                 tm_ld16(d1_re + lane_addr + (uint32_t)j0, vr);
                 tm_ld16(d1_im + lane_addr + (uint32_t)j0, vi);
@@ -318,7 +321,7 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
         // ok is block-uniform here.  Let the MMAs already issued finish (bounded) before
         // the tensor memory is released; a commit that was never waited for is waited once.
         if (tid == 0) atomicOr(status, (unsigned)ST_TIMEOUT);
-        for (int st = 0; st < 2; ++st) gt_wait(smem_u32(&bars[st]), waits[st] & 1);
+        for (int st = 0; st < GT_NS; ++st) gt_wait(smem_u32(&bars[st]), waits[st] & 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
