@@ -35,6 +35,7 @@ struct selr_plan {
     cf *Gp, *V;              // packed Gram matrices / Householder vectors; eigenvectors
     float *lam, *tri;
     int *rank;
+    unsigned *ready;     // tridiagonal -> eigenvector hand-off flags, one per matrix
     long long packed_elems;
     float *sigma;
     int *mat_status;
@@ -260,7 +261,7 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
-                    p->rank, p->sigma,
+                    p->rank, p->ready, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -399,6 +400,7 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
         AL(p->lam, sizeof(float) * (size_t)p->vec_elems);
         AL(p->tri, 4 * sizeof(float) * (size_t)p->vec_elems);
         AL(p->rank, sizeof(int) * (size_t)gs.total);
+        AL(p->ready, sizeof(unsigned) * (size_t)gs.total);
     }
     const size_t nrel = (size_t)(n_inst > 1 + d->M ? n_inst : 1 + d->M);
     AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
@@ -416,7 +418,11 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
         AL(I.db, sizeof(float) * (p->model2d ? I.M : I.L));
     }
 #undef AL
-    if (cudaMemset(p->status, 0, sizeof(unsigned)) != cudaSuccess) { selr_plan_destroy(p); return SELR_ERR_CUDA; }
+    if (cudaMemset(p->status, 0, sizeof(unsigned)) != cudaSuccess ||
+        (p->ready && cudaMemset(p->ready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess)) {
+        selr_plan_destroy(p);
+        return SELR_ERR_CUDA;
+    }
     for (int i = 0; i < n_inst; ++i) {
         Inst &I = p->inst[i];
         const selr_desc &di = ds[i];
@@ -586,6 +592,7 @@ static EigArgs eig_args(selr_plan *p, const int *active) {
     e.active = active;
     e.status = p->status;
     e.ev_chunk = p->ev_chunk;
+    e.ready = p->ready;
     return e;
 }
 

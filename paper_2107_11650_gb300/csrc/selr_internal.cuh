@@ -173,6 +173,7 @@ struct EigArgs {
                          // pairs here ([mat] at g.off + mat s len, row q = pair q)
     int allp;            // compute every eigenpair, not only those above t^2 (needs zsave)
     int ev_chunk;        // inverse-iteration vectors per pass: 16 or 8 (0: by order)
+    unsigned *ready;     // [mat] k_tridiag -> k_eigvec hand-off flags (zero between calls), or null
 };
 cudaError_t eig_init_attributes();
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,

@@ -102,6 +102,58 @@ __device__ __forceinline__ bool is_frozen(const Group &g, int mat, const int *ac
     return false;
 }
 
+// --------------------------------------- tridiagonal -> eigenvector hand-off
+// k_eigvec is launched as a programmatic dependent of k_tridiag: each
+// k_tridiag CTA releases its dependents as soon as it starts, so k_eigvec
+// CTAs start on the SMs that the last, partial wave of k_tridiag leaves idle
+// (512 matrices are 3.4 waves on 152 SMs).  Each matrix has a ready flag: the
+// k_tridiag CTA publishes it (release) after its last write, the k_eigvec CTA
+// waits for it (acquire, bounded) and clears it for the next reduction.  The
+// wait always ends: dependents are only scheduled once every k_tridiag CTA is
+// resident.
+#define READY_WAIT_NS 2000000000ull
+
+__device__ __forceinline__ unsigned long long eig_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void pdl_release_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// End of a k_tridiag CTA: every thread's writes, then the flag.
+__device__ __forceinline__ void publish_ready(const EigArgs &a, const Group &g, int mat) {
+    if (!a.ready) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a.ready + g.moff + mat), "r"(1u) : "memory");
+    }
+}
+
+// Start of a k_eigvec CTA: wait for the flag of its matrix, then clear it.
+__device__ __forceinline__ void wait_ready(const EigArgs &a, const Group &g, int mat) {
+    if (!a.ready) return;
+    if (threadIdx.x == 0) {
+        unsigned *f = a.ready + g.moff + mat;
+        const unsigned long long t0 = eig_globaltimer();
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+            if (v != 0u) break;
+            if (eig_globaltimer() - t0 > READY_WAIT_NS) {
+                atomicOr(a.status, (unsigned)ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(256);
+        }
+        *f = 0u;
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------- Gram
 // One CTA computes a 64x64 block (I >= J) of G = B^H B for one matrix.
 #define GR_T 64
@@ -305,6 +357,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
+    pdl_release_dependents();
     if (is_frozen(g, mat, a.active)) return;
     const int n = g.s;
     const long long pk = (long long)n * (n + 1) / 2;
@@ -534,6 +587,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             ttau[n - 1] = 0.f;
         }
     }
+    publish_ready(a, g, mat);
 }
 
 // Same reduction with G kept in global memory (orders too large for shared
@@ -546,6 +600,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
+    pdl_release_dependents();
     if (is_frozen(g, mat, a.active)) return;
     const int n = g.s;
     const long long pk = (long long)n * (n + 1) / 2;
@@ -655,6 +710,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
         te[n - 1] = mk(0.f, 0.f);
         ttau[n - 1] = 0.f;
     }
+    publish_ready(a, g, mat);
 }
 
 // ------------------------------------------------ real tridiagonal setup
@@ -754,6 +810,7 @@ __global__ void __launch_bounds__(NT) k_eigvec(GroupSet gs, int mat_begin, EigAr
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
     if (is_frozen(g, mat, a.active)) return;
+    wait_ready(a, g, mat);
     const int n = g.s;
     float *zs = a.zsave ? a.zsave + g.off + (long long)mat * n * g.len : nullptr;
     const bool allp = a.allp != 0 && zs != nullptr;
@@ -1450,6 +1507,13 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
     if (g_eig_smem_max == 0) return cudaErrorNotReady;
     int nmax = 0;
     for (int k = 0; k < gs.n; ++k) nmax = max(nmax, gs.g[k].s);
+    // shared memory of the eigenvector kernel, checked before anything is launched (a
+    // reduction whose ready flags no k_eigvec consumes would leave them set)
+    int chunk = ea.ev_chunk == 8 || ea.ev_chunk == 16 ? ea.ev_chunk : ev_chunk(nmax);
+    if (chunk == 16 && nmax > 352) chunk = 8;         // the 16-vector layout exceeds shared memory
+    size_t ev_smem = 0;
+    for (int k = 0; k < gs.n; ++k) ev_smem = max(ev_smem, ev_layout(gs.g[k].s, chunk, chunk + 1).total);
+    if (ev_smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
     // 1. tridiagonalisation
     if (nmax <= EIG_SMEM_MAX_N) {
         const size_t smem = tridiag_smem(nmax);
@@ -1473,16 +1537,21 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // 2. eigenpairs above t^2 and back-transformation
-    int chunk = ea.ev_chunk == 8 || ea.ev_chunk == 16 ? ea.ev_chunk : ev_chunk(nmax);
-    if (chunk == 16 && nmax > 352) chunk = 8;         // the 16-vector layout exceeds shared memory
-    size_t smem = 0;
-    for (int k = 0; k < gs.n; ++k) smem = max(smem, ev_layout(gs.g[k].s, chunk, chunk + 1).total);
-    if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
-    // chunk 16: 512 threads; chunk 8: 256 threads (smaller CTAs, more matrices in flight per SM)
-    if (chunk == 16) k_eigvec<16, 17, 512><<<mat_count, 512, smem, st>>>(gs, mat_begin, ea);
-    else k_eigvec<8, 9, 256><<<mat_count, 256, smem, st>>>(gs, mat_begin, ea);
-    return cudaGetLastError();
+    // 2. eigenpairs above t^2 and back-transformation; chunk 16: 512 threads; chunk 8: 256
+    // threads (smaller CTAs, more matrices in flight per SM).  With ready flags the launch is
+    // a programmatic dependent of the reduction (see wait_ready).
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(mat_count);
+    cfg.blockDim = dim3(chunk == 16 ? 512 : 256);
+    cfg.dynamicSmemBytes = ev_smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = ea.ready ? 1 : 0;
+    if (chunk == 16) return cudaLaunchKernelEx(&cfg, k_eigvec<16, 17, 512>, gs, mat_begin, ea);
+    return cudaLaunchKernelEx(&cfg, k_eigvec<8, 9, 256>, gs, mat_begin, ea);
 }
 
 cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, const SvtArgs &a,
