@@ -141,7 +141,7 @@ __device__ __forceinline__ void gt_step(uint32_t dre, uint32_t dim, uint32_t ide
 
 template <int MODE>
 __global__ void __launch_bounds__(GT_THREADS, 1)
-k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, unsigned *status) {
+k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, unsigned *status, unsigned *ready) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     __shared__ __align__(8) uint64_t bars[GT_NS];
     __shared__ uint32_t tmem_base_s;
@@ -149,6 +149,7 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
+    pdl_release_dependents();
     if (active) {
         if (g.kind == G_PE && active[mat / g.L] == 0) return;
         if (g.kind == G_PARAM && active[mat / g.N] == 0) return;
@@ -326,6 +327,7 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tm) : "memory");
+    publish_flag(flag_of(ready, g, mat));
 }
 
 static bool g_gt_attr = false;
@@ -333,7 +335,7 @@ static bool g_gt_attr = false;
 bool gram_tc_fits(const Group &g) { return g.s >= 1 && g.s <= 256 && g.len >= 1; }
 
 cudaError_t launch_gram_tc(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,
-                           const int *active, int mode, unsigned *status, cudaStream_t st) {
+                           const int *active, int mode, unsigned *status, unsigned *ready, cudaStream_t st) {
     if (mat_count <= 0) return cudaSuccess;
     for (int k = 0; k < gs.n; ++k)
         if (!gram_tc_fits(gs.g[k])) return cudaErrorInvalidValue;
@@ -344,7 +346,7 @@ cudaError_t launch_gram_tc(const GroupSet &gs, int mat_begin, int mat_count, con
         if (e != cudaSuccess) return e;
         g_gt_attr = true;
     }
-    if (mode == 3) k_gram_tc<3><<<mat_count, GT_THREADS, GT_SMEM, st>>>(gs, mat_begin, B0, Gp, active, status);
-    else k_gram_tc<1><<<mat_count, GT_THREADS, GT_SMEM, st>>>(gs, mat_begin, B0, Gp, active, status);
+    if (mode == 3) k_gram_tc<3><<<mat_count, GT_THREADS, GT_SMEM, st>>>(gs, mat_begin, B0, Gp, active, status, ready);
+    else k_gram_tc<1><<<mat_count, GT_THREADS, GT_SMEM, st>>>(gs, mat_begin, B0, Gp, active, status, ready);
     return cudaGetLastError();
 }

@@ -35,7 +35,7 @@ struct selr_plan {
     cf *Gp, *V;              // packed Gram matrices / Householder vectors; eigenvectors
     float *lam, *tri;
     int *rank;
-    unsigned *ready;     // tridiagonal -> eigenvector hand-off flags, one per matrix
+    unsigned *gready, *ready, *vready;   // kernel hand-off flags, one per matrix (see EigArgs)
     long long packed_elems;
     float *sigma;
     int *mat_status;
@@ -261,7 +261,7 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
-                    p->rank, p->ready, p->sigma,
+                    p->rank, p->gready, p->ready, p->vready, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -400,7 +400,9 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
         AL(p->lam, sizeof(float) * (size_t)p->vec_elems);
         AL(p->tri, 4 * sizeof(float) * (size_t)p->vec_elems);
         AL(p->rank, sizeof(int) * (size_t)gs.total);
+        AL(p->gready, sizeof(unsigned) * (size_t)gs.total);
         AL(p->ready, sizeof(unsigned) * (size_t)gs.total);
+        AL(p->vready, sizeof(unsigned) * (size_t)gs.total);
     }
     const size_t nrel = (size_t)(n_inst > 1 + d->M ? n_inst : 1 + d->M);
     AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
@@ -419,7 +421,9 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
     }
 #undef AL
     if (cudaMemset(p->status, 0, sizeof(unsigned)) != cudaSuccess ||
-        (p->ready && cudaMemset(p->ready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess)) {
+        (p->ready && (cudaMemset(p->gready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess ||
+                      cudaMemset(p->ready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess ||
+                      cudaMemset(p->vready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess))) {
         selr_plan_destroy(p);
         return SELR_ERR_CUDA;
     }
@@ -593,6 +597,7 @@ static EigArgs eig_args(selr_plan *p, const int *active) {
     e.status = p->status;
     e.ev_chunk = p->ev_chunk;
     e.ready = p->ready;
+    e.vready = p->vready;
     return e;
 }
 
@@ -629,9 +634,12 @@ static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, c
                 if (part & 2) e = launch_jacobi(v, lb, lc, a, st);
                 if (e == cudaSuccess && (part & 4)) e = launch_svt_apply(v, lb, lc, a, st);
             } else {
-                const EigArgs ea = eig_args(p, a.active);
+                // the tensor-core Gram (one CTA per matrix) hands each matrix to k_tridiag by flag
+                EigArgs ea = eig_args(p, a.active);
+                ea.gready = tc ? p->gready : nullptr;
                 if (part & 1)
-                    e = tc ? launch_gram_tc(v, lb, lc, p->B0, p->Gp, a.active, (int)p->d.gram_precision, p->status, st)
+                    e = tc ? launch_gram_tc(v, lb, lc, p->B0, p->Gp, a.active, (int)p->d.gram_precision, p->status,
+                                            p->gready, st)
                            : launch_gram(v, lb, lc, p->B0, p->Gp, a.active, st);
                 if (e == cudaSuccess && (part & 2)) e = launch_heig(v, lb, lc, ea, st);
                 if (e == cudaSuccess && (part & 4)) e = launch_apply_eig(v, lb, lc, ea, a, st);

@@ -150,10 +150,88 @@ cudaError_t svt_init_attributes();
 cudaError_t launch_jacobi(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
 cudaError_t launch_svt_apply(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
 
+// ----------------------------------------------------- kernel hand-offs
+// The eigensolver's kernels run as a chain of programmatic dependent launches:
+// k_gram_tc -> k_tridiag -> k_eigvec -> k_apply_stream.  Each kernel of the
+// chain releases its dependents as soon as a CTA starts, so the next kernel's
+// CTAs start on the SMs that the last, partial wave of the previous one leaves
+// idle (512 matrices are 3.4 waves of k_tridiag on 152 SMs).  Per matrix and
+// hand-off there is a ready flag: the producing CTA publishes it (release)
+// after its last write, the consuming CTAs wait for it (acquire, bounded) before
+// their first read.  The wait always ends, because dependents are only
+// scheduled once every CTA of the producing kernel is resident.  Flags read by
+// one CTA per matrix are cleared by that CTA; the k_eigvec -> apply flags (read
+// by every row tile of a matrix) are cleared by the next k_tridiag of the
+// matrix, which starts after the previous apply has completed.
+#define READY_WAIT_NS 2000000000ull
+
+__device__ __forceinline__ unsigned long long eig_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void pdl_release_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// End of a producing CTA: every thread's writes, then the flag (if any).
+__device__ __forceinline__ void publish_flag(unsigned *f) {
+    if (!f) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(1u) : "memory");
+    }
+}
+
+// Start of a consuming CTA: wait (at most READY_WAIT_NS, then ST_TIMEOUT) for
+// the flag, optionally clear it.
+__device__ __forceinline__ void wait_flag(unsigned *f, unsigned *status, bool clear) {
+    if (!f) return;
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = eig_globaltimer();
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+            if (v != 0u) break;
+            if (eig_globaltimer() - t0 > READY_WAIT_NS) {
+                atomicOr(status, (unsigned)ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(256);
+        }
+        if (clear) *f = 0u;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned *flag_of(unsigned *base, const Group &g, int mat) {
+    return base ? base + g.moff + mat : nullptr;
+}
+
+// Launch with (pdl) or without programmatic stream serialization on the previous kernel.
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_ex(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // gram_tc.cu: G = B^H B on tcgen05 tensor cores, mode 1 = TF32, mode 3 = 3xTF32 (s <= 256)
 bool gram_tc_fits(const Group &g);
+// ready (or null): per-matrix flags published for a programmatically dependent k_tridiag.
 cudaError_t launch_gram_tc(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,
-                           const int *active, int mode, unsigned *status, cudaStream_t st);
+                           const int *active, int mode, unsigned *status, unsigned *ready, cudaStream_t st);
 
 // svt_small.cu: warp-per-matrix Jacobi SVT for s <= 8, len <= 64 (same SvtArgs epilogue)
 bool svt_small_fits(const Group &g);
@@ -173,7 +251,10 @@ struct EigArgs {
                          // pairs here ([mat] at g.off + mat s len, row q = pair q)
     int allp;            // compute every eigenpair, not only those above t^2 (needs zsave)
     int ev_chunk;        // inverse-iteration vectors per pass: 16 or 8 (0: by order)
-    unsigned *ready;     // [mat] k_tridiag -> k_eigvec hand-off flags (zero between calls), or null
+    // per-matrix hand-off flags of the programmatic launch chain (or null: plain launches)
+    unsigned *gready;    // k_gram_tc -> k_tridiag
+    unsigned *ready;     // k_tridiag -> k_eigvec
+    unsigned *vready;    // k_eigvec -> k_apply_stream / k_apply_eig
 };
 cudaError_t eig_init_attributes();
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,

@@ -102,58 +102,6 @@ __device__ __forceinline__ bool is_frozen(const Group &g, int mat, const int *ac
     return false;
 }
 
-// --------------------------------------- tridiagonal -> eigenvector hand-off
-// k_eigvec is launched as a programmatic dependent of k_tridiag: each
-// k_tridiag CTA releases its dependents as soon as it starts, so k_eigvec
-// CTAs start on the SMs that the last, partial wave of k_tridiag leaves idle
-// (512 matrices are 3.4 waves on 152 SMs).  Each matrix has a ready flag: the
-// k_tridiag CTA publishes it (release) after its last write, the k_eigvec CTA
-// waits for it (acquire, bounded) and clears it for the next reduction.  The
-// wait always ends: dependents are only scheduled once every k_tridiag CTA is
-// resident.
-#define READY_WAIT_NS 2000000000ull
-
-__device__ __forceinline__ unsigned long long eig_globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void pdl_release_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// End of a k_tridiag CTA: every thread's writes, then the flag.
-__device__ __forceinline__ void publish_ready(const EigArgs &a, const Group &g, int mat) {
-    if (!a.ready) return;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a.ready + g.moff + mat), "r"(1u) : "memory");
-    }
-}
-
-// Start of a k_eigvec CTA: wait for the flag of its matrix, then clear it.
-__device__ __forceinline__ void wait_ready(const EigArgs &a, const Group &g, int mat) {
-    if (!a.ready) return;
-    if (threadIdx.x == 0) {
-        unsigned *f = a.ready + g.moff + mat;
-        const unsigned long long t0 = eig_globaltimer();
-        for (;;) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
-            if (v != 0u) break;
-            if (eig_globaltimer() - t0 > READY_WAIT_NS) {
-                atomicOr(a.status, (unsigned)ST_TIMEOUT);
-                break;
-            }
-            __nanosleep(256);
-        }
-        *f = 0u;
-    }
-    __syncthreads();
-}
-
 // ------------------------------------------------------------------- Gram
 // One CTA computes a 64x64 block (I >= J) of G = B^H B for one matrix.
 #define GR_T 64
@@ -359,6 +307,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     const Group &g = gs.g[gi];
     pdl_release_dependents();
     if (is_frozen(g, mat, a.active)) return;
+    wait_flag(flag_of(a.gready, g, mat), a.status, true);
+    if (a.vready && threadIdx.x == 0) a.vready[g.moff + mat] = 0u;
     const int n = g.s;
     const long long pk = (long long)n * (n + 1) / 2;
     const int c0 = HYB ? tridiag_c0(n, (size_t)budget) : 0;   // columns kept in global memory
@@ -587,7 +537,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             ttau[n - 1] = 0.f;
         }
     }
-    publish_ready(a, g, mat);
+    publish_flag(flag_of(a.ready, g, mat));
 }
 
 // Same reduction with G kept in global memory (orders too large for shared
@@ -602,6 +552,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
     const Group &g = gs.g[gi];
     pdl_release_dependents();
     if (is_frozen(g, mat, a.active)) return;
+    wait_flag(flag_of(a.gready, g, mat), a.status, true);
+    if (a.vready && threadIdx.x == 0) a.vready[g.moff + mat] = 0u;
     const int n = g.s;
     const long long pk = (long long)n * (n + 1) / 2;
     cf *Gs = a.Gp + g.poff + (long long)mat * pk;
@@ -710,7 +662,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
         te[n - 1] = mk(0.f, 0.f);
         ttau[n - 1] = 0.f;
     }
-    publish_ready(a, g, mat);
+    publish_flag(flag_of(a.ready, g, mat));
 }
 
 // ------------------------------------------------ real tridiagonal setup
@@ -809,8 +761,9 @@ __global__ void __launch_bounds__(NT) k_eigvec(GroupSet gs, int mat_begin, EigAr
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
+    pdl_release_dependents();
     if (is_frozen(g, mat, a.active)) return;
-    wait_ready(a, g, mat);
+    wait_flag(flag_of(a.ready, g, mat), a.status, true);
     const int n = g.s;
     float *zs = a.zsave ? a.zsave + g.off + (long long)mat * n * g.len : nullptr;
     const bool allp = a.allp != 0 && zs != nullptr;
@@ -846,7 +799,10 @@ __global__ void __launch_bounds__(NT) k_eigvec(GroupSet gs, int mat_begin, EigAr
     const float tnorm = fmaxf(fabsf(gl), fabsf(gu));
     const int r = s_r;
     if (tid == 0) *rank_out = r;
-    if (r == 0) return;
+    if (r == 0) {
+        publish_flag(flag_of(a.vready, g, mat));
+        return;
+    }
     for (int q = warp; q < r; q += NW) {
         const int j = n - 1 - q;
         float lo = fmaxf(gl, t2), hi = gu;
@@ -991,6 +947,7 @@ __global__ void __launch_bounds__(NT) k_eigvec(GroupSet gs, int mat_begin, EigAr
         }
         __syncthreads();
     }
+    publish_flag(flag_of(a.vready, g, mat));
 }
 
 // ------------------------------------------------------------- resolvent
@@ -1202,10 +1159,12 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
+    pdl_release_dependents();
     if (is_frozen(g, mat, a.active)) return;
     const int n = g.s, len = g.len;
     const int e0 = blockIdx.y * AS_ET;
     if (e0 >= len) return;
+    wait_flag(flag_of(ea.vready, g, mat), a.status, false);
     const int r = ea.rank[g.moff + mat];
     if (r > CH || (CH > 32 && r <= CH / 2)) return;   // the other variant / k_apply_eig
     const long long mb = g.off + (long long)mat * n * len;
@@ -1352,6 +1311,7 @@ __global__ void __launch_bounds__(AP_THREADS) k_apply_eig(GroupSet gs, int mat_b
     const int n = g.s, len = g.len;
     const int e0 = blockIdx.y * AP_ET;
     if (e0 >= len) return;
+    wait_flag(flag_of(ea.vready, g, mat), a.status, false);
     const int et = min(AP_ET, len - e0);
     const long long mb = g.off + (long long)mat * n * len;
     const int r = ea.rank[g.moff + mat];
@@ -1494,12 +1454,16 @@ cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const 
 }
 
 template <int RPL, bool HYB>
-static void tridiag_launch(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, size_t smem,
-                           cudaStream_t st) {
+static cudaError_t tridiag_launch(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, size_t smem,
+                                  cudaStream_t st) {
     bool full = true;                  // every order equals 32 * RPL: no bound checks against n
     for (int k = 0; k < gs.n; ++k) full = full && gs.g[k].s == 32 * RPL;
-    if (full) k_tridiag<RPL, HYB, true><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea, (int)smem);
-    else k_tridiag<RPL, HYB, false><<<mat_count, EIG_THREADS, smem, st>>>(gs, mat_begin, ea, (int)smem);
+    const bool pdl = ea.gready != nullptr;
+    if (full)
+        return launch_ex(pdl, k_tridiag<RPL, HYB, true>, dim3(mat_count), dim3(EIG_THREADS), smem, st, gs, mat_begin,
+                         ea, (int)smem);
+    return launch_ex(pdl, k_tridiag<RPL, HYB, false>, dim3(mat_count), dim3(EIG_THREADS), smem, st, gs, mat_begin, ea,
+                     (int)smem);
 }
 
 cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, cudaStream_t st) {
@@ -1514,44 +1478,31 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
     size_t ev_smem = 0;
     for (int k = 0; k < gs.n; ++k) ev_smem = max(ev_smem, ev_layout(gs.g[k].s, chunk, chunk + 1).total);
     if (ev_smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
-    // 1. tridiagonalisation
+    // 1. tridiagonalisation (a programmatic dependent of k_gram_tc when ea.gready is set)
+    cudaError_t e;
     if (nmax <= EIG_SMEM_MAX_N) {
         const size_t smem = tridiag_smem(nmax);
         if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
-        if (nmax <= 32) tridiag_launch<1, false>(gs, mat_begin, mat_count, ea, smem, st);
-        else if (nmax <= 64) tridiag_launch<2, false>(gs, mat_begin, mat_count, ea, smem, st);
-        else if (nmax <= 128) tridiag_launch<4, false>(gs, mat_begin, mat_count, ea, smem, st);
-        else if (nmax <= 192) tridiag_launch<6, false>(gs, mat_begin, mat_count, ea, smem, st);
-        else tridiag_launch<7, false>(gs, mat_begin, mat_count, ea, smem, st);
+        if (nmax <= 32) e = tridiag_launch<1, false>(gs, mat_begin, mat_count, ea, smem, st);
+        else if (nmax <= 64) e = tridiag_launch<2, false>(gs, mat_begin, mat_count, ea, smem, st);
+        else if (nmax <= 128) e = tridiag_launch<4, false>(gs, mat_begin, mat_count, ea, smem, st);
+        else if (nmax <= 192) e = tridiag_launch<6, false>(gs, mat_begin, mat_count, ea, smem, st);
+        else e = tridiag_launch<7, false>(gs, mat_begin, mat_count, ea, smem, st);
     } else if (nmax <= 256) {
         // the first columns of the packed matrix stay in global memory (L2), the rest in smem
-        size_t smem = 0;
-        for (int k = 0; k < gs.n; ++k) {
-            const int n = gs.g[k].s;
-            smem = max(smem, tridiag_smem_c0(n, tridiag_c0(n, (size_t)g_eig_smem_max)));
-        }
-        tridiag_launch<8, true>(gs, mat_begin, mat_count, ea, (size_t)g_eig_smem_max, st);
-        (void)smem;
+        e = tridiag_launch<8, true>(gs, mat_begin, mat_count, ea, (size_t)g_eig_smem_max, st);
     } else {
-        k_tridiag_g<<<mat_count, EIG_THREADS, tridiag_g_smem(nmax), st>>>(gs, mat_begin, ea);
+        e = launch_ex(ea.gready != nullptr, k_tridiag_g, dim3(mat_count), dim3(EIG_THREADS), tridiag_g_smem(nmax), st,
+                      gs, mat_begin, ea);
     }
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // 2. eigenpairs above t^2 and back-transformation; chunk 16: 512 threads; chunk 8: 256
     // threads (smaller CTAs, more matrices in flight per SM).  With ready flags the launch is
-    // a programmatic dependent of the reduction (see wait_ready).
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.gridDim = dim3(mat_count);
-    cfg.blockDim = dim3(chunk == 16 ? 512 : 256);
-    cfg.dynamicSmemBytes = ev_smem;
-    cfg.stream = st;
-    cfg.attrs = at;
-    cfg.numAttrs = ea.ready ? 1 : 0;
-    if (chunk == 16) return cudaLaunchKernelEx(&cfg, k_eigvec<16, 17, 512>, gs, mat_begin, ea);
-    return cudaLaunchKernelEx(&cfg, k_eigvec<8, 9, 256>, gs, mat_begin, ea);
+    // a programmatic dependent of the reduction.
+    const bool pdl = ea.ready != nullptr;
+    if (chunk == 16)
+        return launch_ex(pdl, k_eigvec<16, 17, 512>, dim3(mat_count), dim3(512), ev_smem, st, gs, mat_begin, ea);
+    return launch_ex(pdl, k_eigvec<8, 9, 256>, dim3(mat_count), dim3(256), ev_smem, st, gs, mat_begin, ea);
 }
 
 cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, const SvtArgs &a,
@@ -1565,8 +1516,9 @@ cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, c
     const size_t smem32 = sizeof(cf) * ((size_t)AS_ET * (32 + 1) + (size_t)(AS_THREADS / 32) * AS_ET * (AS_SMALL + 1));
     const size_t smem64 = sizeof(cf) * ((size_t)AS_ET * (64 + 1) + (size_t)(AS_THREADS / 32) * AS_ET * (AS_SMALL + 1));
     dim3 grid_s(mat_count, (maxlen + AS_ET - 1) / AS_ET);
-    k_apply_stream<32><<<grid_s, AS_THREADS, smem32, st>>>(gs, mat_begin, ea, a);
-    cudaError_t e0 = cudaGetLastError();
+    // a programmatic dependent of k_eigvec when ea.vready is set
+    cudaError_t e0 = launch_ex(ea.vready != nullptr, k_apply_stream<32>, grid_s, dim3(AS_THREADS), smem32, st, gs,
+                               mat_begin, ea, a);
     if (e0 != cudaSuccess) return e0;
     k_apply_stream<64><<<grid_s, AS_THREADS, smem64, st>>>(gs, mat_begin, ea, a);
     e0 = cudaGetLastError();
