@@ -1145,6 +1145,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
 // phase 1: Y[e][k] = h_k sum_c B[e][c] v_k[c], lane = e; for r <= AS_SMALL the warps
 // split the rows c (partial sums reduced in a fixed order), otherwise they split the
 // pairs k (one writer per entry), so the result is bitwise reproducible;
+// phase 1 loads AS_P1B rows of B together (memory parallelism at 3 CTAs per SM);
 // phase 2: Z[e][c] = sum_k Y[e][k] conj(v_k[c]) streamed over c with the
 // epilogue (Z out, or D and E update) fused, B re-read from L1/L2.  No large
 // per-thread arrays, so occupancy (and with it memory parallelism) is high.
@@ -1152,6 +1153,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
 #define AS_CH 64          // pairs handled by the streaming apply (variants for r <= 32 and 32 < r <= 64)
 #define AS_SMALL 8        // up to this many pairs phase 1 splits the rows of B over the warps
 #define AS_THREADS 256
+#define AS_P1B 8          // rows of B loaded together in phase 1
 template <int CH>
 __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int mat_begin, EigArgs ea, SvtArgs a) {
     extern __shared__ cf ssm[];
@@ -1189,14 +1191,22 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
 #pragma unroll
         for (int k = 0; k < AS_SMALL; ++k) yr[k] = yi[k] = 0.f;
         if (ein) {
-            for (int c = c0; c < c1; ++c) {
-                const cf b = Bcol[(long long)c * len];
+            for (int cb = c0; cb < c1; cb += AS_P1B) {
+                cf bb[AS_P1B];                     // AS_P1B rows of B in flight together
 #pragma unroll
-                for (int k = 0; k < AS_SMALL; ++k) {
-                    if (k < r) {
-                        const cf v = Vs[(long long)k * n + c];
-                        yr[k] = fmaf(b.x, v.x, fmaf(-b.y, v.y, yr[k]));
-                        yi[k] = fmaf(b.x, v.y, fmaf(b.y, v.x, yi[k]));
+                for (int u = 0; u < AS_P1B; ++u) bb[u] = cb + u < c1 ? Bcol[(long long)(cb + u) * len] : mk(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < AS_P1B; ++u) {
+                    if (cb + u < c1) {
+                        const cf b = bb[u];
+#pragma unroll
+                        for (int k = 0; k < AS_SMALL; ++k) {
+                            if (k < r) {
+                                const cf v = Vs[(long long)k * n + cb + u];
+                                yr[k] = fmaf(b.x, v.x, fmaf(-b.y, v.y, yr[k]));
+                                yi[k] = fmaf(b.x, v.y, fmaf(b.y, v.x, yi[k]));
+                            }
+                        }
                     }
                 }
             }
@@ -1223,15 +1233,23 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
 #pragma unroll
         for (int u = 0; u < KPW; ++u) yr[u] = yi[u] = 0.f;
         if (ein) {
-            for (int c = 0; c < n; ++c) {
-                const cf b = Bcol[(long long)c * len];
+            for (int cb = 0; cb < n; cb += AS_P1B) {
+                cf bb[AS_P1B];
 #pragma unroll
-                for (int u = 0; u < KPW; ++u) {
-                    const int k = w + NWS * u;
-                    if (k < r) {
-                        const cf v = Vs[(long long)k * n + c];
-                        yr[u] = fmaf(b.x, v.x, fmaf(-b.y, v.y, yr[u]));
-                        yi[u] = fmaf(b.x, v.y, fmaf(b.y, v.x, yi[u]));
+                for (int u = 0; u < AS_P1B; ++u) bb[u] = cb + u < n ? Bcol[(long long)(cb + u) * len] : mk(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < AS_P1B; ++u) {
+                    if (cb + u < n) {
+                        const cf b = bb[u];
+#pragma unroll
+                        for (int q = 0; q < KPW; ++q) {
+                            const int k = w + NWS * q;
+                            if (k < r) {
+                                const cf v = Vs[(long long)k * n + cb + u];
+                                yr[q] = fmaf(b.x, v.x, fmaf(-b.y, v.y, yr[q]));
+                                yi[q] = fmaf(b.x, v.y, fmaf(b.y, v.x, yi[q]));
+                            }
+                        }
                     }
                 }
             }
