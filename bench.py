@@ -626,7 +626,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": {"gram": "k_gram (Gram matrices of all 512 lifts)",
                                                 "svd": ("k_jacobi (one-sided Jacobi SVD)" if args.svd == "jacobi" else
                                                         "k_tridiag + k_eigvec (Householder tridiagonal eigensolver, eigenpairs above t^2)"),
-                                                "apply": "k_apply_eig (Z and multiplier update)"}[jac["stage"]],
+                                                "apply": "k_apply_stream (Z and multiplier update)"}[jac["stage"]],
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": None, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock",
                      "launch_ms": jac["ms"]},
