@@ -49,7 +49,7 @@ typedef enum {
     SELR_ERR_CUDA = 3,            /* a CUDA runtime call failed */
     SELR_ERR_NO_CONVERGENCE = 4,  /* a Jacobi SVD hit its sweep cap (device-detected) */
     SELR_ERR_NONFINITE = 5,       /* NaN/Inf met in data or in the iterate (device-detected) */
-    SELR_ERR_TIMEOUT = 6,         /* reserved: a bounded device wait ran out */
+    SELR_ERR_TIMEOUT = 6,         /* a bounded device wait ran out (device-detected) */
     SELR_ERR_UNSUPPORTED = 7,     /* feature not built */
     SELR_ERR_ALLOC = 8            /* device allocation failed */
 } selr_status;
@@ -281,9 +281,23 @@ selr_status selr_profile_enable(selr_plan *plan, int32_t on);
 selr_status selr_profile_read(selr_plan *plan, int32_t stage, float *total_ms, int32_t *count);
 
 /* Synchronise `stream` and return the first device-side condition recorded
- * since the last call (SELR_ERR_NO_CONVERGENCE, SELR_ERR_NONFINITE), or
- * SELR_ERR_CUDA if the stream reports an error; clears the record. */
+ * since the last call (SELR_ERR_TIMEOUT, SELR_ERR_NONFINITE,
+ * SELR_ERR_NO_CONVERGENCE, in that order of precedence), or SELR_ERR_CUDA if
+ * the stream reports an error; clears the record.  SELR_ERR_TIMEOUT means a
+ * bounded device wait ran out (an mbarrier of the tensor-core Gram, or the
+ * per-matrix hand-off between the eigensolver's kernels, 2 s each): the
+ * results of that call are not valid, the context stays usable. */
 selr_status selr_sync_status(selr_plan *plan, selr_stream stream);
+
+/* Failure-handling self-test (no counterpart in the paper): one CTA runs the
+ * bounded hand-off wait of the eigensolver's kernels on a device flag that the
+ * host sets to `set_flag` (0 or 1) beforehand and nothing sets afterwards,
+ * with a limit of limit_us microseconds (1 .. 2 000 000).  Returns SELR_OK
+ * when the flag was set (and the wait consumed it), SELR_ERR_TIMEOUT when the
+ * wait ran out, SELR_ERR_INVALID_ARG for arguments out of range (checked
+ * before any CUDA call), SELR_ERR_ALLOC / SELR_ERR_CUDA otherwise.
+ * Allocates and frees 8 bytes of device memory; synchronises the device. */
+selr_status selr_selftest_wait(int32_t set_flag, int32_t limit_us);
 
 /* ---------------------------------------------------------------------
  * Reverse mode, for unrolled reconstructions whose per-iteration SVT

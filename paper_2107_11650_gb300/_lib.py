@@ -52,6 +52,7 @@ SIGNATURES = {
     "selr_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_int32),
                              ctypes.POINTER(c_float), c_void_p]),
     "selr_sync_status": (c_int32, [c_void_p, c_void_p]),
+    "selr_selftest_wait": (c_int32, [c_int32, c_int32]),
     "selr_set_iterations": (c_int32, [c_void_p, c_int32, c_float]),
     "selr_profile_enable": (c_int32, [c_void_p, c_int32]),
     "selr_profile_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_float), ctypes.POINTER(c_int32)]),

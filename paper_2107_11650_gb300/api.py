@@ -274,6 +274,12 @@ def selr_sync_status(plan: Plan, stream=None) -> int:
     return int(plan.lib.selr_sync_status(plan.handle, _stream(stream)))
 
 
+def selr_selftest_wait(set_flag: bool, limit_us: int) -> int:
+    """Run the eigensolver's bounded hand-off wait on a flag the host set (or did
+    not set); returns the status code (0 = consumed, 6 = SELR_ERR_TIMEOUT)."""
+    return int(_lib.load().selr_selftest_wait(1 if set_flag else 0, int(limit_us)))
+
+
 # ------------------------------------------------------------- reverse mode
 def selr_svt_vjp(plan: Plan, A, Zbar, thresh: float, Abar, tbar, Z_out=None, stream=None):
     """Abar <- VJP of S_t at A for cotangent Zbar; tbar (device float32[1]) <- dL/dt;

@@ -1244,6 +1244,28 @@ extern "C" selr_status selr_profile_read(selr_plan *p, int32_t stage, float *tot
     return SELR_OK;
 }
 
+extern "C" selr_status selr_selftest_wait(int32_t set_flag, int32_t limit_us) {
+    if (limit_us < 1 || limit_us > 2000000 || (set_flag != 0 && set_flag != 1)) return SELR_ERR_INVALID_ARG;
+    unsigned *d = nullptr;                     // [0] flag, [1] status
+    if (cudaMalloc(&d, 2 * sizeof(unsigned)) != cudaSuccess) {
+        g_last_error = cudaGetLastError();
+        return SELR_ERR_ALLOC;
+    }
+    const unsigned init[2] = {(unsigned)set_flag, 0u};
+    unsigned h[2] = {0u, 0u};
+    cudaError_t e = cudaMemcpy(d, init, sizeof(init), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_wait_selftest(d, d + 1, (unsigned long long)limit_us * 1000ull, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        g_last_error = e;
+        return SELR_ERR_CUDA;
+    }
+    if (h[1] & ST_TIMEOUT) return SELR_ERR_TIMEOUT;
+    return h[0] == 0u ? SELR_OK : SELR_ERR_CUDA;    // a consumed flag is cleared
+}
+
 extern "C" selr_status selr_sync_status(selr_plan *p, selr_stream stream) {
     if (!p) return SELR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;

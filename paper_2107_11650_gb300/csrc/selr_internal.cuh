@@ -185,9 +185,10 @@ __device__ __forceinline__ void publish_flag(unsigned *f) {
     }
 }
 
-// Start of a consuming CTA: wait (at most READY_WAIT_NS, then ST_TIMEOUT) for
-// the flag, optionally clear it.
-__device__ __forceinline__ void wait_flag(unsigned *f, unsigned *status, bool clear) {
+// Start of a consuming CTA: wait (at most limit_ns, then ST_TIMEOUT) for the
+// flag, optionally clear it.
+__device__ __forceinline__ void wait_flag(unsigned *f, unsigned *status, bool clear,
+                                          unsigned long long limit_ns = READY_WAIT_NS) {
     if (!f) return;
     if (threadIdx.x == 0) {
         const unsigned long long t0 = eig_globaltimer();
@@ -195,7 +196,7 @@ __device__ __forceinline__ void wait_flag(unsigned *f, unsigned *status, bool cl
             unsigned v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
             if (v != 0u) break;
-            if (eig_globaltimer() - t0 > READY_WAIT_NS) {
+            if (eig_globaltimer() - t0 > limit_ns) {
                 atomicOr(status, (unsigned)ST_TIMEOUT);
                 break;
             }
@@ -226,6 +227,9 @@ static inline cudaError_t launch_ex(bool pdl, void (*kern)(KArgs...), dim3 grid,
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
+
+// One CTA of wait_flag on `flag` with the given limit (failure-handling self-test).
+cudaError_t launch_wait_selftest(unsigned *flag, unsigned *status, unsigned long long limit_ns, cudaStream_t st);
 
 // gram_tc.cu: G = B^H B on tcgen05 tensor cores, mode 1 = TF32, mode 3 = 3xTF32 (s <= 256)
 bool gram_tc_fits(const Group &g);

@@ -1424,6 +1424,16 @@ __global__ void __launch_bounds__(AP_THREADS) k_apply_eig(GroupSet gs, int mat_b
 }
 
 // ---------------------------------------------------------------- launchers
+// The hand-off wait of the launch chain on a flag set (or never set) by the host.
+__global__ void k_wait_selftest(unsigned *flag, unsigned *status, unsigned long long limit_ns) {
+    wait_flag(flag, status, true, limit_ns);
+}
+
+cudaError_t launch_wait_selftest(unsigned *flag, unsigned *status, unsigned long long limit_ns, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(flag, status, limit_ns);
+    return cudaGetLastError();
+}
+
 static int g_eig_smem_max = 0;
 
 cudaError_t eig_init_attributes() {

@@ -97,3 +97,7 @@ def test_null_arguments(lib):
     assert lib.selr_sync_status(None, None) == 1
     assert lib.selr_solve(None, None, None, None, None, None, None) == 1
     assert lib.selr_plan_workspace_bytes(None) == 0
+    # the wait self-test validates its arguments before any CUDA call
+    assert lib.selr_selftest_wait(0, 0) == 1
+    assert lib.selr_selftest_wait(2, 100) == 1
+    assert lib.selr_selftest_wait(1, 2000001) == 1

@@ -6,6 +6,8 @@ number of iterations (FP32 CUDA path vs FP64 oracle), for the batched
 """
 import os
 
+import time
+
 import numpy as np
 import pytest
 
@@ -190,6 +192,24 @@ def test_device_status_reports_sweep_cap_and_nonfinite():
     plan2 = api.Plan(api.Desc.from_workload(wl))
     api.selr_solve(plan2, _dev(Y), _dev(inp["mask"], torch.uint8), X)
     assert api.selr_sync_status(plan2) == 5         # SELR_ERR_NONFINITE
+
+
+def test_handoff_wait_times_out_and_context_survives():
+    """The bounded wait of the eigensolver's launch chain (k_gram_tc -> k_tridiag ->
+    k_eigvec -> k_apply_stream), run on a flag that nothing sets, gives up after its
+    limit with SELR_ERR_TIMEOUT; a flag that is set is consumed at once; the context
+    stays usable (an eigensolver solve afterwards is clean)."""
+    api = _api()
+    assert api.selr_selftest_wait(True, 1000) == 0
+    t0 = time.perf_counter()
+    assert api.selr_selftest_wait(False, 2000) == 6      # SELR_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    wl = synth.get_config("shlr_4c_64").with_(n_iter=2)
+    inp = synth.make_inputs(wl)
+    plan = api.Plan(api.Desc.from_workload(wl, svd="eig"))
+    X = torch.empty_like(_dev(inp["Y"]))
+    api.selr_solve(plan, _dev(inp["Y"]), _dev(inp["mask"], torch.uint8), X)
+    assert api.selr_sync_status(plan) == 0
 
 
 def test_batched_and_plain_agree_bitwise_repeatable():
