@@ -178,6 +178,7 @@ __device__ __forceinline__ int sturm_lt(const float *d, const float *f2, int n, 
     float q = d[0] - x;
     if (fabsf(q) < pivmin) q = -pivmin;
     if (q < 0.f) ++cnt;
+#pragma unroll 4
     for (int k = 1; k < n; ++k) {
         q = (d[k] - x) - __fdividef(f2[k - 1], q);
         if (fabsf(q) < pivmin) q = -pivmin;
@@ -753,7 +754,7 @@ __host__ __device__ inline EvLayout ev_layout(int n, int chunk, int st) {
 // thread-per-vector solves and the warp-per-vector reductions avoid bank
 // conflicts.
 template <int IV_CHUNK, int IV_ST, int NT>
-__global__ void __launch_bounds__(NT) k_eigvec(GroupSet gs, int mat_begin, EigArgs a) {
+__global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs, int mat_begin, EigArgs a) {
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char vsm[];
     __shared__ float red[4];
@@ -903,16 +904,35 @@ __global__ void __launch_bounds__(NT) k_eigvec(GroupSet gs, int mat_begin, EigAr
             Yc[idx] = cscale(ph[i], zv[i * IV_ST + w]);
         }
         __syncthreads();
+        // reflectors kb, kb-1, ..., kb-EV_HB+1 (reflector k has n-k-1 entries) are staged in
+        // shared memory per batch; the next batch is loaded into registers while the current
+        // one is applied, so the L2 latency of the loads is off the critical path
+        constexpr int EV_PF = (480 + NT - 1) / NT;          // entries per thread and reflector
+        cf pf[EV_HB][EV_PF];
+        auto load_batch = [&](int kb) {
+#pragma unroll
+            for (int b = 0; b < EV_HB; ++b) {
+                const int k = kb - b;
+#pragma unroll
+                for (int u = 0; u < EV_PF; ++u) {
+                    const int i = tid + u * NT;
+                    pf[b][u] = (k >= 0 && i < n - k - 1) ? Gglob[colstart(k, n) + 1 + i] : mk(0.f, 0.f);
+                }
+            }
+        };
+        load_batch(n - 3);
         for (int kb = n - 3; kb >= 0; kb -= EV_HB) {
             const int nbat = min(EV_HB, kb + 1);
-            // stage reflectors kb, kb-1, ..., kb-nbat+1 (reflector k has n-k-1 entries)
-            for (int b = 0; b < nbat; ++b) {
-                const int k = kb - b;
-                const int m = n - k - 1;
-                const cf *hv = Gglob + colstart(k, n) + 1;
-                for (int i = tid; i < m; i += NT) hb[(long long)b * n + i] = hv[i];
+#pragma unroll
+            for (int b = 0; b < EV_HB; ++b) {
+#pragma unroll
+                for (int u = 0; u < EV_PF; ++u) {
+                    const int i = tid + u * NT;
+                    if (b < nbat && i < n - (kb - b) - 1) hb[(long long)b * n + i] = pf[b][u];
+                }
             }
             __syncthreads();
+            if (kb - EV_HB >= 0) load_batch(kb - EV_HB);     // in flight during the apply below
             for (int w = warp; w < qc; w += NW) {
                 for (int b = 0; b < nbat; ++b) {
                     const int k = kb - b;
