@@ -45,6 +45,7 @@
 #define EIG_SMEM_MAX_N 208       // packed G of order <= 208 stays in shared memory
 #define INV_ITERS 4
 #define EV_HB 8                  // Householder reflectors staged per back-transformation batch
+#define EV_BT_MI 6               // reflector entries per lane held in registers (orders <= 193)
 #define TB 4                     // trailing columns per pass of the tridiagonal sweep (8 sums per reduction)
 
 __device__ __forceinline__ long long colstart(int j, int n) { return (long long)j * (2 * n - j + 1) / 2; }
@@ -942,17 +943,45 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
                     const cf *vk = hb + (long long)b * n;
                     cf *y = Yc + (long long)w * n + k + 1;
                     float sr = 0.f, si = 0.f;
-                    for (int i = lane; i < m; i += 32) {
-                        const cf v = vk[i], yy = y[i];
-                        sr += v.x * yy.x + v.y * yy.y;
-                        si += v.x * yy.y - v.y * yy.x;
-                    }
-                    sr = wsum(sr) * tau;
-                    si = wsum(si) * tau;
-                    for (int i = lane; i < m; i += 32) {
-                        const cf v = vk[i];
-                        y[i].x -= v.x * sr - v.y * si;
-                        y[i].y -= v.x * si + v.y * sr;
+                    if (m <= 32 * EV_BT_MI) {
+                        // all loads of the reflector and of y issued together (y kept for the update)
+                        cf vv[EV_BT_MI], yv[EV_BT_MI];
+#pragma unroll
+                        for (int u = 0; u < EV_BT_MI; ++u) {
+                            const int i = lane + 32 * u;
+                            vv[u] = i < m ? vk[i] : mk(0.f, 0.f);
+                            yv[u] = i < m ? y[i] : mk(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < EV_BT_MI; ++u) {
+                            if (lane + 32 * u < m) {
+                                sr += vv[u].x * yv[u].x + vv[u].y * yv[u].y;
+                                si += vv[u].x * yv[u].y - vv[u].y * yv[u].x;
+                            }
+                        }
+                        sr = wsum(sr) * tau;
+                        si = wsum(si) * tau;
+#pragma unroll
+                        for (int u = 0; u < EV_BT_MI; ++u) {
+                            const int i = lane + 32 * u;
+                            if (i < m) {
+                                const cf v = vk[i];
+                                y[i] = mk(yv[u].x - (v.x * sr - v.y * si), yv[u].y - (v.x * si + v.y * sr));
+                            }
+                        }
+                    } else {
+                        for (int i = lane; i < m; i += 32) {
+                            const cf v = vk[i], yy = y[i];
+                            sr += v.x * yy.x + v.y * yy.y;
+                            si += v.x * yy.y - v.y * yy.x;
+                        }
+                        sr = wsum(sr) * tau;
+                        si = wsum(si) * tau;
+                        for (int i = lane; i < m; i += 32) {
+                            const cf v = vk[i];
+                            y[i].x -= v.x * sr - v.y * si;
+                            y[i].y -= v.x * si + v.y * sr;
+                        }
                     }
                     __syncwarp();
                 }
