@@ -1359,8 +1359,10 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
             } else {
                 const cf A = Av[u], D = Dv[u];
                 const cf Dn = mk(D.x + a.tau * (A.x - D.x * ib - zr[u]), D.y + a.tau * (A.y - D.y * ib - zi[u]));
-                Dp[vi] = Dn;
-                Ep[vi] = mk(zr[u] - Dn.x * ib, zi[u] - Dn.y * ib);
+                // streaming stores: D and E are not read again in this launch, so they should not
+                // evict B, whose rows the epilogue reads a second time
+                __stcs(reinterpret_cast<float2 *>(Dp + vi), make_float2(Dn.x, Dn.y));
+                __stcs(reinterpret_cast<float2 *>(Ep + vi), make_float2(zr[u] - Dn.x * ib, zi[u] - Dn.y * ib));
             }
         }
     }
