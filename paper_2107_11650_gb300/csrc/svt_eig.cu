@@ -45,7 +45,6 @@
 #define EIG_SMEM_MAX_N 208       // packed G of order <= 208 stays in shared memory
 #define INV_ITERS 4
 #define EV_HB 8                  // Householder reflectors staged per back-transformation batch
-#define EV_BT_MI 6               // reflector entries per lane held in registers (orders <= 193)
 #define TB 4                     // trailing columns per pass of the tridiagonal sweep (8 sums per reduction)
 
 __device__ __forceinline__ long long colstart(int j, int n) { return (long long)j * (2 * n - j + 1) / 2; }
@@ -102,6 +101,15 @@ __device__ __forceinline__ bool is_frozen(const Group &g, int mat, const int *ac
     if (g.kind == G_PARAM) return active[mat / g.N] == 0;
     return false;
 }
+
+// 8-byte asynchronous global -> shared copy (src_bytes 0: the destination is zero-filled and
+// nothing is read).
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ------------------------------------------------------------------- Gram
 // One CTA computes a 64x64 block (I >= J) of G = B^H B for one matrix.
@@ -725,7 +733,7 @@ __device__ __forceinline__ void gershgorin(const float *dd, const float *ff, con
 // ---------------------------------------------------------------- eigvec
 // Shared-memory layout of k_eigvec (16-byte aligned regions).
 struct EvLayout {
-    size_t ph, dd, ff, f2, taus, lam, clu, zv, lu0, lu1, lu2, llm, lpv, yc, hb, total;
+    size_t ph, dd, ff, f2, taus, lam, clu, zv, lu0, lu1, lu2, llm, lpv, yc, total;
 };
 __host__ __device__ inline EvLayout ev_layout(int n, int chunk, int st) {
     EvLayout L;
@@ -744,7 +752,6 @@ __host__ __device__ inline EvLayout ev_layout(int n, int chunk, int st) {
     L.llm = o; o += al16((size_t)st * n * 4);
     L.lpv = o; o += al16((size_t)st * n);
     L.yc = o; o += al16((size_t)chunk * n * 8);
-    L.hb = o; o += al16((size_t)EV_HB * n * 8);
     L.total = o;
     return L;
 }
@@ -760,6 +767,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
     extern __shared__ __align__(16) unsigned char vsm[];
     __shared__ float red[4];
     __shared__ int s_r, s_cst, s_wend;
+    __shared__ cf s_cm[EV_HB * EV_HB];    // C_ji of the current batch of reflectors
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
@@ -780,7 +788,6 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
     float *lu2 = (float *)(vsm + LY.lu2), *llm = (float *)(vsm + LY.llm);
     unsigned char *lpv = vsm + LY.lpv;
     cf *Yc = (cf *)(vsm + LY.yc);
-    cf *hb = (cf *)(vsm + LY.hb);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float t2 = allp ? -FLT_MAX : g.thresh * g.thresh;
     const float *td = tri_d(a, g, mat), *ttau = td + n;
@@ -905,89 +912,102 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
             Yc[idx] = cscale(ph[i], zv[i * IV_ST + w]);
         }
         __syncthreads();
-        // reflectors kb, kb-1, ..., kb-EV_HB+1 (reflector k has n-k-1 entries) are staged in
-        // shared memory per batch; the next batch is loaded into registers while the current
-        // one is applied, so the L2 latency of the loads is off the critical path
-        constexpr int EV_PF = (480 + NT - 1) / NT;          // entries per thread and reflector
-        cf pf[EV_HB][EV_PF];
-        auto load_batch = [&](int kb) {
-#pragma unroll
-            for (int b = 0; b < EV_HB; ++b) {
-                const int k = kb - b;
-#pragma unroll
-                for (int u = 0; u < EV_PF; ++u) {
-                    const int i = tid + u * NT;
-                    pf[b][u] = (k >= 0 && i < n - k - 1) ? Gglob[colstart(k, n) + 1 + i] : mk(0.f, 0.f);
+        // Reflectors are applied in batches of EV_HB, u_j = v_{kb-j} (j = 0 .. nbat-1, in the order
+        // of application), staged in shared memory by absolute row (zero on rows <= kb - j).
+        // With d_j = u_j^H y and C_ji = u_j^H u_i, applying them one after the other is
+        //   s_j = d_j - sum_{i<j} tau_i C_ji s_i,   y <- y - sum_j tau_j u_j s_j,
+        // so each vector needs one round of independent reductions per batch instead of one
+        // reduction per reflector; C (independent of y) is formed by all warps after staging.
+        // Batches are double-buffered in the inverse-iteration arrays (free from here on: zv was
+        // copied to Yc above) and copied with cp.async while the previous batch is applied.
+        cf *hbuf[2] = {(cf *)(vsm + LY.zv), (cf *)(vsm + LY.zv) + (long long)EV_HB * n};
+        auto issue_batch = [&](int kb, cf *buf) {
+            for (int j = 0; j < EV_HB; ++j) {
+                const int k = kb - j;
+                for (int row = tid; row < n; row += NT) {
+                    const bool ok = k >= 0 && row > k;
+                    cp_async8(buf + (long long)j * n + row, ok ? Gglob + colstart(k, n) + (row - k) : Gglob, ok ? 8 : 0);
                 }
             }
+            cp_async_commit();
         };
-        load_batch(n - 3);
-        for (int kb = n - 3; kb >= 0; kb -= EV_HB) {
+        issue_batch(n - 3, hbuf[0]);
+        int bsel = 0;
+        for (int kb = n - 3; kb >= 0; kb -= EV_HB, bsel ^= 1) {
             const int nbat = min(EV_HB, kb + 1);
-#pragma unroll
-            for (int b = 0; b < EV_HB; ++b) {
-#pragma unroll
-                for (int u = 0; u < EV_PF; ++u) {
-                    const int i = tid + u * NT;
-                    if (b < nbat && i < n - (kb - b) - 1) hb[(long long)b * n + i] = pf[b][u];
+            const int r0 = kb - nbat + 2;                    // first row any u_j of the batch touches
+            cf *hb = hbuf[bsel];
+            cp_async_wait_all();
+            __syncthreads();                                 // batch kb staged; the other buffer is free
+            if (kb - EV_HB >= 0) issue_batch(kb - EV_HB, hbuf[bsel ^ 1]);
+            // C_ji = u_j^H u_i, i < j, over the rows of u_i (rows > kb - i)
+            for (int pq = warp; pq < nbat * (nbat - 1) / 2; pq += NW) {
+                int j = 1, i = pq;
+                while (i >= j) { i -= j; ++j; }
+                const cf *uj = hb + (long long)j * n, *ui = hb + (long long)i * n;
+                float cr = 0.f, ci = 0.f;
+                for (int row = kb - i + 1 + lane; row < n; row += 32) {
+                    const cf x = uj[row], z = ui[row];
+                    cr += x.x * z.x + x.y * z.y;
+                    ci += x.x * z.y - x.y * z.x;
                 }
+                cr = wsum(cr);
+                ci = wsum(ci);
+                if (lane == 0) s_cm[j * EV_HB + i] = mk(cr, ci);
             }
             __syncthreads();
-            if (kb - EV_HB >= 0) load_batch(kb - EV_HB);     // in flight during the apply below
             for (int w = warp; w < qc; w += NW) {
-                for (int b = 0; b < nbat; ++b) {
-                    const int k = kb - b;
-                    const float tau = taus[k];
-                    if (tau == 0.f) continue;
-                    const int m = n - k - 1;
-                    const cf *vk = hb + (long long)b * n;
-                    cf *y = Yc + (long long)w * n + k + 1;
-                    float sr = 0.f, si = 0.f;
-                    if (m <= 32 * EV_BT_MI) {
-                        // all loads of the reflector and of y issued together (y kept for the update)
-                        cf vv[EV_BT_MI], yv[EV_BT_MI];
+                cf *y = Yc + (long long)w * n;
+                float dr[EV_HB], di[EV_HB], tj[EV_HB];
 #pragma unroll
-                        for (int u = 0; u < EV_BT_MI; ++u) {
-                            const int i = lane + 32 * u;
-                            vv[u] = i < m ? vk[i] : mk(0.f, 0.f);
-                            yv[u] = i < m ? y[i] : mk(0.f, 0.f);
-                        }
+                for (int j = 0; j < EV_HB; ++j) {
+                    dr[j] = di[j] = 0.f;
+                    tj[j] = j < nbat ? taus[kb - j] : 0.f;
+                }
+                for (int row = r0 + lane; row < n; row += 32) {
+                    const cf yy = y[row];
 #pragma unroll
-                        for (int u = 0; u < EV_BT_MI; ++u) {
-                            if (lane + 32 * u < m) {
-                                sr += vv[u].x * yv[u].x + vv[u].y * yv[u].y;
-                                si += vv[u].x * yv[u].y - vv[u].y * yv[u].x;
-                            }
-                        }
-                        sr = wsum(sr) * tau;
-                        si = wsum(si) * tau;
-#pragma unroll
-                        for (int u = 0; u < EV_BT_MI; ++u) {
-                            const int i = lane + 32 * u;
-                            if (i < m) {
-                                const cf v = vk[i];
-                                y[i] = mk(yv[u].x - (v.x * sr - v.y * si), yv[u].y - (v.x * si + v.y * sr));
-                            }
-                        }
-                    } else {
-                        for (int i = lane; i < m; i += 32) {
-                            const cf v = vk[i], yy = y[i];
-                            sr += v.x * yy.x + v.y * yy.y;
-                            si += v.x * yy.y - v.y * yy.x;
-                        }
-                        sr = wsum(sr) * tau;
-                        si = wsum(si) * tau;
-                        for (int i = lane; i < m; i += 32) {
-                            const cf v = vk[i];
-                            y[i].x -= v.x * sr - v.y * si;
-                            y[i].y -= v.x * si + v.y * sr;
+                    for (int j = 0; j < EV_HB; ++j) {
+                        if (j < nbat) {
+                            const cf u = hb[(long long)j * n + row];
+                            dr[j] += u.x * yy.x + u.y * yy.y;
+                            di[j] += u.x * yy.y - u.y * yy.x;
                         }
                     }
-                    __syncwarp();
+                }
+#pragma unroll
+                for (int j = 0; j < EV_HB; ++j) {
+                    dr[j] = wsum(dr[j]);
+                    di[j] = wsum(di[j]);
+                }
+                // forward substitution (every lane), then dr, di <- tau_j s_j
+#pragma unroll
+                for (int j = 0; j < EV_HB; ++j) {
+                    float sr = dr[j], si = di[j];
+#pragma unroll
+                    for (int i = 0; i < j; ++i) {
+                        const cf c = s_cm[j * EV_HB + i];
+                        sr -= c.x * dr[i] - c.y * di[i];
+                        si -= c.x * di[i] + c.y * dr[i];
+                    }
+                    dr[j] = tj[j] * sr;
+                    di[j] = tj[j] * si;
+                }
+                for (int row = r0 + lane; row < n; row += 32) {
+                    float ar = 0.f, ai = 0.f;
+#pragma unroll
+                    for (int j = 0; j < EV_HB; ++j) {
+                        if (j < nbat) {
+                            const cf u = hb[(long long)j * n + row];
+                            ar += u.x * dr[j] - u.y * di[j];
+                            ai += u.x * di[j] + u.y * dr[j];
+                        }
+                    }
+                    y[row] = mk(y[row].x - ar, y[row].y - ai);
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
         for (int idx = tid; idx < qc * n; idx += NT) {
             const int w = idx / n, i = idx - w * n;
             const cf y = Yc[idx];
