@@ -156,7 +156,10 @@ def _lowrank_plus_noise(rng, nmat, rows, cols, rank, noise):
 
 @pytest.mark.parametrize("svd", ["eig", "jacobi"])
 @pytest.mark.parametrize("shape", [(57, 32), (241, 192), (181, 192), (5, 32), (17, 9), (9, 17), (33, 33),
-                                   (241, 384), (1, 7), (7, 1), (2, 2)])
+                                   (241, 384), (1, 7), (7, 1), (2, 2),
+                                   # orders 193-208 (seven rows per lane), > 256 (global-memory
+                                   # reduction) and the largest accepted order
+                                   (205, 210), (300, 280), (480, 480)])
 def test_svt_matches_oracle(shape, svd):
     api = _api()
     rng = np.random.default_rng(sum(shape))
