@@ -205,12 +205,22 @@ selr_status selr_svt(selr_plan *plan, void *A, int32_t nmat, int32_t rows, int32
  * attributes) for that device, so make it before any stream capture.  All
  * calls on one device share the scratch: calls that may overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the
- * caller.  Device-side conditions (sweep cap reached) are not reported.
+ * caller.  Device-side conditions (sweep cap reached, non-finite input) are
+ * read back with selr_svt_noalloc_status.
  * rank_out: device int32[nmat] receiving #{sigma > t}, or NULL. */
 #define SELR_SVT_NOALLOC_MAX_ELEMS (1 << 20)
 #define SELR_SVT_NOALLOC_MAX_MATS 65536
 selr_status selr_svt_noalloc(void *A, int32_t nmat, int32_t rows, int32_t cols, float thresh,
                              int32_t max_sweeps, float tol, int32_t *rank_out, selr_stream stream);
+
+/* Condition recorded by the last selr_svt_noalloc call on the current device
+ * (no counterpart in the paper): synchronises `stream` (use the stream of that
+ * call), reads the fixed status word of the allocation-free scratch and
+ * returns SELR_ERR_NONFINITE (NaN/Inf met), SELR_ERR_NO_CONVERGENCE (a matrix
+ * reached max_sweeps) or SELR_OK; SELR_ERR_CUDA if a CUDA call fails.  The
+ * word is cleared by the next selr_svt_noalloc call, not by this read.
+ * Allocates nothing. */
+selr_status selr_svt_noalloc_status(selr_stream stream);
 
 /* Real adjoint of the lift (the transpose appearing in Eq. 15 / S7):
  * x_out = L^T E for the family `axis`.  Plain channel j contributes

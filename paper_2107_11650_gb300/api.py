@@ -232,15 +232,41 @@ def selr_svt(plan: Plan, A, thresh: float, rank_out=None, stream=None):
           "selr_svt")
 
 
+def _same_device(t, dev, name):
+    if t is not None and isinstance(t, torch.Tensor) and t.device != dev:
+        raise ValueError(f"{name} is on {t.device}, expected {dev}")
+
+
 def selr_svt_noalloc(A, thresh: float, max_sweeps: int = 30, tol: float = 2.0e-6, rank_out=None, stream=None):
-    """Allocation-free S_t of A [nmat][rows][cols] in place (no plan; fixed library scratch)."""
+    """Allocation-free S_t of A [nmat][rows][cols] in place (no plan; fixed library scratch).
+
+    The library resolves its scratch on the CURRENT device, so the call is made
+    with A's device current and, by default, on that device's current stream."""
     lib = _lib.load()
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError("A must be a CUDA tensor")
     if A.dim() != 3:
         raise ValueError("A must be [nmat][rows][cols]")
+    _same_device(rank_out, A.device, "rank_out")
+    if stream is not None and stream.device != A.device:
+        raise ValueError(f"stream is on {stream.device}, expected {A.device}")
     nmat, rows, cols = A.shape
-    check(lib.selr_svt_noalloc(_ptr(A, torch.complex64, "A"), nmat, rows, cols, float(thresh), int(max_sweeps),
-                               float(tol), _ptr(rank_out, torch.int32, "rank_out", nmat, allow_none=True),
-                               _stream(stream)), "selr_svt_noalloc")
+    with torch.cuda.device(A.device):
+        s = torch.cuda.current_stream(A.device) if stream is None else stream
+        check(lib.selr_svt_noalloc(_ptr(A, torch.complex64, "A"), nmat, rows, cols, float(thresh),
+                                   int(max_sweeps), float(tol),
+                                   _ptr(rank_out, torch.int32, "rank_out", nmat, allow_none=True),
+                                   ctypes.c_void_p(s.cuda_stream)), "selr_svt_noalloc")
+
+
+def selr_svt_noalloc_status(device=None, stream=None) -> int:
+    """Synchronise and return the condition of the last selr_svt_noalloc call on
+    `device` (0 = SELR_OK, 4 = sweep cap reached, 5 = non-finite values)."""
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        s = torch.cuda.current_stream(dev) if stream is None else stream
+        return int(lib.selr_svt_noalloc_status(ctypes.c_void_p(s.cuda_stream)))
 
 
 def selr_adjoint(plan: Plan, axis: str, E, x_out, stream=None):

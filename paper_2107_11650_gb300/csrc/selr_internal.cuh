@@ -160,9 +160,18 @@ cudaError_t launch_svt_apply(const GroupSet &gs, int mat_begin, int mat_count, c
 // after its last write, the consuming CTAs wait for it (acquire, bounded) before
 // their first read.  The wait always ends, because dependents are only
 // scheduled once every CTA of the producing kernel is resident.  Flags read by
-// one CTA per matrix are cleared by that CTA; the k_eigvec -> apply flags (read
-// by every row tile of a matrix) are cleared by the next k_tridiag of the
-// matrix, which starts after the previous apply has completed.
+// one CTA per matrix are cleared by that CTA as it consumes them.  The
+// k_eigvec -> apply flags are read by every row tile of a matrix, so no
+// consumer can clear them; k_tridiag clears them instead, and it does so
+// BEFORE its griddepcontrol.launch_dependents (store, fence, block barrier,
+// then the trigger).  k_eigvec is scheduled only after every k_tridiag CTA has
+// triggered, and the apply only after every k_eigvec CTA has, so by the time
+// any apply tile polls, the flag of the previous call is gone and only this
+// call's k_eigvec can set it again.  (Clearing it after the trigger, as an
+// earlier version did, let an apply tile see the previous call's flag while
+// k_tridiag was still waiting for the tensor-core Gram, and use stale ranks
+// and eigenvectors.)  k_tridiag itself starts after the previous call's apply
+// kernels have completed: the chain's first kernel is an ordinary launch.
 #define READY_WAIT_NS 2000000000ull
 
 __device__ __forceinline__ unsigned long long eig_globaltimer() {
@@ -183,6 +192,16 @@ __device__ __forceinline__ void publish_flag(unsigned *f) {
         __threadfence();
         asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(1u) : "memory");
     }
+}
+
+// Start of a CTA whose dependents poll `f`: clear it and make the store visible
+// at GPU scope before any thread of the CTA executes the programmatic trigger.
+__device__ __forceinline__ void clear_flag_before_release(unsigned *f) {
+    if (f && threadIdx.x == 0) {
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(0u) : "memory");
+        __threadfence();
+    }
+    __syncthreads();
 }
 
 // Start of a consuming CTA: wait (at most limit_ns, then ST_TIMEOUT) for the

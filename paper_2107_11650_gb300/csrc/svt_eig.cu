@@ -315,10 +315,10 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
+    clear_flag_before_release(flag_of(a.vready, g, mat));
     pdl_release_dependents();
     if (is_frozen(g, mat, a.active)) return;
     wait_flag(flag_of(a.gready, g, mat), a.status, true);
-    if (a.vready && threadIdx.x == 0) a.vready[g.moff + mat] = 0u;
     const int n = g.s;
     const long long pk = (long long)n * (n + 1) / 2;
     const int c0 = HYB ? tridiag_c0(n, (size_t)budget) : 0;   // columns kept in global memory
@@ -560,10 +560,10 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
+    clear_flag_before_release(flag_of(a.vready, g, mat));
     pdl_release_dependents();
     if (is_frozen(g, mat, a.active)) return;
     wait_flag(flag_of(a.gready, g, mat), a.status, true);
-    if (a.vready && threadIdx.x == 0) a.vready[g.moff + mat] = 0u;
     const int n = g.s;
     const long long pk = (long long)n * (n + 1) / 2;
     cf *Gs = a.Gp + g.poff + (long long)mat * pk;

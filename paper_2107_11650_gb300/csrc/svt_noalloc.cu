@@ -16,8 +16,9 @@
 // cudaGetSymbolAddress once per device, with that device current, on the
 // first call made on it.  That first call should therefore come before any
 // stream capture.  All calls on a device share the scratch, which keeps the
-// previous call's contents; the status word is cleared on every call, and
-// calls that overlap on the GPU (different streams or host threads) race.
+// previous call's contents; the status word is cleared on every call (and can
+// be read back with selr_svt_noalloc_status), and calls that overlap on the
+// GPU (different streams or host threads) race.
 #include "selr_internal.cuh"
 
 #include <math.h>
@@ -125,5 +126,27 @@ extern "C" selr_status selr_svt_noalloc(void *A, int32_t nmat, int32_t rows, int
         cudaGetLastError();
         return SELR_ERR_CUDA;
     }
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_svt_noalloc_status(selr_stream stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return SELR_ERR_CUDA;
+    }
+    NoallocPtrs p;
+    selr_status st = noalloc_setup(dev, &p);
+    if (st != SELR_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    unsigned h = 0;
+    if (cudaMemcpyAsync(&h, p.status, sizeof(unsigned), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess) {
+        cudaGetLastError();
+        return SELR_ERR_CUDA;
+    }
+    if (h & ST_TIMEOUT) return SELR_ERR_TIMEOUT;
+    if (h & ST_NONFINITE) return SELR_ERR_NONFINITE;
+    if (h & ST_NOCONV) return SELR_ERR_NO_CONVERGENCE;
     return SELR_OK;
 }

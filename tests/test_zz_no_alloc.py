@@ -5,8 +5,9 @@ stream capture, services with a fixed memory budget, frameworks that own all
 device allocations) use selr_svt_noalloc instead of a plan.  This file checks,
 through the C ABI, that two consecutive calls give the same S_t as the
 plan-based selr_svt within the SVT tolerance of the other tests (1e-4
-relative, FP32 Jacobi), that oversize inputs are rejected with
-SELR_ERR_SHAPE, and that a call needs no plan.  It is collected last so that a
+relative, FP32 Jacobi) and the FP64 oracle's S_t, that the status word reads
+clean after them, that oversize inputs are rejected with SELR_ERR_SHAPE, and
+that a call needs no plan.  It is collected last so that a
 run stopping at the first failure has already run every other test, and it
 passes both alone in a fresh process and after the rest of the suite.
 """
@@ -14,6 +15,8 @@ import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
+
+from oracle import svt as osvt
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -58,6 +61,17 @@ def test_noalloc_matches_plan_svt_twice_in_a_row():
         assert err < TOL, err
         sv = np.linalg.svd(A, compute_uv=False)
         assert (rank.cpu().numpy() == (sv > t).sum(axis=1)).all()
+        assert api.selr_svt_noalloc_status() == 0
+        exact = osvt.svt(A, t)
+        per_mat = np.linalg.norm(z - exact, axis=(1, 2)) / np.linalg.norm(exact, axis=(1, 2))
+        assert per_mat.max() < TOL, per_mat
+
+
+def test_noalloc_checks_devices_of_its_arguments():
+    from paper_2107_11650_gb300 import api
+    A = torch.zeros((2, 8, 8), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ValueError):
+        api.selr_svt_noalloc(A, 1.0, rank_out=torch.zeros(2, dtype=torch.int32))
 
 
 def test_noalloc_rejects_oversize_and_bad_arguments():
