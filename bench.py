@@ -134,11 +134,9 @@ def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
 
 
 def gram_for(args, model2d):
-    """Gram precision of the plans: --gram if given, else 3xtf32 for the 2D models and fp32
-    for the parameter models (where the tensor-core Gram misses the 1e-4 accuracy bar)."""
-    if args.gram:
-        return args.gram
-    return "3xtf32" if model2d else "fp32"
+    """Gram precision the plans start from (before autotuning): --gram if given, else
+    3xtf32 (FP32-level accuracy on every model)."""
+    return args.gram or "3xtf32"
 
 
 def instance_workload(wl, rank):
@@ -609,8 +607,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--svd", default="eig", choices=["eig", "jacobi"])
     ap.add_argument("--gram", default=None, choices=["fp32", "tf32", "3xtf32"],
-                    help="Gram precision before autotuning (default: 3xtf32 for SHLR / SHLR-V, fp32 for "
-                         "the parameter models, where the tensor-core Gram misses the 1e-4 accuracy bar)")
+                    help="Gram precision before autotuning (default: 3xtf32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--allow-tf32", action="store_true")

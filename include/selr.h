@@ -91,12 +91,9 @@ typedef enum {
     SELR_GRAM_TF32 = 1,    /* one TF32 product per term: ~1e-3 relative error in G             */
     SELR_GRAM_3XTF32 = 3   /* x = x_hi + x_lo split, three TF32 products: about FP32 accuracy  */
 } selr_gram_precision;
-/* Measured against the FP64 oracle: SHLR / SHLR-V reconstructions with 3XTF32 stay at
- * FP32 level (1.8e-7 after 30 iterations, 12-coil 256x256).  The parameter-dimension
- * models do not (SHLR-P / SHLR-VP, 2 coils 8x48x8 echoes, 10 iterations: 1.9e-3 against
- * < 1e-4 with FP32), although an emulation of the 3xTF32 arithmetic on the same lifts
- * stays at FP32 level: a defect of the tensor-core path on those plans, not yet found.
- * Use FP32 for SHLR-P / SHLR-VP; the autotuner does. */
+/* Measured against the FP64 oracle: reconstructions with 3XTF32 stay at FP32 level
+ * (SHLR 12-coil 256x256: 1.8e-7 after 30 iterations; SHLR-P / SHLR-VP 2 coils 8x48x8
+ * echoes: below 1e-4 after 10 iterations, as with FP32). */
 
 /* Problem description (Sec. III; Algorithms S1 and S2). */
 typedef struct {
@@ -261,9 +258,7 @@ selr_status selr_solve(selr_plan *plan, const void *Y, const uint8_t *mask, void
  * (2 iterations each) of the caller's problem Y / mask (as for selr_solve;
  * X_scratch receives throw-away images) and keeps the fastest settings in the
  * plan: with SELR_SVD_EIG the Gram precision among the modes of FP32-level
- * accuracy (SELR_GRAM_FP32, SELR_GRAM_3XTF32 for SHLR / SHLR-V; SELR_GRAM_FP32
- * alone for SHLR-P / SHLR-VP, see selr_gram_precision;
- * also SELR_GRAM_TF32 when flags & 1) and the number of eigenvectors refined per inverse-iteration
+ * accuracy (SELR_GRAM_FP32, SELR_GRAM_3XTF32; also SELR_GRAM_TF32 when flags & 1) and the number of eigenvectors refined per inverse-iteration
  * pass (8 or 16); with SELR_SVD_JACOBI the sweep cap (twice the largest
  * number of sweeps a matrix needed, + 2, if below the current cap and no
  * matrix reached it).

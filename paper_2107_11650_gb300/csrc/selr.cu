@@ -1179,14 +1179,7 @@ extern "C" selr_status selr_plan_autotune(selr_plan *p, const void *Y, const uin
         }
     } else {
         int grams[3] = {SELR_GRAM_FP32, SELR_GRAM_3XTF32, SELR_GRAM_TF32};
-        int ngram = (flags & 1) ? 3 : 2;
-        if (!p->model2d) {
-            // on the parameter-dimension models the tensor-core Gram misses FP32 accuracy (relative
-            // error ~2e-3 after 10 iterations against < 1e-4 with FP32; cause not yet found, an
-            // emulation of the 3xTF32 arithmetic stays at FP32 level): FP32 only (TF32 on request)
-            grams[1] = SELR_GRAM_TF32;
-            ngram = (flags & 1) ? 2 : 1;
-        }
+        const int ngram = (flags & 1) ? 3 : 2;
         const int chunks[2] = {16, 8};
         float best = 3.4e38f;
         int bg = p->d.gram_precision, bc = p->ev_chunk;
