@@ -160,8 +160,70 @@ def whole_job_value(world, steps, ms):
 
 
 def flops_svd_per_matrix(l, s):
-    """Algorithmic flops of one SVD (Gram + Hermitian eigensolve convention): 8 l s^2 + 36 s^3."""
+    """Textbook flops of one SVD (Gram + full Hermitian eigensolve): 8 l s^2 + 36 s^3."""
     return 8.0 * l * s * s + 36.0 * s ** 3
+
+
+# Flops of the eigensolver SVT as this method does it, per l x s matrix with r
+# singular values above t (real flops; a complex multiply-add is 8):
+#   Gram G = B^H B, lower triangle with diagonal         4 l s (s + 1)
+#   Householder tridiagonalisation of the Hermitian G      (16/3) s^3
+#   multisection of each of the r eigenvalues:  12 rounds x 32 Sturm counts of s steps,
+#     4 flops a step (a subtraction, a division, a comparison folded into a multiply-add)
+#                                                          1536 s r
+#   inverse iteration (LU of the shifted tridiagonal and two solves, three passes)  90 s r
+#   back-transformation of r vectors through s - 1 reflectors          8 s^2 r
+#   apply Z = (B V) diag(h) V^H and the multiplier update            16 l s r
+def method_flops(l, s, r):
+    return {"gram": 4.0 * l * s * (s + 1),
+            "tridiag": 16.0 / 3.0 * s ** 3,
+            "eigvec": (1536.0 + 90.0) * s * r + 8.0 * s * s * r,
+            "apply": 16.0 * l * s * r}
+
+
+def step_bytes(plan, model2d):
+    """Algorithmic HBM bytes of one ADMM iteration: the persistent multipliers D of
+    every lifted matrix read and written once, plus the k-space sized passes (adjoint
+    output, the DC's reads of Y, mask, both adjoints and K and its write, the FFTs of
+    the adjoints and of K to the two hybrid arrays): about 16 complex k-space arrays."""
+    fams = ("row", "col") if model2d else ("pe", "param")
+    lift = sum(n * r * c for n, r, c in (plan.lift_shape(a) for a in fams))
+    return 2 * 8 * lift + 16 * 8 * plan.nK
+
+
+def measured_peaks(api):
+    """FP32 FMA (scalar FFMA and packed FFMA2) from libselr's probe and TF32 tensor
+    throughput from a cuBLAS FP32 GEMM with TF32 allowed (8192^3, best of 5)."""
+    import torch
+    out = {}
+    try:
+        f1, _ = api.selr_probe_fp32_peak(False, 4096)
+        f2, _ = api.selr_probe_fp32_peak(True, 4096)
+        out.update(fp32_ffma_tflops=f1, fp32_ffma2_tflops=f2, fp32_tflops=max(f1, f2))
+    except Exception as e:                      # reported, not fatal
+        out["fp32_error"] = str(e)
+    try:
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        c = a @ b
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out["tf32_tflops"] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, b, c
+        torch.cuda.empty_cache()
+    except Exception as e:
+        out["tf32_error"] = str(e)
+    return out
 
 
 def run_gpu(args, rank, world):
@@ -217,6 +279,8 @@ def run_gpu(args, rank, world):
         ms = max_over_ranks(e0.elapsed_time(e1), world)
         clocks = clk.stop() if clk else None
         st2 = api.selr_sync_status(plan, stream)
+        if mode == "batched" and args.svd == "eig":
+            results["rank_sums"] = api.selr_plan_rank_sums(plan, stream)   # ranks over the timed iterations
         # stage split, outside the timed region: the same K iterations with one graph per
         # stage and events between the stages (the stage boundaries cut the programmatic
         # launch chain of the eigensolver, so these stage times add up to more than ms)
@@ -235,24 +299,42 @@ def run_gpu(args, rank, world):
         else:
             plan.close()
     plan = results["plan"]
-    st_ = results["batched"]["stages"]
-    # algorithmic flops per launch of each SVT stage, summed over both lift families:
-    # 8 l s^2 (Gram), 36 s^3 (Hermitian eigensolve), 8 l s^2 (apply)
-    algo = {"gram": 0.0, "svd": 0.0, "apply": 0.0}
-    for ax in (("row", "col") if model2d else ("pe", "param")):
-        nm_, r_, c_ = plan.lift_shape(ax)
-        l, s = max(r_, c_), min(r_, c_)
-        algo["gram"] += nm_ * 8.0 * l * s * s
-        algo["apply"] += nm_ * 8.0 * l * s * s
-        algo["svd"] += nm_ * (flops_svd_per_matrix(l, s) if args.svd == "jacobi" else 36.0 * s ** 3)
-    dom = max(algo, key=lambda k: st_[k][0])
-    ms_dom = st_[dom][0] / max(st_[dom][1], 1)
-    jac = dict(ms=ms_dom, flops=algo[dom], stage=dom)
+    jac = work_model(plan, model2d, args.svd, results.get("rank_sums"), results["batched"]["stages"])
     e2e = time_e2e(plan, Yh, mh, stream, reps=2)
     e2e_ms = max_over_ranks(1000.0 * plan.desc.max_iter / e2e["value"], world)
     e2e["value"] = whole_job_value(world, plan.desc.max_iter, e2e_ms)
     results["accuracy"] = accuracy_vs_oracle(plan, wl, Y, mask, stream) if rank == 0 else None
     return results, jac, e2e, wl
+
+
+def work_model(plan, model2d, svd, rank_sums, stages):
+    """Per-iteration algorithmic work of the batched step: flops by kind (the method's
+    own count, method_flops, with each family's mean rank over the timed iterations),
+    the SVD stage's flops per launch, and its measured duration (stage-profiled run)."""
+    fams = ("row", "col") if model2d else ("pe", "param")
+    tot = {"gram": 0.0, "tridiag": 0.0, "eigvec": 0.0, "apply": 0.0, "small_svt": 0.0}
+    ranks = {}
+    m0 = 0
+    for ax in fams:
+        nm_, r_, c_ = plan.lift_shape(ax)
+        l, s = max(r_, c_), min(r_, c_)
+        if s <= 8 and l <= 64:                 # warp-per-matrix Jacobi family: textbook count
+            tot["small_svt"] += nm_ * 2.0 * flops_svd_per_matrix(l, s)
+        elif svd == "jacobi":
+            tot["small_svt"] += nm_ * 2.0 * flops_svd_per_matrix(l, s)
+        else:
+            rbar = 0.0
+            if rank_sums is not None:
+                sums, it = rank_sums
+                rbar = float(sums[m0:m0 + nm_].sum()) / max(it * nm_, 1)
+            ranks[ax] = rbar
+            for k, v in method_flops(l, s, rbar).items():
+                tot[k] += nm_ * v
+        m0 += nm_
+    st_ = stages
+    ms_svd = st_["svd"][0] / max(st_["svd"][1], 1)
+    return dict(ms=ms_svd, flops=tot["tridiag"] + tot["eigvec"], stage="svd", flops_by_kind=tot, mean_rank=ranks,
+                bytes=step_bytes(plan, model2d))
 
 
 def accuracy_vs_oracle(plan, wl, Y, mask, stream):
@@ -305,12 +387,14 @@ def time_e2e(plan, Yh, mh, stream, reps):
 _ORACLE_CACHE = {}
 
 
-def oracle_sample(wl, frac_mats=64):
-    """One bounded oracle step: the full X-update plus the SVTs of a sample of
-    the lifted matrices (the SVT is where the oracle's time goes).  2D models:
-    `frac_mats` row lifts; parameter models: the same fraction of the PE and
-    of the parameter lifts.  Returns (seconds, fraction of one iteration's
-    SVT work done)."""
+def oracle_sample(wl, n_svt=64):
+    """One bounded oracle step on the workload's initial state: the X-update
+    (Eq. 15 / S7) and the lifts of every matrix, timed in full, then the SVT and
+    multiplier update (Eqs. 13-17 / S5-S9) of about n_svt of the lifted matrices
+    (every k-th matrix of each family, so the sample spans the whole array),
+    timed on their own.  Returns (estimated seconds of one full
+    iteration = full part + SVT part x matrices / sampled matrices, wall seconds
+    of the step, sampled share of the SVTs)."""
     from oracle import admm as oadmm
     from oracle.svt import svt
     if wl.name not in _ORACLE_CACHE:
@@ -323,32 +407,52 @@ def oracle_sample(wl, frac_mats=64):
         t0 = time.perf_counter()
         K = s.x_update(st["Zr"], st["Zc"], st["Dr"], st["Dc"])
         LXr, LXc = s.lifts(K)
-        Z = svt(LXr[:frac_mats] + st["Dr"][:frac_mats] / b, 1.0 / b)
-        _ = st["Dr"][:frac_mats] + wl.tau * (LXr[:frac_mats] - Z)
-        dt = time.perf_counter() - t0
-        return dt, frac_mats / (LXr.shape[0] + LXc.shape[0])
-    s = oadmm.ShlrParam(inp["Y"], inp["mask"], wl)
+        t1 = time.perf_counter()
+        nt = LXr.shape[0] + LXc.shape[0]
+        step = max(1, nt // max(n_svt, 1))
+        ir, ic = np.arange(0, LXr.shape[0], step), np.arange(step // 2, LXc.shape[0], step)
+        Zr = svt(LXr[ir] + st["Dr"][ir] / b, 1.0 / b)
+        Zc = svt(LXc[ic] + st["Dc"][ic] / b, 1.0 / b)
+        _ = (st["Dr"][ir] + wl.tau * (LXr[ir] - Zr), st["Dc"][ic] + wl.tau * (LXc[ic] - Zc))
+        t2 = time.perf_counter()
+        share = (len(ir) + len(ic)) / nt
+    else:
+        s = oadmm.ShlrParam(inp["Y"], inp["mask"], wl)
+        st = s.init_state()
+        t0 = time.perf_counter()
+        K = s.x_update(st["Zpe"], st["Zp"], st["Dpe"], st["Dp"])
+        LXpe, LXp = s.lifts(K)
+        t1 = time.perf_counter()
+        step = max(1, LXpe.shape[0] // max(n_svt, 1))
+        ipe, ipp = np.arange(0, LXpe.shape[0], step), np.arange(0, LXp.shape[0], step)
+        share = len(ipe) / LXpe.shape[0]
+        Z1 = svt(LXpe[ipe] + st["Dpe"][ipe] / b, 1.0 / b)
+        Z2 = svt(LXp[ipp] + st["Dp"][ipp] / b, wl.lam2 / b)
+        _ = (st["Dpe"][ipe] + wl.tau * (LXpe[ipe] - Z1), st["Dp"][ipp] + wl.tau * (LXp[ipp] - Z2))
+        t2 = time.perf_counter()
+    return (t1 - t0) + (t2 - t1) / share, t2 - t0, share
+
+
+def cpu_baseline(wl, iters=2):
+    """The oracle timed over `iters` full ADMM iterations of the workload (the first
+    iterations of Algorithm S1 / S2 from the initial state); cores = CPU time / wall
+    time of the run (the threads the BLAS and FFT actually kept busy)."""
+    from oracle import admm as oadmm
+    if wl.name not in _ORACLE_CACHE:
+        _ORACLE_CACHE[wl.name] = synth.make_inputs(wl)
+    inp = _ORACLE_CACHE[wl.name]
+    two_d = wl.model in ("SHLR", "SHLR_V")
+    s = oadmm.Shlr2D(inp["Y"], inp["mask"], wl) if two_d else oadmm.ShlrParam(inp["Y"], inp["mask"], wl)
     st = s.init_state()
-    t0 = time.perf_counter()
-    K = s.x_update(st["Zpe"], st["Zp"], st["Dpe"], st["Dp"])
-    LXpe, LXp = s.lifts(K)
-    npe = max(1, LXpe.shape[0] * frac_mats // 512)
-    npp = max(1, LXp.shape[0] * frac_mats // 512)
-    Z1 = svt(LXpe[:npe] + st["Dpe"][:npe] / b, 1.0 / b)
-    Z2 = svt(LXp[:npp] + st["Dp"][:npp] / b, wl.lam2 / b)
-    _ = (st["Dpe"][:npe] + wl.tau * (LXpe[:npe] - Z1), st["Dp"][:npp] + wl.tau * (LXp[:npp] - Z2))
-    dt = time.perf_counter() - t0
-    return dt, npe / LXpe.shape[0]
-
-
-def cpu_baseline(wl, steps=1):
-    vals = []
-    for _ in range(steps):
-        dt, frac = oracle_sample(wl)
-        vals.append(frac / dt)             # iterations/s (scaled by the SVT fraction)
-    return {"value": float(np.median(vals)), "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 NumPy oracle on {wl.name}: full X-update + SVTs of 1/8 of the lifted matrices of one "
-                      "ADMM iteration, scaled to a full iteration by that fraction"}
+    act = None if two_d else np.ones(wl.M, bool)
+    c0, t0 = time.process_time(), time.perf_counter()
+    for _ in range(iters):
+        st, _ = s.step(st) if two_d else s.step(st, act)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    return {"value": iters / wall, "unit": "iters/s", "cores": round(cpu / wall, 1), "host_cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"FP64 NumPy oracle on {wl.name}: {iters} full ADMM iterations timed ({wall:.1f} s)"}
 
 
 def run_reference_unrolled(args):
@@ -394,28 +498,35 @@ def run_reference_unrolled(args):
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores (rank 0 only).  A step is the bounded
+    sample of oracle_sample: value = 1 / (median estimated seconds of one full
+    iteration); ms_per_step = the measured wall time of a step."""
     if world > 1 and rank != 0:
         return None
     if args.config == "unrolled_16_uneven":
         return run_reference_unrolled(args)
     wl = synth.get_config(args.config)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle_sample(wl, frac_mats=8)
-    vals = []
-    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_sample(wl, n_svt=8)
+    est, walls = [], []
+    c0, t0 = time.process_time(), time.perf_counter()
     for _ in range(args.steps):
-        dt, frac = oracle_sample(wl, frac_mats=16)
-        vals.append(frac / dt)
+        e, w, share = oracle_sample(wl, n_svt=64)
+        est.append(e)
+        walls.append(w)
     wall = time.perf_counter() - t0
-    v = float(np.median(vals))
+    cores = (time.process_time() - c0) / wall
+    v = 1.0 / float(np.median(est))
+    sample = (f"per step: X-update and lifts of one ADMM iteration timed in full, SVT + multiplier update of "
+              f"{share:.4f} of the lifted matrices timed and scaled by 1/{share:.4f}")
     line = {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(walls)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": wl.name, "coils": wl.J, "size": [wl.M, wl.N], "window": wl.window,
                        "model": wl.model, "mask": f"{wl.mask} R={wl.R} acs={wl.n_acs}"},
-            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "per step: full X-update + SVTs of 16 of 512 lifted matrices, "
-                                       "scaled to one iteration by the SVT share"},
+            "iteration_s_estimated": float(np.median(est)),
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": round(cores, 1), "host_cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line))
@@ -634,10 +745,28 @@ def main():
         return
     b = results["batched"]
     value = whole_job_value(world, b["steps"], b["ms"])
+    from paper_2107_11650_gb300 import api
     peaks = _peaks()
+    mp = measured_peaks(api)
     smax = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * smax * 1e6 / 1e12          # TFLOP/s, FP32 FMA pipe at max SM clock
+    if "fp32_tflops" in mp:
+        fp32_peak, fp32_src = mp["fp32_tflops"], ("measured: selr_probe_fp32_peak, FP32 FMA chains on every SM "
+                                                  f"(FFMA {mp['fp32_ffma_tflops']:.1f}, FFMA2 "
+                                                  f"{mp['fp32_ffma2_tflops']:.1f} TFLOP/s; the larger)")
+    else:
+        fp32_peak, fp32_src = 152 * 128 * 2 * smax * 1e6 / 1e12, "derived: 152 SMs x 128 lanes x 2 x max SM clock"
+    tf32_peak = mp.get("tf32_tflops")
     achieved = jac["flops"] / (jac["ms"] / 1000.0) / 1e12
+    gram = (results.get("tuning") or {}).get("gram", gram_for(args, wl.model in ("SHLR", "SHLR_V")))
+    fk = jac["flops_by_kind"]
+    p_tc = {"fp32": fp32_peak, "tf32": tf32_peak, "3xtf32": (tf32_peak / 3.0) if tf32_peak else None}.get(gram)
+    hbm = peaks.get("hbm_gbs", 6800.3)
+    t_star = None
+    if p_tc:
+        t_star = 1e3 * (fk["gram"] / (p_tc * 1e12)
+                        + (fk["tridiag"] + fk["eigvec"] + fk["apply"] + fk["small_svt"]) / (fp32_peak * 1e12)
+                        + jac["bytes"] / (hbm * 1e9))
+    t_meas = b["ms"] / b["steps"]
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": b["steps"],
         "warmup": args.warmup, "ms_per_step": b["ms"] / b["steps"], "higher_is_better": True,
@@ -650,13 +779,21 @@ def main():
         "plain": ({"value": whole_job_value(world, results["plain"]["steps"], results["plain"]["ms"]),
                    "ms_per_step": results["plain"]["ms"] / results["plain"]["steps"],
                    "steps": results["plain"]["steps"]} if "plain" in results else None),
-        "roofline": {"bound": "alu", "kernel": {"gram": "k_gram (Gram matrices of all 512 lifts)",
-                                                "svd": ("k_jacobi (one-sided Jacobi SVD)" if args.svd == "jacobi" else
-                                                        "k_tridiag + k_eigvec (Householder tridiagonal eigensolver, eigenpairs above t^2)"),
-                                                "apply": "k_apply_stream (Z and multiplier update)"}[jac["stage"]],
+        "roofline": {"bound": "alu",
+                     "kernel": ("k_jacobi (one-sided Jacobi SVD)" if args.svd == "jacobi" else
+                                "k_tridiag + k_eigvec (Householder tridiagonalisation, multisection, inverse "
+                                "iteration and back-transformation of the pairs above t^2)"),
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": None, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock",
-                     "launch_ms": jac["ms"]},
+                     "traffic": None, "peak_source": fp32_src,
+                     "flops_per_launch": jac["flops"], "launch_ms": jac["ms"],
+                     "flop_model": "(16/3) s^3 + (8 s^2 + 1626 s) r per matrix, r = mean rank over the timed "
+                                   "iterations", "mean_rank": jac["mean_rank"]},
+        "step_bound": {"T_star_ms": t_star, "T_ms": t_meas, "frac": (t_star / t_meas) if t_star else None,
+                       "formula": "F_gram / P_gram + F_fp32 / P_fp32 + bytes / BW_hbm",
+                       "flops": fk, "bytes": jac["bytes"], "gram": gram,
+                       "peaks": {"fp32_tflops": fp32_peak, "tf32_tflops": tf32_peak,
+                                 "gram_tflops": p_tc, "hbm_gbs": hbm,
+                                 "hbm_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}},
         "e2e": {"value": e2e["value"], "unit": "iters/s", "h2d_bytes_per_step": e2e["h2d"],
                 "d2h_bytes_per_step": e2e["d2h"]},
         "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in b["stages"].items()},

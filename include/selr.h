@@ -250,9 +250,35 @@ selr_status selr_dc(selr_plan *plan, const void *Y, const uint8_t *mask, void *a
  * X_out: [L][J][M][N] complex64 image.  iters_out (host, may be NULL):
  * iterations run (max over FE positions for parameter models).
  * rel_out (host, may be NULL): last relative change.
- * With tol >= 0 the call synchronises `stream` once per iteration. */
+ * state_inout (device, may be NULL): a checkpoint of the iteration of
+ * selr_state_bytes() bytes holding K, the multipliers D, E = Z - D / beta
+ * and the per-FE activity flags (the state between two passes of the loop
+ * body of Algorithm S1 / S2).  When non-NULL the final state is written to
+ * it.  resume = 1 (state_inout required) starts from that state instead of
+ * the initialisation above and runs max_iter further iterations; the state
+ * must come from a plan of the same description.  The kernels are
+ * deterministic, so k1 iterations, a checkpoint and k2 resumed iterations
+ * give bitwise the result of k1 + k2 iterations in one call.
+ * With tol >= 0 the call synchronises `stream` once per iteration.
+ * Errors: SELR_ERR_INVALID_ARG (NULL arrays, resume not 0/1, resume without
+ * a state), SELR_ERR_CUDA. */
 selr_status selr_solve(selr_plan *plan, const void *Y, const uint8_t *mask, void *X_out,
-                       int32_t *iters_out, float *rel_out, selr_stream stream);
+                       void *state_inout, int32_t resume, int32_t *iters_out, float *rel_out,
+                       selr_stream stream);
+
+/* Bytes of a solver state buffer for selr_solve's state_inout (host output). */
+selr_status selr_state_bytes(const selr_plan *plan, size_t *bytes);
+
+/* Per-matrix sums of the number of singular values above t found by the
+ * eigensolver (SELR_SVD_EIG families) over the iterations of the last
+ * selr_solve call (instrumentation: the rank histogram that sets the
+ * eigensolver's work, Eqs. 16-17).  out: host int64[n], n = the plan's total
+ * number of lifted matrices (every family, in family order); iterations
+ * (host, may be NULL): iterations of that call.  Matrices of the
+ * warp-per-matrix Jacobi family read 0.  Synchronises `stream`.
+ * SELR_ERR_UNSUPPORTED for a SELR_SVD_JACOBI plan. */
+selr_status selr_plan_rank_sums(selr_plan *plan, int64_t *out, int32_t n, int32_t *iterations,
+                                selr_stream stream);
 
 /* Autotuner (engineering extension, not in the paper): runs short solves
  * (2 iterations each) of the caller's problem Y / mask (as for selr_solve;
@@ -368,6 +394,16 @@ selr_status selr_axpby(int64_t n, float a, const void *x, float b, const void *y
 /* *out = Re sum_i conj(x_i) y_i over n complex64 elements (device), reduced
  * in a fixed order in double precision; out is a device float. */
 selr_status selr_dot_re(selr_plan *plan, int64_t n, const void *x, const void *y, float *out, selr_stream stream);
+
+/* Measurement utility (no counterpart in the paper): the FP32 FMA rate of the
+ * current device, the denominator of the eigensolver's roofline.  Runs
+ * independent FMA chains (x <- x a + b; scalar FFMA when packed = 0, packed
+ * two-lane FFMA2 when packed = 1) in 8 CTAs of 256 threads per SM for
+ * `iters` (1 .. 2^20) iterations, twice, and reports the second launch:
+ * *tflops_out (host) = 2 x FMAs / seconds / 1e12, *ms_out (host, may be
+ * NULL) its duration.  Allocates 4 bytes of device memory; synchronises
+ * the device. */
+selr_status selr_probe_fp32_peak(int32_t packed, int32_t iters, float *tflops_out, float *ms_out);
 
 /* Name of the last CUDA runtime error behind a SELR_ERR_CUDA returned on
  * the calling host thread (diagnostics; static storage). */

@@ -50,8 +50,12 @@ SIGNATURES = {
     "selr_svt_noalloc_status": (c_int32, [c_void_p]),
     "selr_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "selr_dc": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
-    "selr_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_int32),
-                             ctypes.POINTER(c_float), c_void_p]),
+    "selr_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                             ctypes.POINTER(c_int32), ctypes.POINTER(c_float), c_void_p]),
+    "selr_state_bytes": (c_int32, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "selr_plan_rank_sums": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_int64), c_int32, ctypes.POINTER(c_int32),
+                                      c_void_p]),
+    "selr_probe_fp32_peak": (c_int32, [c_int32, c_int32, ctypes.POINTER(c_float), ctypes.POINTER(c_float)]),
     "selr_sync_status": (c_int32, [c_void_p, c_void_p]),
     "selr_selftest_wait": (c_int32, [c_int32, c_int32]),
     "selr_set_iterations": (c_int32, [c_void_p, c_int32, c_float]),

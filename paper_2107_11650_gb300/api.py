@@ -200,13 +200,13 @@ class BatchPlan(Plan):
             packed[off:off + d.L * d.J * d.M * d.N].view(d.L, d.J, d.M, d.N)
 
 
-def selr_solve_batch(plan: BatchPlan, Y, mask, X_out, stream=None):
+def selr_solve_batch(plan: BatchPlan, Y, mask, X_out, state=None, resume=False, stream=None):
     """selr_solve on packed arrays of a batch plan; returns (iterations, largest relative change)."""
     it, rel = ctypes.c_int32(), ctypes.c_float()
     check(plan.lib.selr_solve(plan.handle, _ptr(Y, torch.complex64, "Y", plan.nK),
                               _ptr(mask, torch.uint8, "mask", plan.n_mask),
-                              _ptr(X_out, torch.complex64, "X_out", plan.nK), ctypes.byref(it), ctypes.byref(rel),
-                              _stream(stream)), "selr_solve")
+                              _ptr(X_out, torch.complex64, "X_out", plan.nK), _state_ptr(plan, state, resume),
+                              1 if resume else 0, ctypes.byref(it), ctypes.byref(rel), _stream(stream)), "selr_solve")
     return it.value, rel.value
 
 
@@ -284,15 +284,60 @@ def selr_dc(plan: Plan, Y, mask, adj_a, adj_b, K, rel_out=None, stream=None):
                            _ptr(rel_out, torch.float32, "rel_out", 1, allow_none=True), _stream(stream)), "selr_dc")
 
 
-def selr_solve(plan: Plan, Y, mask, X_out, stream=None):
-    """Run the reconstruction; returns (iterations, last relative change)."""
+def selr_state_bytes(plan: Plan) -> int:
+    n = ctypes.c_size_t()
+    check(plan.lib.selr_state_bytes(plan.handle, ctypes.byref(n)), "selr_state_bytes")
+    return int(n.value)
+
+
+def new_state(plan: Plan, device=None):
+    """A device buffer for selr_solve's checkpoint (uint8, selr_state_bytes long)."""
+    return torch.empty(selr_state_bytes(plan), dtype=torch.uint8, device=device or "cuda")
+
+
+def _state_ptr(plan, state, resume):
+    if state is None:
+        if resume:
+            raise ValueError("resume needs a state buffer")
+        return None
+    return _ptr(state, torch.uint8, "state", selr_state_bytes(plan))
+
+
+def selr_solve(plan: Plan, Y, mask, X_out, state=None, resume=False, stream=None):
+    """Run the reconstruction; returns (iterations, last relative change).
+
+    state: optional uint8 device buffer (new_state) that receives the final
+    checkpoint; resume=True starts from the checkpoint it holds."""
     d = plan.desc
     it, rel = ctypes.c_int32(), ctypes.c_float()
     check(plan.lib.selr_solve(plan.handle, _ptr(Y, torch.complex64, "Y", plan.nK),
                               _ptr(mask, torch.uint8, "mask", d.L * d.M * d.N),
-                              _ptr(X_out, torch.complex64, "X_out", plan.nK), ctypes.byref(it), ctypes.byref(rel),
-                              _stream(stream)), "selr_solve")
+                              _ptr(X_out, torch.complex64, "X_out", plan.nK), _state_ptr(plan, state, resume),
+                              1 if resume else 0, ctypes.byref(it), ctypes.byref(rel), _stream(stream)), "selr_solve")
     return it.value, rel.value
+
+
+def selr_plan_rank_sums(plan: Plan, stream=None):
+    """(per-matrix rank sums over the last solve as a numpy int64 array, iterations)."""
+    import numpy as np
+    fams = ("row", "col") if plan.desc.model in ("SHLR", "SHLR_V") else ("pe", "param")
+    n = sum(plan.lift_shape(a)[0] for a in fams) if not isinstance(plan, BatchPlan) else None
+    if n is None:
+        raise ValueError("rank sums of a batch plan: use the instance plans")
+    out = np.zeros(n, dtype=np.int64)
+    it = ctypes.c_int32()
+    check(plan.lib.selr_plan_rank_sums(plan.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n,
+                                       ctypes.byref(it), _stream(stream)), "selr_plan_rank_sums")
+    return out, it.value
+
+
+def selr_probe_fp32_peak(packed=False, iters=4096):
+    """Measured FP32 FMA rate of the current device: (TFLOP/s, ms of the timed launch)."""
+    lib = _lib.load()
+    tf, ms = ctypes.c_float(), ctypes.c_float()
+    check(lib.selr_probe_fp32_peak(1 if packed else 0, int(iters), ctypes.byref(tf), ctypes.byref(ms)),
+          "selr_probe_fp32_peak")
+    return tf.value, ms.value
 
 
 def selr_sync_status(plan: Plan, stream=None) -> int:

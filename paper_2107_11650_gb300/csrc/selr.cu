@@ -36,6 +36,8 @@ struct selr_plan {
     float *lam, *tri;
     int *rank;
     unsigned *gready, *ready, *vready;   // kernel hand-off flags, one per matrix (see EigArgs)
+    unsigned long long *rank_acc;        // per-matrix sum of eigensolver ranks over the last solve
+    int rank_iters;                      // iterations accumulated in rank_acc
     long long packed_elems;
     float *sigma;
     int *mat_status;
@@ -261,7 +263,7 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
-                    p->rank, p->gready, p->ready, p->vready, p->sigma,
+                    p->rank, p->gready, p->ready, p->vready, p->rank_acc, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -403,6 +405,7 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
         AL(p->gready, sizeof(unsigned) * (size_t)gs.total);
         AL(p->ready, sizeof(unsigned) * (size_t)gs.total);
         AL(p->vready, sizeof(unsigned) * (size_t)gs.total);
+        AL(p->rank_acc, sizeof(unsigned long long) * (size_t)gs.total);
     }
     const size_t nrel = (size_t)(n_inst > 1 + d->M ? n_inst : 1 + d->M);
     AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
@@ -637,6 +640,7 @@ static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, c
                 // the tensor-core Gram (one CTA per matrix) hands each matrix to k_tridiag by flag
                 EigArgs ea = eig_args(p, a.active);
                 ea.gready = tc ? p->gready : nullptr;
+                ea.rank_acc = a.mode == 1 ? p->rank_acc : nullptr;    // ADMM iterations only
                 if (part & 1)
                     e = tc ? launch_gram_tc(v, lb, lc, p->B0, p->Gp, a.active, (int)p->d.gram_precision, p->status,
                                             p->gready, st)
@@ -836,6 +840,44 @@ static cudaError_t capture(selr_plan *p, int s0, int s1, const cf *Y, const uint
     return e;
 }
 
+// Layout of a solver state (checkpoint) buffer: the iterate K, the multipliers D,
+// E = Z - D / beta (the Z of Eqs. 16-17 is never stored on its own) and the per-FE
+// activity flags, each region starting on a 256-byte boundary.
+struct StateLayout {
+    size_t k, d, e, act, act_next, total;
+};
+static StateLayout state_layout(const selr_plan *p) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    StateLayout L;
+    L.k = 0;
+    L.d = al(L.k + sizeof(cf) * (size_t)p->nK);
+    L.e = al(L.d + sizeof(cf) * (size_t)p->lift_elems);
+    L.act = al(L.e + sizeof(cf) * (size_t)p->lift_elems);
+    L.act_next = al(L.act + sizeof(int) * (size_t)p->d.M);
+    L.total = al(L.act_next + sizeof(int) * (size_t)p->d.M);
+    return L;
+}
+
+extern "C" selr_status selr_state_bytes(const selr_plan *p, size_t *bytes) {
+    if (!p || !bytes) return SELR_ERR_INVALID_ARG;
+    *bytes = state_layout(p).total;
+    return SELR_OK;
+}
+
+static cudaError_t state_copy(selr_plan *p, unsigned char *state, int save, cudaStream_t st) {
+    const StateLayout L = state_layout(p);
+    struct { void *plan; size_t off, bytes; } r[] = {
+        {p->K, L.k, sizeof(cf) * (size_t)p->nK}, {p->D, L.d, sizeof(cf) * (size_t)p->lift_elems},
+        {p->E, L.e, sizeof(cf) * (size_t)p->lift_elems}, {p->active, L.act, sizeof(int) * (size_t)p->d.M},
+        {p->active_next, L.act_next, sizeof(int) * (size_t)p->d.M}};
+    for (auto &x : r) {
+        cudaError_t e = save ? cudaMemcpyAsync(state + x.off, x.plan, x.bytes, cudaMemcpyDeviceToDevice, st)
+                             : cudaMemcpyAsync(x.plan, state + x.off, x.bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t admm_init(selr_plan *p, const cf *Y, cudaStream_t st) {
     cudaError_t e;
     if ((e = cudaMemcpyAsync(p->K, Y, sizeof(cf) * p->nK, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
@@ -856,11 +898,15 @@ static cudaError_t output_image(selr_plan *p, cf *X, cudaStream_t st) {
 }
 
 extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *mask, void *X_out,
-                                  int32_t *iters_out, float *rel_out, selr_stream stream) {
-    if (!p || !Yv || !mask || !X_out) return SELR_ERR_INVALID_ARG;
+                                  void *state_inout, int32_t resume, int32_t *iters_out, float *rel_out,
+                                  selr_stream stream) {
+    if (!p || !Yv || !mask || !X_out || (resume != 0 && resume != 1) || (resume && !state_inout))
+        return SELR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const cf *Y = (const cf *)Yv;
-    CK(admm_init(p, Y, st));
+    if (resume) CK(state_copy(p, (unsigned char *)state_inout, 0, st));
+    else CK(admm_init(p, Y, st));
+    if (p->rank_acc) CK(cudaMemsetAsync(p->rank_acc, 0, sizeof(unsigned long long) * (size_t)p->gs.total, st));
     int iters = 0;
     float last_rel = -1.f;
     const bool fixed = p->d.tol < 0.f;
@@ -922,6 +968,8 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
         }
     }
     p->prof_count = p->prof_on ? (iters < p->prof_cap ? iters : p->prof_cap) : 0;
+    p->rank_iters = iters;
+    if (state_inout) CK(state_copy(p, (unsigned char *)state_inout, 1, st));
     CK(output_image(p, (cf *)X_out, st));
     if (rel_out || iters_out) {
         if (rel_out && fixed) {
@@ -937,6 +985,17 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
 }
 
 extern "C" const char *selr_last_error_string(void) { return cudaGetErrorString(g_last_error); }
+
+extern "C" selr_status selr_plan_rank_sums(selr_plan *p, int64_t *out, int32_t n, int32_t *iterations,
+                                           selr_stream stream) {
+    if (!p || !out || n != p->gs.total) return SELR_ERR_INVALID_ARG;
+    if (!p->rank_acc) return SELR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(out, p->rank_acc, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (iterations) *iterations = p->rank_iters;
+    return SELR_OK;
+}
 
 // ------------------------------------------------------------ reverse mode
 static selr_status grad_workspace(selr_plan *p) {
@@ -1126,11 +1185,11 @@ static selr_status time_solve(selr_plan *p, const void *Y, const uint8_t *mask, 
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return SELR_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return SELR_ERR_CUDA; }
-    selr_status s = selr_solve(p, Y, mask, X, nullptr, nullptr, (selr_stream)st);       // warm / capture
+    selr_status s = selr_solve(p, Y, mask, X, nullptr, 0, nullptr, nullptr, (selr_stream)st);       // warm / capture
     float best = 3.4e38f;
     for (int rep = 0; rep < 2 && s == SELR_OK; ++rep) {
         if (cudaEventRecord(e0, st) != cudaSuccess) { s = SELR_ERR_CUDA; break; }
-        s = selr_solve(p, Y, mask, X, nullptr, nullptr, (selr_stream)st);
+        s = selr_solve(p, Y, mask, X, nullptr, 0, nullptr, nullptr, (selr_stream)st);
         if (s != SELR_OK) break;
         float t = 0.f;
         if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -1157,7 +1216,7 @@ extern "C" selr_status selr_plan_autotune(selr_plan *p, const void *Y, const uin
     selr_status s = SELR_OK;
     if (p->d.svd_method == SELR_SVD_JACOBI) {
         // sweep cap from the sweeps the matrices actually needed in two iterations
-        s = selr_solve(p, Y, mask, X_scratch, nullptr, nullptr, stream);
+        s = selr_solve(p, Y, mask, X_scratch, nullptr, 0, nullptr, nullptr, stream);
         if (s == SELR_OK) {
             int *h = (int *)malloc(sizeof(int) * (size_t)p->gs.total);
             if (!h) s = SELR_ERR_ALLOC;

@@ -278,6 +278,7 @@ struct EigArgs {
     unsigned *gready;    // k_gram_tc -> k_tridiag
     unsigned *ready;     // k_tridiag -> k_eigvec
     unsigned *vready;    // k_eigvec -> k_apply_stream / k_apply_eig
+    unsigned long long *rank_acc;   // [mat] running sum of ranks over a solve, or null
 };
 cudaError_t eig_init_attributes();
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,

@@ -807,7 +807,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
     const float gl = red[0], gu = red[1], pivmin = red[2];
     const float tnorm = fmaxf(fabsf(gl), fabsf(gu));
     const int r = s_r;
-    if (tid == 0) *rank_out = r;
+    if (tid == 0) {
+        *rank_out = r;
+        if (a.rank_acc) a.rank_acc[g.moff + mat] += (unsigned long long)r;   // one CTA per matrix
+    }
     if (r == 0) {
         publish_flag(flag_of(a.vready, g, mat));
         return;

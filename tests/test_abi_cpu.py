@@ -95,9 +95,17 @@ def test_null_arguments(lib):
     assert lib.selr_plan_create(None, None) == 1
     assert lib.selr_plan_destroy(None) == 0
     assert lib.selr_sync_status(None, None) == 1
-    assert lib.selr_solve(None, None, None, None, None, None, None) == 1
+    assert lib.selr_solve(None, None, None, None, None, 0, None, None, None) == 1
     assert lib.selr_plan_workspace_bytes(None) == 0
     # the wait self-test validates its arguments before any CUDA call
     assert lib.selr_selftest_wait(0, 0) == 1
     assert lib.selr_selftest_wait(2, 100) == 1
     assert lib.selr_selftest_wait(1, 2000001) == 1
+    # state, rank and probe entry points validate their arguments before any CUDA call
+    n = ctypes.c_size_t()
+    assert lib.selr_state_bytes(None, ctypes.byref(n)) == 1
+    assert lib.selr_plan_rank_sums(None, None, 0, None, None) == 1
+    tf = ctypes.c_float()
+    assert lib.selr_probe_fp32_peak(2, 16, ctypes.byref(tf), None) == 1
+    assert lib.selr_probe_fp32_peak(0, 0, ctypes.byref(tf), None) == 1
+    assert lib.selr_probe_fp32_peak(0, 16, None, None) == 1
