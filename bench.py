@@ -717,7 +717,7 @@ def main():
     ap.add_argument("--exec", default="both", choices=["both", "batched", "plain"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--svd", default="eig", choices=["eig", "jacobi"])
-    ap.add_argument("--gram", default=None, choices=["fp32", "tf32", "3xtf32"],
+    ap.add_argument("--gram", default=None, choices=["fp32", "tf32", "3xtf32", "bf16x3", "bf16x6"],
                     help="Gram precision before autotuning (default: 3xtf32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -759,7 +759,9 @@ def main():
     achieved = jac["flops"] / (jac["ms"] / 1000.0) / 1e12
     gram = (results.get("tuning") or {}).get("gram", gram_for(args, wl.model in ("SHLR", "SHLR_V")))
     fk = jac["flops_by_kind"]
-    p_tc = {"fp32": fp32_peak, "tf32": tf32_peak, "3xtf32": (tf32_peak / 3.0) if tf32_peak else None}.get(gram)
+    bf16 = peaks.get("bf16_tflops")
+    p_tc = {"fp32": fp32_peak, "tf32": tf32_peak, "3xtf32": (tf32_peak / 3.0) if tf32_peak else None,
+            "bf16x3": (bf16 / 3.0) if bf16 else None, "bf16x6": (bf16 / 6.0) if bf16 else None}.get(gram)
     hbm = peaks.get("hbm_gbs", 6800.3)
     t_star = None
     if p_tc:

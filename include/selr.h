@@ -89,7 +89,11 @@ typedef enum {
 typedef enum {
     SELR_GRAM_FP32 = 0,    /* FP32 FMA (default)                                              */
     SELR_GRAM_TF32 = 1,    /* one TF32 product per term: ~1e-3 relative error in G             */
-    SELR_GRAM_3XTF32 = 3   /* x = x_hi + x_lo split, three TF32 products: about FP32 accuracy  */
+    SELR_GRAM_3XTF32 = 3,  /* x = x_hi + x_lo split, three TF32 products: about FP32 accuracy  */
+    SELR_GRAM_BF16X3 = 4,  /* x = x_hi + x_lo in bf16, three BF16 products (kind::f16):
+                              ~2^-16 relative error in G                                        */
+    SELR_GRAM_BF16X6 = 6   /* x = x_hi + x_mid + x_lo in bf16, the six products of order <= 4:
+                              about FP32 accuracy                                               */
 } selr_gram_precision;
 /* Measured against the FP64 oracle: reconstructions with 3XTF32 stay at FP32 level
  * (SHLR 12-coil 256x256: 1.8e-7 after 30 iterations; SHLR-P / SHLR-VP 2 coils 8x48x8
@@ -284,7 +288,8 @@ selr_status selr_plan_rank_sums(selr_plan *plan, int64_t *out, int32_t n, int32_
  * (2 iterations each) of the caller's problem Y / mask (as for selr_solve;
  * X_scratch receives throw-away images) and keeps the fastest settings in the
  * plan: with SELR_SVD_EIG the Gram precision among the modes of FP32-level
- * accuracy (SELR_GRAM_FP32, SELR_GRAM_3XTF32; also SELR_GRAM_TF32 when flags & 1) and the number of eigenvectors refined per inverse-iteration
+ * accuracy (SELR_GRAM_FP32, SELR_GRAM_3XTF32, SELR_GRAM_BF16X6; also SELR_GRAM_TF32 and
+ * SELR_GRAM_BF16X3 when flags & 1) and the number of eigenvectors refined per inverse-iteration
  * pass (8 or 16); with SELR_SVD_JACOBI the sweep cap (twice the largest
  * number of sweeps a matrix needed, + 2, if below the current cap and no
  * matrix reached it).

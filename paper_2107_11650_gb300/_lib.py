@@ -20,7 +20,7 @@ MODELS = {"SHLR": 0, "SHLR_V": 1, "SHLR_P": 2, "SHLR_VP": 3}
 AXES = {"row": 0, "col": 1, "pe": 2, "param": 3}
 EXEC = {"batched": 0, "plain": 1}
 SVD = {"eig": 0, "jacobi": 1}
-GRAM = {"fp32": 0, "tf32": 1, "3xtf32": 3}
+GRAM = {"fp32": 0, "tf32": 1, "3xtf32": 3, "bf16x3": 4, "bf16x6": 6}
 
 # Every function declared in include/selr.h, with its ctypes signature.
 c_void_p, c_int32, c_float, c_size_t = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_size_t

@@ -12,7 +12,13 @@
 // Precision.  TF32 keeps 10 mantissa bits.  mode 1 (TF32): one product per
 // term.  mode 3 (3xTF32): x = x_h + x_l with x_h = tf32(x), x_l = tf32(x - x_h)
 // and a.b ~ a_h.b_h + a_h.b_l + a_l.b_h, which recovers about FP32 accuracy
-// (the dropped a_l.b_l term is 2^-22 relative).
+// (the dropped a_l.b_l term is 2^-22 relative).  BF16 keeps 7 stored mantissa
+// bits (kind::f16 with both operands bf16, K = 16 per MMA, at twice the TF32
+// rate).  mode 4 (BF16x3): x = x_h + x_l, x_h = bf16(x), x_l = bf16(x - x_h),
+// three products as above: the dropped terms and the rounding of x_l leave
+// ~2^-16 relative.  mode 6 (BF16x6): x = x_h + x_m + x_l (each the bf16 of the
+// remainder), the six products a_i.b_j with i + j <= 4 (indices 1..3), FP32
+// level.  x - x_h is exact in FP32 in every split.
 //
 // Kernel.  One CTA (8 warps) per matrix, s <= 256, N = s rounded up to 16.
 // s <= 192: one pass over K with two accumulator pairs in tensor memory,
@@ -34,8 +40,8 @@
 #define GT_NS 3                  // shared-memory stages
 #define GT_KC 16                  // real K elements per chunk (64 bytes per row)
 #define GT_TILE_ROWS 256          // rows held per operand tile (s <= 256)
-#define GT_TILE_BYTES (GT_TILE_ROWS * GT_KC * 4)   // 16 KB
-#define GT_STAGE_BYTES (4 * GT_TILE_BYTES)         // Xh, Xl, Yh, Yl
+#define GT_TILE_BYTES (GT_TILE_ROWS * GT_KC * 4)   // 16 KB (TF32; a BF16 tile takes half)
+#define GT_STAGE_BYTES (4 * GT_TILE_BYTES)         // Xh, Xl, Yh, Yl (BF16x6: six 8 KB tiles)
 #define GT_SMEM (GT_NS * GT_STAGE_BYTES + 1024)    // stages + alignment slack
 #define GT_WAIT_NS 2000000000ull   // 2 s bound on any single wait
 
@@ -56,24 +62,58 @@ __device__ __forceinline__ uint32_t gt_off(int r, int k) {
     return (uint32_t)(((r >> 3) * (GT_KC / 4) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
 
+// The same layout for 16-bit elements: a row of a chunk is 32 bytes, two core
+// matrices (8 rows x 8 elements) along K.
+__device__ __forceinline__ uint32_t gb_off(int r, int k) {
+    return (uint32_t)(((r >> 3) * (GT_KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
 // Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), fixed
-// constant 0b001 at bits 46-48, no swizzle.
+// constant 0b001 at bits 46-48, no swizzle.  LBO = 128 bytes between core
+// matrices along K; SBO = bytes between 8-row groups (512 for TF32 chunks,
+// 256 for BF16 chunks).
+template <bool BF>
 __device__ __forceinline__ uint64_t gt_desc(uint32_t addr) {
-    const uint64_t lbo = 128 >> 4, sbo = (GT_KC / 4 * 128) >> 4;
+    const uint64_t lbo = 128 >> 4, sbo = (BF ? GT_KC / 8 * 128 : GT_KC / 4 * 128) >> 4;
     return (uint64_t)((addr & 0x3FFFF) >> 4) | (lbo << 16) | (sbo << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::tf32: D F32 (bits 4-5 = 1), A and B TF32
-// (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+// Instruction descriptor, D F32 (bits 4-5 = 1), both operands K-major, N >> 3
+// at bits 17-22, M >> 4 at 24-28; A and B types at bits 7-9 and 10-12:
+// kind::tf32 TF32 = 2, kind::f16 BF16 = 1 (A and B always of the same type).
+template <bool BF>
 __device__ __forceinline__ uint32_t gt_idesc(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    const uint32_t ty = BF ? 1u : 2u;
+    return (1u << 4) | (ty << 7) | (ty << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+template <bool BF>
 __device__ __forceinline__ void gt_mma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    if (BF)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// Two floats to a bf16 pair (round to nearest even), element lo in the low half.
+__device__ __forceinline__ uint32_t to_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+// (a, b) -> (b, -a) on a bf16 pair: swap the halves, flip the sign of the new high half.
+__device__ __forceinline__ uint32_t bf_rot(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x80000000u; }
+
+__device__ __forceinline__ void st2(uint32_t addr, uint32_t a, uint32_t b) {
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 
 __device__ __forceinline__ void gt_commit(uint32_t bar) {
@@ -118,21 +158,24 @@ __device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
 }
 
-// Issue the products of one K = 8 step into accumulator pair (dre, dim):
-// A rows at byte offset arow, B rows at brow, both tiles at k-offset ko.
+// Issue the products of one K step (8 TF32 or 16 BF16 elements) into accumulator
+// pair (dre, dim): A rows at byte offset arow, B rows at brow, tiles at k-offset
+// ko.  x[t] / y[t]: the tiles of split term t of X and of its rotation Y.
 template <int MODE>
-__device__ __forceinline__ void gt_step(uint32_t dre, uint32_t dim, uint32_t idesc, uint32_t bxh, uint32_t bxl,
-                                        uint32_t byh, uint32_t byl, uint32_t arow, uint32_t brow, uint32_t ko,
+__device__ __forceinline__ void gt_step(uint32_t dre, uint32_t dim, uint32_t idesc, const uint32_t *x,
+                                        const uint32_t *y, uint32_t arow, uint32_t brow, uint32_t ko,
                                         uint32_t first) {
-    const uint64_t ah = gt_desc(bxh + arow + ko);
-    gt_mma(dre, ah, gt_desc(bxh + brow + ko), idesc, first);
-    gt_mma(dim, ah, gt_desc(byh + brow + ko), idesc, first);
-    if (MODE == 3) {
-        const uint64_t al = gt_desc(bxl + arow + ko);
-        gt_mma(dre, ah, gt_desc(bxl + brow + ko), idesc, 1u);
-        gt_mma(dim, ah, gt_desc(byl + brow + ko), idesc, 1u);
-        gt_mma(dre, al, gt_desc(bxh + brow + ko), idesc, 1u);
-        gt_mma(dim, al, gt_desc(byh + brow + ko), idesc, 1u);
+    constexpr bool BF = MODE >= 4;
+    // products a_i . b_j of the split terms: (0,0), then (0,1), (1,0), then (0,2), (1,1), (2,0)
+    constexpr int NP = MODE == 1 ? 1 : (MODE == 6 ? 6 : 3);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int i = (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : 0);
+        const int j = (q == 1 || q == 4) ? 1 : (q == 3 ? 2 : 0);
+        const uint64_t a = gt_desc<BF>(x[i] + arow + ko);
+        const uint32_t acc = q == 0 ? first : 1u;
+        gt_mma<BF>(dre, a, gt_desc<BF>(x[j] + brow + ko), idesc, acc);
+        gt_mma<BF>(dim, a, gt_desc<BF>(y[j] + brow + ko), idesc, acc);
     }
 }
 
@@ -183,8 +226,11 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
     const uint32_t tm = tmem_base_s;
     const uint32_t d0_re = tm, d0_im = tm + (uint32_t)N;
     const uint32_t d1_re = tm + 2u * N, d1_im = tm + 2u * N + (uint32_t)N1;
-    const uint32_t idesc0 = gt_idesc(128, N), idesc1 = N1 ? gt_idesc(128, N1) : 0u;
-    const uint32_t rowgrp = GT_KC / 4 * 128;       // bytes per 8-row group (SBO)
+    constexpr bool BF = MODE >= 4;
+    constexpr int NT = MODE == 1 ? 1 : (MODE == 6 ? 3 : 2);          // split terms
+    constexpr uint32_t TILE = BF ? GT_TILE_BYTES / 2 : GT_TILE_BYTES;
+    const uint32_t idesc0 = gt_idesc<BF>(128, N), idesc1 = N1 ? gt_idesc<BF>(128, N1) : 0u;
+    const uint32_t rowgrp = BF ? GT_KC / 8 * 128 : GT_KC / 4 * 128;   // bytes per 8-row group (SBO)
     uint32_t waits[GT_NS] = {};                    // completed waits per stage (parity)
     bool ok = true;
     cf *G = Gp + g.poff + (long long)mat * ((long long)n * (n + 1) / 2);
@@ -219,44 +265,59 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
 #pragma unroll
             for (int u = 0; u < GT_QPT; ++u) { ca[u] = pa[u]; cb[u] = pb[u]; }
             if (kc + 1 < nk) gload(kc + 1);            // next chunk's loads in flight meanwhile
-            const uint32_t bxh = smem_u32(stage), bxl = bxh + GT_TILE_BYTES;
-            const uint32_t byh = bxh + 2 * GT_TILE_BYTES, byl = bxh + 3 * GT_TILE_BYTES;
+            // tiles of the split terms of X (x[t]) and of the rotation Y (y[t])
+            uint32_t xt[3], yt[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                xt[t] = smem_u32(stage) + (uint32_t)t * TILE;
+                yt[t] = smem_u32(stage) + (uint32_t)(NT + t) * TILE;
+            }
 #pragma unroll
             for (int u = 0; u < GT_QPT; ++u) {
                 const int idx = tid + GT_THREADS * u;
                 if (idx >= nq) continue;
                 const int r = idx / GT_QPR, q = idx - r * GT_QPR;
-                const uint32_t off = gt_off(r, 4 * q);
                 // (re0, im0, re1, im1) and the rotation (im0, -re0, im1, -re1)
-                const uint32_t h0 = to_tf32(ca[u].x), h1 = to_tf32(ca[u].y);
-                const uint32_t h2 = to_tf32(cb[u].x), h3 = to_tf32(cb[u].y);
-                st4(bxh + off, h0, h1, h2, h3);
-                st4(byh + off, h1, h0 ^ 0x80000000u, h3, h2 ^ 0x80000000u);
-                if (MODE == 3) {
-                    const uint32_t l0 = to_tf32(ca[u].x - __uint_as_float(h0));
-                    const uint32_t l1 = to_tf32(ca[u].y - __uint_as_float(h1));
-                    const uint32_t l2 = to_tf32(cb[u].x - __uint_as_float(h2));
-                    const uint32_t l3 = to_tf32(cb[u].y - __uint_as_float(h3));
-                    st4(bxl + off, l0, l1, l2, l3);
-                    st4(byl + off, l1, l0 ^ 0x80000000u, l3, l2 ^ 0x80000000u);
+                if (!BF) {
+                    const uint32_t off = gt_off(r, 4 * q);
+                    const uint32_t h0 = to_tf32(ca[u].x), h1 = to_tf32(ca[u].y);
+                    const uint32_t h2 = to_tf32(cb[u].x), h3 = to_tf32(cb[u].y);
+                    st4(xt[0] + off, h0, h1, h2, h3);
+                    st4(yt[0] + off, h1, h0 ^ 0x80000000u, h3, h2 ^ 0x80000000u);
+                    if (MODE == 3) {
+                        const uint32_t l0 = to_tf32(ca[u].x - __uint_as_float(h0));
+                        const uint32_t l1 = to_tf32(ca[u].y - __uint_as_float(h1));
+                        const uint32_t l2 = to_tf32(cb[u].x - __uint_as_float(h2));
+                        const uint32_t l3 = to_tf32(cb[u].y - __uint_as_float(h3));
+                        st4(xt[1] + off, l0, l1, l2, l3);
+                        st4(yt[1] + off, l1, l0 ^ 0x80000000u, l3, l2 ^ 0x80000000u);
+                    }
+                } else {
+                    const uint32_t off = gb_off(r, 4 * q);
+                    float ra = ca[u].x, ia = ca[u].y, rb = cb[u].x, ib = cb[u].y;   // remainders
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) {
+                        const uint32_t w0 = to_bf16x2(ra, ia), w1 = to_bf16x2(rb, ib);
+                        st2(xt[t] + off, w0, w1);
+                        st2(yt[t] + off, bf_rot(w0), bf_rot(w1));
+                        ra -= bf_lo(w0); ia -= bf_hi(w0); rb -= bf_lo(w1); ib -= bf_hi(w1);
+                    }
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // TF32: two K = 8 steps (two core matrices each); BF16: one K = 16 step
 #pragma unroll
-                for (int k8 = 0; k8 < GT_KC / 8; ++k8) {
-                    const uint32_t ko = (uint32_t)k8 * 2 * 128;              // two core matrices along K
+                for (int k8 = 0; k8 < (BF ? 1 : GT_KC / 8); ++k8) {
+                    const uint32_t ko = (uint32_t)k8 * 2 * 128;
                     const uint32_t first = (kc == 0 && k8 == 0) ? 0u : 1u;
                     if (single) {
-                        gt_step<MODE>(d0_re, d0_im, idesc0, bxh, bxl, byh, byl, 0u, 0u, ko, first);
-                        if (N1)
-                            gt_step<MODE>(d1_re, d1_im, idesc1, bxh, bxl, byh, byl, 16u * rowgrp, 16u * rowgrp, ko,
-                                          first);
+                        gt_step<MODE>(d0_re, d0_im, idesc0, xt, yt, 0u, 0u, ko, first);
+                        if (N1) gt_step<MODE>(d1_re, d1_im, idesc1, xt, yt, 16u * rowgrp, 16u * rowgrp, ko, first);
                     } else {
-                        gt_step<MODE>(d0_re, d0_im, idesc0, bxh, bxl, byh, byl, (uint32_t)pass * 16u * rowgrp, 0u,
-                                      ko, first);
+                        gt_step<MODE>(d0_re, d0_im, idesc0, xt, yt, (uint32_t)pass * 16u * rowgrp, 0u, ko, first);
                     }
                 }
                 gt_commit(smem_u32(&bars[st]));
@@ -343,10 +404,14 @@ cudaError_t launch_gram_tc(const GroupSet &gs, int mat_begin, int mat_count, con
     if (!g_gt_attr) {
         e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM);
         if (e != cudaSuccess) return e;
         g_gt_attr = true;
     }
     if (mode == 3) k_gram_tc<3><<<mat_count, GT_THREADS, GT_SMEM, st>>>(gs, mat_begin, B0, Gp, active, status, ready);
+    else if (mode == 4) k_gram_tc<4><<<mat_count, GT_THREADS, GT_SMEM, st>>>(gs, mat_begin, B0, Gp, active, status, ready);
+    else if (mode == 6) k_gram_tc<6><<<mat_count, GT_THREADS, GT_SMEM, st>>>(gs, mat_begin, B0, Gp, active, status, ready);
     else k_gram_tc<1><<<mat_count, GT_THREADS, GT_SMEM, st>>>(gs, mat_begin, B0, Gp, active, status, ready);
     return cudaGetLastError();
 }

@@ -184,7 +184,8 @@ static selr_status validate(const selr_desc *d) {
     if (d->exec != SELR_EXEC_BATCHED && d->exec != SELR_EXEC_PLAIN) return SELR_ERR_INVALID_ARG;
     if (d->svd_method != SELR_SVD_EIG && d->svd_method != SELR_SVD_JACOBI) return SELR_ERR_INVALID_ARG;
     if (d->gram_precision != SELR_GRAM_FP32 && d->gram_precision != SELR_GRAM_TF32 &&
-        d->gram_precision != SELR_GRAM_3XTF32)
+        d->gram_precision != SELR_GRAM_3XTF32 && d->gram_precision != SELR_GRAM_BF16X3 &&
+        d->gram_precision != SELR_GRAM_BF16X6)
         return SELR_ERR_INVALID_ARG;
     const bool two_d = d->model <= SELR_SHLR_V;
     if (two_d) {
@@ -1237,8 +1238,8 @@ extern "C" selr_status selr_plan_autotune(selr_plan *p, const void *Y, const uin
             }
         }
     } else {
-        int grams[3] = {SELR_GRAM_FP32, SELR_GRAM_3XTF32, SELR_GRAM_TF32};
-        const int ngram = (flags & 1) ? 3 : 2;
+        const int grams[5] = {SELR_GRAM_FP32, SELR_GRAM_3XTF32, SELR_GRAM_BF16X6, SELR_GRAM_TF32, SELR_GRAM_BF16X3};
+        const int ngram = (flags & 1) ? 5 : 3;
         const int chunks[2] = {16, 8};
         float best = 3.4e38f;
         int bg = p->d.gram_precision, bc = p->ev_chunk;

@@ -4,8 +4,10 @@
 FP32 FMA, TF32 tensor-core products (10 mantissa bits: each product carries
 ~2^-11 relative error, so G and the eigenvalues near the threshold move by
 ~1e-4 of ||G||), or 3xTF32 (hi/lo split, the dropped lo*lo term is 2^-22
-relative, i.e. FP32 level).  Measured on GB300: SVT relative error 0.6-1e-6
-(FP32), 1.1-2.1e-6 (3xTF32), 0.7-3.2e-4 (TF32) on the shapes below; the
+relative, i.e. FP32 level); BF16x3 (bf16 hi/lo split, three products,
+~2^-16 per product in the worst case) and BF16x6 (hi/mid/lo, six products).
+Measured on GB300: SVT relative error 0.6-1e-6 (FP32), 1.1-2.1e-6 (3xTF32),
+0.7-3.2e-4 (TF32), ~2e-6 (BF16x3), ~1e-6 (BF16x6) on the shapes below; the
 bounds keep a factor ~5 above the worst measured value.  Families with s <= 8
 use the warp-per-matrix Jacobi kernel whatever the mode.
 """
@@ -22,7 +24,7 @@ from oracle.metrics import rel_l2
 
 pytestmark = pytest.mark.gpu
 
-BOUND = {"fp32": 1e-5, "3xtf32": 1e-5, "tf32": 2e-3}
+BOUND = {"fp32": 1e-5, "3xtf32": 1e-5, "tf32": 2e-3, "bf16x6": 1e-5, "bf16x3": 2e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -58,7 +60,7 @@ def test_svt_gram_precision(nmat, rows, cols):
     t = 0.5 * (s[k // 3] + s[k // 3 + 1])
     ref = osvt.svt(A, t)
     errs = {}
-    for gram in ("fp32", "tf32", "3xtf32"):
+    for gram in ("fp32", "tf32", "3xtf32", "bf16x3", "bf16x6"):
         plan = api.Plan(api.Desc(model="SHLR", J=12, M=320, N=320, window=16, gram=gram))
         dA = torch.from_numpy(A.astype(np.complex64)).cuda()
         api.selr_svt(plan, dA, t)
@@ -67,11 +69,13 @@ def test_svt_gram_precision(nmat, rows, cols):
         plan.close()
     for gram, e in errs.items():
         assert e <= BOUND[gram], (gram, errs)
-    if k > 16:      # tensor-core path: the split recovers FP32-level accuracy
+    if k > 16:      # tensor-core path: the splits recover accuracy
         assert errs["3xtf32"] < 0.2 * errs["tf32"], errs
+        assert errs["bf16x3"] < 0.2 * errs["tf32"], errs
+        assert errs["bf16x6"] <= 1.5 * errs["bf16x3"] + 1e-7, errs
 
 
-@pytest.mark.parametrize("gram", ["3xtf32", "tf32"])
+@pytest.mark.parametrize("gram", ["3xtf32", "tf32", "bf16x6", "bf16x3"])
 def test_solve_gram_precision(gram):
     """SHLR-V (24 channels) on a reduced 6-coil 64x64 case, 30 iterations."""
     api = _api()
@@ -85,7 +89,7 @@ def test_solve_gram_precision(gram):
     api.selr_solve(plan, Y, torch.from_numpy(inp["mask"]).cuda(), X)
     assert api.selr_sync_status(plan) == 0
     err = rel_l2(X.cpu().numpy().astype(np.complex128), ref)
-    assert err <= (1e-4 if gram == "3xtf32" else 5e-3), err
+    assert err <= {"3xtf32": 1e-4, "bf16x6": 1e-4, "bf16x3": 1e-3, "tf32": 5e-3}[gram], err
     plan.close()
 
 
@@ -103,7 +107,7 @@ def test_autotune_keeps_accuracy(svd):
     with torch.cuda.stream(s):
         t = plan.autotune(Y, mask, stream=s)
     if svd == "eig":
-        assert t["gram"] in ("fp32", "3xtf32") and t["ev_chunk"] in (8, 16)
+        assert t["gram"] in ("fp32", "3xtf32", "bf16x6") and t["ev_chunk"] in (8, 16)
     else:
         assert 2 <= t["jacobi_max_sweeps"] <= 30
     assert plan.desc.max_iter == 30
