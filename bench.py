@@ -102,8 +102,9 @@ def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
     """Kernels libselr launches per ADMM iteration (mirrors admm_stage and svd_apply in
     selr.cu): adjoint, FFTs of the adjoints, DC + reduction, hybrid FFTs, lift, and the
     SVT kernels: either the warp-per-matrix SVT (s <= 8, len <= 64) or Gram, tridiagonal
-    reduction, eigenvectors and the three apply kernels (streaming for r <= 32 and
-    32 < r <= 64 pairs, general above) (eig), Jacobi and apply (jacobi).  Batched, one
+    reduction, eigenvectors, the three apply kernels (streaming for r <= 32 and
+    32 < r <= 64 pairs, general above) and the FP64 re-solve of flagged matrices (eig),
+    Jacobi and apply (jacobi).  Batched, one
     SVT launch sequence covers each run of consecutive lift families of the same SVT
     size class (svt_class in selr.cu); plain, one per matrix."""
     fams = [plan.lift_shape(a) for a in (("row", "col") if model2d else ("pe", "param"))]
@@ -121,12 +122,12 @@ def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
         return 7
 
     def svt_kernels(r, c):
-        return 1 if svt_class(r, c) == 0 else (6 if svd == "eig" else 2)
+        return 1 if svt_class(r, c) == 0 else (7 if svd == "eig" else 2)
 
     if exec_mode == "batched":
         classes = [svt_class(r, c) for _, r, c in fams]
         runs = [k for i, k in enumerate(classes) if i == 0 or k != classes[i - 1]]
-        per = 1 + fft_a + 2 + fft_a + 1 + sum(1 if k == 0 else (6 if svd == "eig" else 2) for k in runs)
+        per = 1 + fft_a + 2 + fft_a + 1 + sum(1 if k == 0 else (7 if svd == "eig" else 2) for k in runs)
     else:
         nmat = sum(nm for nm, _, _ in fams)
         per = nmat + fft_a + 2 + fft_a + sum(nm * (1 + svt_kernels(r, c)) for nm, r, c in fams)

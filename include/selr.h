@@ -118,13 +118,19 @@ typedef struct {
     int32_t exec;             /* selr_exec                                                */
     int32_t svd_method;       /* selr_svd_method                                          */
     int32_t gram_precision;   /* selr_gram_precision (SELR_SVD_EIG path)                   */
+    int32_t fp64_fallback;    /* SELR_SVD_EIG: 1 (default) = re-solve in FP64 every matrix whose
+                                 thresholding is not determined in FP32 (t^2 below the FP32
+                                 resolution 64 eps_32 lambda_max of its Gram eigenvalues, with
+                                 eigenvalues between them); 0 = FP32 only.  A re-solved matrix
+                                 costs ~0.1 s (FP64 one-sided Jacobi); the plan holds 8 FP64
+                                 work slots of min(rows, cols) x max(rows, cols) elements. */
 } selr_desc;
 
 typedef struct selr_plan selr_plan;   /* opaque; owns its device workspace */
 
 /* Fill *desc with defaults (SHLR, weight 1, beta = tau = 20, lambda = 1e4,
  * lambda2 = 2, d_init = 1, max_iter = 30, tol = -1, 30 sweeps, tol 2e-6,
- * batched, SELR_SVD_EIG, SELR_GRAM_FP32). */
+ * batched, SELR_SVD_EIG, SELR_GRAM_FP32, fp64_fallback = 1). */
 void selr_desc_default(selr_desc *desc);
 
 /* Validate *desc and allocate the plan's device workspace on the current

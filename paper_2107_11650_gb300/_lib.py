@@ -32,7 +32,7 @@ class SelrDesc(ctypes.Structure):
                 ("lambda_", c_float), ("lambda2", c_float), ("beta", c_float), ("tau", c_float),
                 ("d_init", c_float), ("max_iter", c_int32), ("tol", c_float),
                 ("jacobi_max_sweeps", c_int32), ("jacobi_tol", c_float), ("exec_", c_int32),
-                ("svd_method", c_int32), ("gram_precision", c_int32)]
+                ("svd_method", c_int32), ("gram_precision", c_int32), ("fp64_fallback", c_int32)]
 
 
 SIGNATURES = {

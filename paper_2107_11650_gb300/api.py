@@ -40,6 +40,7 @@ class Desc:
     exec: str = "batched"
     svd: str = "eig"
     gram: str = "fp32"
+    fp64_fallback: int = 1
 
     @classmethod
     def from_workload(cls, w, **over):
@@ -60,6 +61,7 @@ class Desc:
         d.exec_ = EXEC[self.exec]
         d.svd_method = SVD[self.svd]
         d.gram_precision = GRAM[self.gram]
+        d.fp64_fallback = int(self.fp64_fallback)
         return d
 
 

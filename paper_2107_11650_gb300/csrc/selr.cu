@@ -37,6 +37,8 @@ struct selr_plan {
     int *rank;
     unsigned *gready, *ready, *vready;   // kernel hand-off flags, one per matrix (see EigArgs)
     unsigned long long *rank_acc;        // per-matrix sum of eigensolver ranks over the last solve
+    void *f64work;                       // FP64 re-solve slots (SELR_FP64_SLOTS x f64slot double2)
+    long long f64slot;
     int rank_iters;                      // iterations accumulated in rank_acc
     long long packed_elems;
     float *sigma;
@@ -114,6 +116,7 @@ extern "C" void selr_desc_default(selr_desc *d) {
     d->exec = SELR_EXEC_BATCHED;
     d->svd_method = SELR_SVD_EIG;
     d->gram_precision = SELR_GRAM_FP32;
+    d->fp64_fallback = 1;
 }
 
 extern "C" const char *selr_status_string(selr_status s) {
@@ -181,6 +184,7 @@ static selr_status validate(const selr_desc *d) {
         !isfinite(d->d_init) || !(d->lambda2 >= 0.f))
         return SELR_ERR_INVALID_ARG;
     if (d->weight != 0 && d->weight != 1) return SELR_ERR_INVALID_ARG;
+    if (d->fp64_fallback != 0 && d->fp64_fallback != 1) return SELR_ERR_INVALID_ARG;
     if (d->exec != SELR_EXEC_BATCHED && d->exec != SELR_EXEC_PLAIN) return SELR_ERR_INVALID_ARG;
     if (d->svd_method != SELR_SVD_EIG && d->svd_method != SELR_SVD_JACOBI) return SELR_ERR_INVALID_ARG;
     if (d->gram_precision != SELR_GRAM_FP32 && d->gram_precision != SELR_GRAM_TF32 &&
@@ -264,7 +268,7 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
-                    p->rank, p->gready, p->ready, p->vready, p->rank_acc, p->sigma,
+                    p->rank, p->gready, p->ready, p->vready, p->rank_acc, p->f64work, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -311,7 +315,8 @@ static selr_status check_batch(const selr_desc *ds, int n) {
         if (b.model != a.model || b.weight != a.weight || b.beta != a.beta || b.tau != a.tau ||
             b.d_init != a.d_init || b.max_iter != a.max_iter || b.tol != a.tol || b.exec != a.exec ||
             b.svd_method != a.svd_method || b.gram_precision != a.gram_precision ||
-            b.jacobi_max_sweeps != a.jacobi_max_sweeps || b.jacobi_tol != a.jacobi_tol)
+            b.jacobi_max_sweeps != a.jacobi_max_sweeps || b.jacobi_tol != a.jacobi_tol ||
+            b.fp64_fallback != a.fp64_fallback)
             return SELR_ERR_INVALID_ARG;
     }
     return SELR_OK;
@@ -407,6 +412,12 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
         AL(p->ready, sizeof(unsigned) * (size_t)gs.total);
         AL(p->vready, sizeof(unsigned) * (size_t)gs.total);
         AL(p->rank_acc, sizeof(unsigned long long) * (size_t)gs.total);
+        if (d->fp64_fallback) {
+            long long mx = 0;
+            for (int k = 0; k < gs.n; ++k) mx = mx > (long long)gs.g[k].s * gs.g[k].len ? mx : (long long)gs.g[k].s * gs.g[k].len;
+            p->f64slot = mx;
+            AL(p->f64work, 16 * (size_t)mx * SELR_FP64_SLOTS);
+        }
     }
     const size_t nrel = (size_t)(n_inst > 1 + d->M ? n_inst : 1 + d->M);
     AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
@@ -642,12 +653,15 @@ static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, c
                 EigArgs ea = eig_args(p, a.active);
                 ea.gready = tc ? p->gready : nullptr;
                 ea.rank_acc = a.mode == 1 ? p->rank_acc : nullptr;    // ADMM iterations only
+                ea.fp64_fallback = p->f64work != nullptr;
                 if (part & 1)
                     e = tc ? launch_gram_tc(v, lb, lc, p->B0, p->Gp, a.active, (int)p->d.gram_precision, p->status,
                                             p->gready, st)
                            : launch_gram(v, lb, lc, p->B0, p->Gp, a.active, st);
                 if (e == cudaSuccess && (part & 2)) e = launch_heig(v, lb, lc, ea, st);
                 if (e == cudaSuccess && (part & 4)) e = launch_apply_eig(v, lb, lc, ea, a, st);
+                if (e == cudaSuccess && (part & 4) && p->f64work)
+                    e = launch_svt_fp64(v, lb, lc, ea, a, p->f64work, p->f64slot, SELR_FP64_SLOTS, st);
             }
             if (e != cudaSuccess) return e;
         }

@@ -279,6 +279,7 @@ struct EigArgs {
     unsigned *ready;     // k_tridiag -> k_eigvec
     unsigned *vready;    // k_eigvec -> k_apply_stream / k_apply_eig
     unsigned long long *rank_acc;   // [mat] running sum of ranks over a solve, or null
+    int fp64_fallback;   // flag near-degenerate matrices (rank -1) for the FP64 re-solve
 };
 cudaError_t eig_init_attributes();
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,
@@ -292,6 +293,12 @@ cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, c
 // 2 (g.off + mat s len), 2 rank vectors of length s.
 cudaError_t launch_resolvent(const GroupSet &gs, int mat_count, const EigArgs &ea, const cf *W, cf *Y,
                              cudaStream_t st);
+
+// svt_fp64.cu: FP64 one-sided Jacobi S_t of the matrices k_eigvec flagged (rank -1), with the
+// outputs of the FP32 apply; `slots` CTAs, each with slot_elems double2 of `work`.
+#define SELR_FP64_SLOTS 8
+cudaError_t launch_svt_fp64(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, const SvtArgs &a,
+                            void *work, long long slot_elems, int slots, cudaStream_t st);
 
 // grad.cu
 cudaError_t launch_cgemm(int batch, int m, int n, int k, cf alpha, const cf *A, int opa, long long lda, long long sa,

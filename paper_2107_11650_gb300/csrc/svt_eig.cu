@@ -802,6 +802,16 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
         gershgorin(dd, ff, f2, n, &gl, &gu, &pivmin);
         red[0] = gl; red[1] = gu; red[2] = pivmin;
         s_r = allp ? n : n - ((t2 >= gu) ? n : sturm_lt(dd, f2, n, t2, pivmin));
+        // near-degenerate at the threshold: t^2 below the FP32 resolution floor
+        // F = 64 eps_32 lambda_max of the Gram eigenvalues, with eigenvalues between t^2
+        // and F, so the count above t^2 is not determined in FP32 -> FP64 re-solve
+        if (!allp && a.fp64_fallback && s_r > 0) {
+            const float F = 32.f * FLT_EPSILON * fmaxf(fabsf(gl), fabsf(gu));
+            if (t2 < F) {
+                const int cF = n - ((F >= gu) ? n : sturm_lt(dd, f2, n, F, pivmin));
+                if (cF != s_r) s_r = -1;
+            }
+        }
     }
     __syncthreads();
     const float gl = red[0], gu = red[1], pivmin = red[2];
@@ -809,9 +819,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
     const int r = s_r;
     if (tid == 0) {
         *rank_out = r;
-        if (a.rank_acc) a.rank_acc[g.moff + mat] += (unsigned long long)r;   // one CTA per matrix
+        if (a.rank_acc && r > 0) a.rank_acc[g.moff + mat] += (unsigned long long)r;   // one CTA per matrix
     }
-    if (r == 0) {
+    if (r <= 0) {               // nothing above t^2, or flagged for the FP64 re-solve (r = -1)
         publish_flag(flag_of(a.vready, g, mat));
         return;
     }
@@ -1240,7 +1250,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_apply_stream(GroupSet gs, int ma
     if (e0 >= len) return;
     wait_flag(flag_of(ea.vready, g, mat), a.status, false);
     const int r = ea.rank[g.moff + mat];
-    if (r > CH || (CH > 32 && r <= CH / 2)) return;   // the other variant / k_apply_eig
+    if (r < 0 || r > CH || (CH > 32 && r <= CH / 2)) return;   // FP64 re-solve / other variant / k_apply_eig
     const long long mb = g.off + (long long)mat * n * len;
     if (blockIdx.y == 0 && threadIdx.x == 0 && a.rank_out) a.rank_out[g.moff + mat] = r;
     const float t = g.thresh;

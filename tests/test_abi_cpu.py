@@ -53,6 +53,7 @@ def _desc(lib, **kw):
     (dict(model=7), 1), (dict(J=0), 1), (dict(beta=0.0), 1), (dict(tau=-1.0), 1), (dict(max_iter=0), 1),
     (dict(weight=3), 1), (dict(exec_=5), 1), (dict(jacobi_tol=0.0), 1), (dict(lambda2=-1.0), 1),
     (dict(svd_method=2), 1), (dict(gram_precision=2), 1), (dict(gram_precision=-1), 1),
+    (dict(fp64_fallback=2), 1), (dict(gram_precision=5), 1),
     (dict(M=63), 2), (dict(N=14 * 7), 2), (dict(window=65), 2), (dict(L=2), 2),
     (dict(model=3, L=8, window_param=9, N=64), 2), (dict(model=2, L=8, window_param=4, N=66 * 7), 2),
 ])
@@ -67,7 +68,8 @@ def test_descriptor_defaults(lib):
     d = _desc(lib)
     assert (d.model, d.J, d.M, d.N, d.L, d.window) == (0, 4, 64, 64, 1, 8)
     assert (d.svd_method, d.gram_precision, d.exec_) == (0, 0, 0)
-    assert ctypes.sizeof(_lib.SelrDesc) == 20 * 4
+    assert d.fp64_fallback == 1
+    assert ctypes.sizeof(_lib.SelrDesc) == 21 * 4
 
 
 def test_batch_descriptor_validation(lib):

@@ -4,10 +4,11 @@ Per batched ADMM iteration libselr launches the adjoint (1), the transforms of t
 adjoints (2 for 2D models, 1 otherwise), the DC divide and its reduction (2), the hybrid
 transforms (2 / 1), the lift (1), and for every run of consecutive lift families of one
 SVT size class either the warp-per-matrix SVT (s <= 8, len <= 64: 1 kernel), or the Gram,
-tridiagonal reduction, eigenvectors and three apply kernels (eigensolver: 6), or Jacobi and
-apply (2); parameter models add the copy of the active flags (1).  The 12-coil 256x256
-launch list (ncu) shows 14 kernels per iteration: tridiag, eigvec, Gram, the three apply
-kernels, lift, four transforms, adjoint, DC and the reduction.
+tridiagonal reduction, eigenvectors, three apply kernels and the FP64 re-solve of flagged
+matrices (eigensolver: 7), or Jacobi and apply (2); parameter models add the copy of the
+active flags (1).  The 12-coil 256x256 iteration has 15 kernels: tridiag, eigvec, Gram,
+the three apply kernels, the FP64 re-solve, lift, four transforms, adjoint, DC and the
+reduction.
 """
 import bench
 
@@ -20,25 +21,25 @@ class _Plan:
         return self._f[axis]
 
 
-def test_bench_workload_counts_fourteen_per_iteration():
+def test_bench_workload_counts_fifteen_per_iteration():
     p = _Plan({"row": (256, 241, 192), "col": (256, 241, 192)})
-    assert bench.kernel_launches_per_iteration(p, True, "batched") == 14
+    assert bench.kernel_launches_per_iteration(p, True, "batched") == 15
     assert bench.kernel_launches_per_iteration(p, True, "batched", svd="jacobi") == 10
 
 
 def test_families_in_different_classes_get_their_own_sequence():
     # SHLR-V-like rows (s = 241) and a family of s = 192: two eigensolver sequences
     p = _Plan({"row": (256, 241, 384), "col": (256, 241, 192)})
-    assert bench.kernel_launches_per_iteration(p, True, "batched") == 8 + 12
+    assert bench.kernel_launches_per_iteration(p, True, "batched") == 8 + 14
 
 
 def test_parameter_model_small_and_eig_classes():
     # SHLR-VP: 1536 PE lifts 181x192 (eigensolver) + 36864 parameter lifts 5x32 (warp SVT)
     p = _Plan({"pe": (1536, 181, 192), "param": (36864, 5, 32)})
-    assert bench.kernel_launches_per_iteration(p, False, "batched") == 1 + 1 + 2 + 1 + 1 + 6 + 1 + 1
+    assert bench.kernel_launches_per_iteration(p, False, "batched") == 1 + 1 + 2 + 1 + 1 + 7 + 1 + 1
 
 
 def test_plain_mode_counts_per_matrix():
     p = _Plan({"row": (4, 57, 32), "col": (4, 57, 32)})
-    # per matrix: its lift and its six eigensolver kernels
-    assert bench.kernel_launches_per_iteration(p, True, "plain") == 8 + 2 + 2 + 2 + 8 * 7
+    # per matrix: its lift and its seven eigensolver kernels
+    assert bench.kernel_launches_per_iteration(p, True, "plain") == 8 + 2 + 2 + 2 + 8 * 8
