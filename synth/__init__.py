@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .configs import CONFIGS, Workload, get_config, unrolled_batch  # noqa: F401
+from .configs import ACS_SWEEP, CONFIGS, Workload, get_config, unrolled_batch, unrolled_instance  # noqa: F401
 
 
 # ---------------------------------------------------------------- transforms
@@ -139,6 +139,46 @@ def mask_1d_gaussian(M, N, R, n_center, rng, axis=0, sigma_frac=0.25):
     return m
 
 
+def mask_1d_uniform(M, N, R, n_center, axis=0, shift=0):
+    """Uniform (regular) 1D Cartesian mask: every R-th line counted from the
+    centre line (offset by ``shift``), plus ``n_center`` centre (ACS) lines."""
+    size = M if axis == 0 else N
+    R = int(round(R))
+    c = size // 2
+    lines = ((np.arange(size) - c - shift) % R) == 0
+    c0 = c - n_center // 2
+    lines[c0:c0 + n_center] = True
+    m = np.zeros((M, N), dtype=np.uint8)
+    if axis == 0:
+        m[lines, :] = 1
+    else:
+        m[:, lines] = 1
+    return m
+
+
+def partial_fourier(mask, frac, axis=0):
+    """Partial Fourier: keep the first ceil(frac * size) lines along ``axis``
+    (which contain the centre for frac > 1/2) and drop the rest of the
+    high-frequency side."""
+    m = mask.copy()
+    size = m.shape[axis]
+    keep = int(np.ceil(frac * size))
+    sl = [slice(None)] * m.ndim
+    sl[axis] = slice(keep, size)
+    m[tuple(sl)] = 0
+    return m
+
+
+def acs_sweep_masks(M, N, rate, acs_lines, seed, axis=0):
+    """1D Gaussian-density Cartesian masks, all at the same total sampling rate,
+    that differ in the number of centre (ACS) lines: {n_acs: mask}."""
+    out = {}
+    for n_acs in acs_lines:
+        rng = np.random.default_rng(seed)
+        out[int(n_acs)] = mask_1d_gaussian(M, N, 1.0 / rate, int(n_acs), rng, axis=axis)
+    return out
+
+
 def mask_poisson_2d(M, N, R, rng, acs=8, max_tries=30):
     """2D Poisson-disc mask (dart throwing) with an ``acs`` x ``acs`` centre block.
 
@@ -247,10 +287,14 @@ def make_inputs(cfg, small=None):
             mask = mask_1d_random(M, N, cfg.R, cfg.n_acs, rng_mask)
         elif cfg.mask == "poisson2d":
             mask = mask_poisson_2d(M, N, cfg.R, rng_mask, acs=cfg.n_acs)
+        elif cfg.mask == "uniform1d":
+            mask = mask_1d_uniform(M, N, cfg.R, cfg.n_acs)
         elif cfg.mask == "full":
             mask = np.ones((M, N), dtype=np.uint8)
         else:
             raise ValueError(cfg.mask)
+        if cfg.pf < 1.0:
+            mask = partial_fourier(mask, cfg.pf, axis=0)
         Y = acquire_2d(x, mask, cfg.sigma_n, cfg.seed)
         s = 1.0 / np.abs(Y).max()
         return {"Y": Y * s, "mask": mask, "truth": x * s}
@@ -263,8 +307,12 @@ def make_inputs(cfg, small=None):
         r = np.random.default_rng(cfg.seed + l)
         if cfg.mask == "full":
             masks[l] = 1
+        elif cfg.mask == "uniform1d":
+            masks[l] = mask_1d_uniform(M, N, cfg.R, cfg.n_acs, axis=1, shift=l)   # echo-varying offsets
         else:
             masks[l] = mask_1d_random(M, N, cfg.R, cfg.n_acs, r, axis=1)
+        if cfg.pf < 1.0:
+            masks[l] = partial_fourier(masks[l], cfg.pf, axis=1)
     Y = acquire_param(series, masks, cfg.sigma_n, cfg.seed)
     s = 1.0 / np.abs(Y).max()
     return {"Y": Y * s, "mask": masks, "truth": series * s}

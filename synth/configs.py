@@ -20,9 +20,10 @@ class Workload:
     window: int = 8
     window_param: int = 4
     weight: int = 1       # 0: W = I ; 1: circular finite-difference filter
-    mask: str = "random1d"
+    mask: str = "random1d"  # random1d, gauss1d, uniform1d, poisson2d, full
     R: float = 4.0
     n_acs: int = 24
+    pf: float = 1.0       # partial Fourier: fraction of the phase-encoding lines kept
     sigma_n: float = 0.0
     seed: int = 1
     te_ms: float = 10.0
@@ -57,25 +58,50 @@ CONFIGS = {
     "shlrvp_8c_192_8e": Workload(name="shlrvp_8c_192_8e", model="SHLR_VP", J=8, M=192, N=192, L=8,
                                  window=12, window_param=4, mask="random1d", R=6.0, n_acs=8,
                                  sigma_n=1e-3, seed=4, te_ms=10.0, beta=20.0, tau=20.0, lam2=2.0),
+    # the paper's further parallel-imaging patterns on the 12-coil 256x256 data:
+    # uniform R = 6 with 20 ACS lines; that pattern with 3/4 partial Fourier; the
+    # Gaussian Cartesian pattern (rate ~0.34) with 3/4 partial Fourier; the 2D
+    # Poisson-disc pattern with 4/5 partial Fourier (SHLR-V)
+    "shlr_12c_256_uniform6": Workload(name="shlr_12c_256_uniform6", model="SHLR", J=12, M=256, N=256,
+                                      window=16, mask="uniform1d", R=6.0, n_acs=20, sigma_n=1e-3, seed=2,
+                                      beta=20.0, tau=20.0),
+    "shlr_12c_256_uniform6_pf34": Workload(name="shlr_12c_256_uniform6_pf34", model="SHLR", J=12, M=256, N=256,
+                                           window=16, mask="uniform1d", R=6.0, n_acs=20, pf=0.75, sigma_n=1e-3,
+                                           seed=2, beta=20.0, tau=20.0),
+    "shlr_12c_256_gauss_pf34": Workload(name="shlr_12c_256_gauss_pf34", model="SHLR", J=12, M=256, N=256,
+                                        window=16, mask="gauss1d", R=2.94, n_acs=24, pf=0.75, sigma_n=1e-3,
+                                        seed=2, beta=20.0, tau=20.0),
+    "shlrv_12c_256_poisson_pf45": Workload(name="shlrv_12c_256_poisson_pf45", model="SHLR_V", J=12, M=256,
+                                           N=256, window=16, mask="poisson2d", R=5.0, n_acs=8, pf=0.8,
+                                           sigma_n=1e-3, seed=2, beta=20.0, tau=20.0),
 }
+
+# the ACS-line sweep: Gaussian Cartesian masks of one sampling rate, different ACS counts
+ACS_SWEEP = dict(rate=0.34, acs_lines=(8, 12, 16, 20, 24, 28, 32))
 
 
 def get_config(name: str) -> Workload:
     return CONFIGS[name]
 
 
-def unrolled_batch(n_inst: int = 16, n_iter: int = 10):
+def unrolled_batch(n_inst: int = 16, n_iter: int = 10, window: int = 16, n_acs: int = 24):
     """The uneven batch of the differentiable unrolled reconstruction: n_inst
     SHLR instances with M = N in 128..320 and 8..32 coils (every size and
-    coil count of the lists appears), window 6 (so C p = 6 J <= 192), 1D
-    random masks R = 4 with N/16 ACS lines, noise 1e-3, n_iter unrolled
-    iterations.  Deterministic: instance i takes sizes[i % 6], coils[3 i % 5]."""
+    coil count of the lists appears), window 16 (C p = 16 J up to 512
+    columns), 1D random masks R = 4 with 24 ACS lines, noise 1e-3, n_iter
+    unrolled iterations (the parallel-imaging recipe of the 12-coil workload).
+    Deterministic: instance i takes sizes[i % 6], coils[3 i % 5]."""
     sizes = [128, 160, 192, 240, 256, 320]
     coils = [8, 12, 16, 24, 32]
     out = []
     for i in range(n_inst):
         n = sizes[i % len(sizes)]
         out.append(Workload(name=f"unrolled_{i:02d}", model="SHLR", J=coils[(3 * i) % len(coils)], M=n, N=n,
-                            window=6, mask="random1d", R=4.0, n_acs=n // 16, sigma_n=1e-3, seed=500 + i,
+                            window=window, mask="random1d", R=4.0, n_acs=n_acs, sigma_n=1e-3, seed=500 + i,
                             beta=20.0, tau=20.0, n_iter=n_iter))
     return out
+
+
+def unrolled_instance(name: str) -> Workload:
+    """Instance `unrolled_NN` of unrolled_batch()."""
+    return unrolled_batch()[int(name.split("_")[1])]

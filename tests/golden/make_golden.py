@@ -21,11 +21,11 @@ import synth  # noqa: E402
 from oracle import admm  # noqa: E402
 
 N_SAMPLES = 4096
-RUNS = {"shlr_12c_256": 30, "shlrv_12c_256": 30}
+RUNS = {"shlr_12c_256": 30, "shlrv_12c_256": 30, "shlrvp_8c_192_8e": 30, "unrolled_03": 10, "unrolled_11": 10}
 
 
 def make(name, n_iter):
-    wl = synth.get_config(name)
+    wl = synth.unrolled_instance(name) if name.startswith("unrolled_") else synth.get_config(name)
     inp = synth.make_inputs(wl)
     t0 = time.time()
     if wl.model in ("SHLR", "SHLR_V"):

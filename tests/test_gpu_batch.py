@@ -99,3 +99,69 @@ def test_batch_rejects_single_operator_calls():
     with pytest.raises(api._lib.SelrError):
         plan.lift_shape("row")
     plan.close()
+
+
+def _param_instances(model):
+    base = get_config("shlrvp_8c_192_8e").with_(model=model)
+    sizes = [(2, 6, 48, 8, 8, 4), (1, 4, 40, 6, 6, 3), (3, 5, 36, 8, 7, 4)]     # J, M, N, L, p, p_P
+    out = []
+    for i, (J, M, N, L, p, pP) in enumerate(sizes):
+        cfg = base.with_(J=J, M=M, N=N, L=L, window=p, window_param=pP, seed=61 + i,
+                         lam2=2.0 if i != 1 else 1.5)
+        d = synth.make_inputs(cfg)
+        out.append((cfg, d["Y"], d["mask"]))
+    return out
+
+
+@pytest.mark.parametrize("model,gram", [("SHLR_VP", "fp32"), ("SHLR_P", "3xtf32")])
+def test_parameter_model_batch_matches_single_plans_and_oracle(model, gram):
+    """Uneven SHLR-P / SHLR-VP instances (different coils, FE positions, PE
+    lengths, echo counts, windows and lambda2) in one batched plan: the PE lifts
+    of all instances share the eigensolver launches and the echo-vector lifts
+    the warp-per-matrix SVT; each instance equals its own plan and the oracle
+    (Algorithm S2)."""
+    api = _api()
+    n_iter = 8
+    inst = _param_instances(model)
+    descs = [api.Desc.from_workload(c, max_iter=n_iter, gram=gram) for c, _, _ in inst]
+    plan = api.BatchPlan(descs)
+    Yp = plan.pack([torch.from_numpy(Y.astype(np.complex64)).cuda() for _, Y, _ in inst], torch.complex64)
+    mp = plan.pack([torch.from_numpy(m).cuda() for _, _, m in inst], torch.uint8, mask=True)
+    Xp = torch.empty_like(Yp)
+    it, _ = api.selr_solve_batch(plan, Yp, mp, Xp)
+    assert it == n_iter and api.selr_sync_status(plan) == 0
+    for i, (cfg, Y, m) in enumerate(inst):
+        single = api.Plan(descs[i])
+        Yd = torch.from_numpy(Y.astype(np.complex64)).cuda()
+        Xs = torch.empty_like(Yd)
+        api.selr_solve(single, Yd, torch.from_numpy(m).cuda(), Xs)
+        xb = plan.unpack(Xp, i).cpu().numpy().astype(np.complex128)
+        assert rel_l2(xb, Xs.cpu().numpy().astype(np.complex128)) <= 1e-5, i
+        ref = oadmm.shlr_p(Y, m, cfg, n_iter=n_iter)[0]
+        assert rel_l2(xb, ref) <= 1e-4, i
+        single.close()
+    plan.close()
+
+
+def test_parameter_model_batch_per_position_stopping():
+    """tol >= 0: every FE position of every instance stops on its own criterion;
+    the batch runs as long as the slowest position, and each instance equals the
+    oracle run with the same stopping rule."""
+    api = _api()
+    tol = 1e-4
+    inst = _param_instances("SHLR_VP")
+    descs = [api.Desc.from_workload(c, max_iter=40, tol=tol) for c, _, _ in inst]
+    plan = api.BatchPlan(descs)
+    Yp = plan.pack([torch.from_numpy(Y.astype(np.complex64)).cuda() for _, Y, _ in inst], torch.complex64)
+    mp = plan.pack([torch.from_numpy(m).cuda() for _, _, m in inst], torch.uint8, mask=True)
+    Xp = torch.empty_like(Yp)
+    it, _ = api.selr_solve_batch(plan, Yp, mp, Xp)
+    assert api.selr_sync_status(plan) == 0
+    longest = 0
+    for i, (cfg, Y, m) in enumerate(inst):
+        Xo, _, iters = oadmm.shlr_p(Y, m, cfg, n_iter=40, tol=tol)
+        longest = max(longest, int(iters.max()))
+        xb = plan.unpack(Xp, i).cpu().numpy().astype(np.complex128)
+        assert rel_l2(xb, Xo) < 1e-3, i
+    assert abs(it - longest) <= 1
+    plan.close()

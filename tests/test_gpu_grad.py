@@ -282,3 +282,26 @@ def test_unrolled_batch_sums_instance_gradients():
     g_tau = net.taus.grad.cpu().numpy().astype(np.float64)
     assert np.abs(g_t - ref_t).max() <= 2e-3 * np.abs(ref_t).max(), (g_t, ref_t)
     assert np.abs(g_tau - ref_tau).max() <= 2e-3 * np.abs(ref_tau).max(), (g_tau, ref_tau)
+
+
+def test_unrolled_forward_full_size_instance_matches_stored_oracle():
+    """The differentiable forward (per-op calls of UnrolledSHLR, t_k = 1/beta,
+    tau_k = tau, which is Algorithm S1) on the largest instance of the unrolled
+    batch (24 coils, 320x320, window 16, 24 ACS lines: lifted 305 x 384, order
+    305), 10 iterations, against FP64 oracle values stored by
+    tests/golden/make_golden.py."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "unrolled_11_10it.npz")
+    if not os.path.exists(path):
+        pytest.skip("no stored oracle values for unrolled_11")
+    from paper_2107_11650_gb300 import api
+    from paper_2107_11650_gb300.unrolled import UnrolledSHLR
+    g = np.load(path)
+    wl = synth.unrolled_instance("unrolled_11")
+    inp = synth.make_inputs(wl)
+    net = UnrolledSHLR(api.Desc.from_workload(wl, gram="3xtf32"), torch.from_numpy(inp["mask"]).cuda(), wl.n_iter)
+    with torch.no_grad():
+        X = net(torch.from_numpy(inp["Y"].astype(np.complex64)).cuda())
+    assert api.selr_sync_status(net.engine.plan) == 0
+    xs = X.cpu().numpy().astype(np.complex128).ravel()[g["idx"]]
+    assert np.linalg.norm(xs - g["values"]) / np.linalg.norm(g["values"]) < 1e-4
