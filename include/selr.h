@@ -140,18 +140,19 @@ void selr_desc_default(selr_desc *desc);
  * *out is set to NULL on failure. */
 selr_status selr_plan_create(const selr_desc *desc, selr_plan **out);
 
-/* One plan for n_inst independent reconstructions of uneven size (2D models
- * only), batched: every step of an iteration runs for all instances at once,
- * and all lifted matrices of one SVT size class (tiny / tridiagonal buckets
- * n <= 32, 64, 128, 208, larger) across all instances go to one launch per
- * kernel (the paper solves one problem at a time; batching is an engineering
- * extension).  descs[i] may differ in J, M, N, window and lambda; every other
- * field must equal descs[0] (SELR_ERR_INVALID_ARG otherwise;
- * SELR_ERR_UNSUPPORTED for parameter models).  1 <= n_inst <= 32.
- * selr_solve then takes packed arrays: instance i's Y / X [J][M][N] at
- * element offset k_offset(i) and its mask [M][N] at mask_offset(i)
- * (selr_plan_instance_layout).  With tol >= 0 the batch runs until every
- * instance meets the stopping rule (rel_out: the largest change).  The
+/* One plan for n_inst independent reconstructions of uneven size, batched:
+ * every step of an iteration runs for all instances at once, and all lifted
+ * matrices of one SVT size class (tiny / tridiagonal buckets n <= 32, 64,
+ * 128, 208, larger) across all instances go to one launch per kernel (the
+ * paper solves one problem at a time; batching is an engineering extension).
+ * descs[i] may differ in J, M, N, L, window, window_param, lambda and lambda2;
+ * every other field must equal descs[0] (SELR_ERR_INVALID_ARG otherwise).
+ * 1 <= n_inst <= 32.  selr_solve then takes packed arrays: instance i's
+ * Y / X [L][J][M][N] at element offset k_offset(i) and its mask [L][M][N] at
+ * mask_offset(i) (selr_plan_instance_layout).  With tol >= 0 a 2D batch runs
+ * until every instance meets the stopping rule (rel_out: the largest change);
+ * a parameter-model batch freezes each FE position of each instance on its own
+ * criterion (Algorithm S2) and stops when none is left.  The
  * single-operator entry points (selr_lift_shape, selr_transform, selr_lift,
  * selr_adjoint, selr_dc, selr_dc_vjp) return SELR_ERR_UNSUPPORTED on a plan
  * with more than one instance; selr_svt / selr_svt_vjp work on any plan. */
@@ -405,6 +406,46 @@ selr_status selr_axpby(int64_t n, float a, const void *x, float b, const void *y
 /* *out = Re sum_i conj(x_i) y_i over n complex64 elements (device), reduced
  * in a fixed order in double precision; out is a device float. */
 selr_status selr_dot_re(selr_plan *plan, int64_t n, const void *x, const void *y, float *out, selr_stream stream);
+
+/* ---------------------------------------------------------------------
+ * Evaluation of reconstructions (Sec. IV; Supplement S3).  Plan-free; every
+ * pointer is a device pointer unless marked host; nothing is allocated;
+ * reductions run in a fixed order (deterministic).
+ * --------------------------------------------------------------------- */
+
+/* SSOS coil combination: out[b][p] = sqrt(sum_j |X[b][j][p]|^2) for X
+ * [nb][J][npix] complex64 (nb = 1 for a 2D image [J][M][N] with npix = M N;
+ * nb = L echoes for parameter data [L][J][M][N]).  out: float [nb][npix]. */
+selr_status selr_ssos(const void *X, int32_t nb, int32_t J, int64_t npix, float *out, selr_stream stream);
+
+/* RLNE = ||x - xhat||_2 / ||x||_2 (Supplement S3) over n floats; *out
+ * (device float) receives it (0 when x = 0).  FP64 accumulation. */
+selr_status selr_rlne(const float *x, const float *xhat, int64_t n, float *out, selr_stream stream);
+
+/* MSSIM of reference A and image B (real [M][N], Supplement S3): the mean over
+ * every window position that fits in the image of
+ *   (2 mu_a mu_b + C1)(2 sigma_ab + C2) / ((mu_a^2 + mu_b^2 + C1)(sigma_a^2 + sigma_b^2 + C2)),
+ * with Gaussian-weighted local statistics.  The paper fixes neither window nor
+ * constants: an 11 x 11 Gaussian window (sigma 1.5, weights summing to 1) and
+ * C1 = (0.01 L)^2, C2 = (0.03 L)^2 are taken, L = dynamic range (host value,
+ * > 0; usually max A, see selr_max).  ssim_map: caller-owned float
+ * [(M - 10)(N - 10)] receiving the per-window values; *out (device float) the
+ * mean.  M, N >= 11. */
+selr_status selr_mssim(const float *A, const float *B, int32_t M, int32_t N, float L, float *ssim_map, float *out,
+                       selr_stream stream);
+
+/* *out (device float) = max of v[0..n). */
+selr_status selr_max(const float *v, int64_t n, float *out, selr_stream stream);
+
+/* Pixel-by-pixel nonlinear least-squares T2 fit (Sec. IV, T2 mapping): for
+ * every pixel p of S [L][npix] (magnitudes, e.g. SSOS per echo) fits
+ * S_l = M0 exp(-TE_l / T2) by Levenberg-Marquardt in FP64 on (M0, 1/T2)
+ * from the log-linear fit.  te_ms: HOST float [L] echo times, 2 <= L <= 32.
+ * T2_out [npix] (ms) and M0_out [npix] (may be NULL) are NaN where a sample
+ * is not positive or T2 falls outside [t2_min, t2_max] (the paper excludes
+ * T2 values outside a reasonable range without stating it). */
+selr_status selr_t2_fit(const float *S, const float *te_ms, int32_t L, int64_t npix, float t2_min, float t2_max,
+                        float *T2_out, float *M0_out, selr_stream stream);
 
 /* Measurement utility (no counterpart in the paper): the FP32 FMA rate of the
  * current device, the denominator of the eigensolver's roofline.  Runs

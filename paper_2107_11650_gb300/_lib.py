@@ -56,6 +56,12 @@ SIGNATURES = {
     "selr_plan_rank_sums": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_int64), c_int32, ctypes.POINTER(c_int32),
                                       c_void_p]),
     "selr_probe_fp32_peak": (c_int32, [c_int32, c_int32, ctypes.POINTER(c_float), ctypes.POINTER(c_float)]),
+    "selr_ssos": (c_int32, [c_void_p, c_int32, c_int32, ctypes.c_int64, c_void_p, c_void_p]),
+    "selr_rlne": (c_int32, [c_void_p, c_void_p, ctypes.c_int64, c_void_p, c_void_p]),
+    "selr_mssim": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_float, c_void_p, c_void_p, c_void_p]),
+    "selr_max": (c_int32, [c_void_p, ctypes.c_int64, c_void_p, c_void_p]),
+    "selr_t2_fit": (c_int32, [c_void_p, ctypes.POINTER(c_float), c_int32, ctypes.c_int64, c_float, c_float, c_void_p,
+                              c_void_p, c_void_p]),
     "selr_sync_status": (c_int32, [c_void_p, c_void_p]),
     "selr_selftest_wait": (c_int32, [c_int32, c_int32]),
     "selr_set_iterations": (c_int32, [c_void_p, c_int32, c_float]),

@@ -392,3 +392,62 @@ def selr_dot_re(plan: Plan, x, y, out, stream=None):
     n = x.numel()
     check(plan.lib.selr_dot_re(plan.handle, n, _ptr(x, torch.complex64, "x"), _ptr(y, torch.complex64, "y", n),
                                _ptr(out, torch.float32, "out", 1), _stream(stream)), "selr_dot_re")
+
+
+# ------------------------------------------------------------- evaluation
+def selr_ssos(X, stream=None):
+    """SSOS over coils of X [J][M][N] or [L][J][M][N] complex64 -> float32 [M][N] or [L][M][N]."""
+    lib = _lib.load()
+    if X.dim() not in (3, 4):
+        raise ValueError("X must be [J][M][N] or [L][J][M][N]")
+    nb, J = (1, X.shape[0]) if X.dim() == 3 else (X.shape[0], X.shape[1])
+    npix = X.shape[-1] * X.shape[-2]
+    out = torch.empty((nb,) + tuple(X.shape[-2:]), dtype=torch.float32, device=X.device)
+    check(lib.selr_ssos(_ptr(X, torch.complex64, "X"), nb, J, npix, _ptr(out, torch.float32, "out"), _stream(stream)),
+          "selr_ssos")
+    return out[0] if X.dim() == 3 else out
+
+
+def selr_rlne(x, xhat, stream=None):
+    """RLNE of xhat against x (float32 device tensors of equal size) -> device float32[1]."""
+    lib = _lib.load()
+    out = torch.empty(1, dtype=torch.float32, device=x.device)
+    check(lib.selr_rlne(_ptr(x, torch.float32, "x"), _ptr(xhat, torch.float32, "xhat", x.numel()), x.numel(),
+                        _ptr(out, torch.float32, "out"), _stream(stream)), "selr_rlne")
+    return out
+
+
+def selr_max(v, stream=None):
+    lib = _lib.load()
+    out = torch.empty(1, dtype=torch.float32, device=v.device)
+    check(lib.selr_max(_ptr(v, torch.float32, "v"), v.numel(), _ptr(out, torch.float32, "out"), _stream(stream)),
+          "selr_max")
+    return out
+
+
+def selr_mssim(A, B, L=None, stream=None):
+    """MSSIM of reference A and image B (float32 [M][N] device tensors) -> (device float32[1], SSIM map)."""
+    lib = _lib.load()
+    M, N = A.shape
+    if L is None:
+        L = float(selr_max(A, stream).item())
+    smap = torch.empty((M - 10, N - 10), dtype=torch.float32, device=A.device)
+    out = torch.empty(1, dtype=torch.float32, device=A.device)
+    check(lib.selr_mssim(_ptr(A, torch.float32, "A"), _ptr(B, torch.float32, "B", A.numel()), M, N, float(L),
+                         _ptr(smap, torch.float32, "ssim_map"), _ptr(out, torch.float32, "out"), _stream(stream)),
+          "selr_mssim")
+    return out, smap
+
+
+def selr_t2_fit(S, te_ms, t2_min=1.0, t2_max=1000.0, stream=None):
+    """Pixelwise T2 fit of magnitudes S [L][...] (float32 device) at echo times te_ms -> (T2, M0)."""
+    lib = _lib.load()
+    L = S.shape[0]
+    npix = S.numel() // L
+    te = (ctypes.c_float * L)(*[float(t) for t in te_ms])
+    T2 = torch.empty(S.shape[1:], dtype=torch.float32, device=S.device)
+    M0 = torch.empty_like(T2)
+    check(lib.selr_t2_fit(_ptr(S, torch.float32, "S"), te, L, npix, float(t2_min), float(t2_max),
+                          _ptr(T2, torch.float32, "T2"), _ptr(M0, torch.float32, "M0"), _stream(stream)),
+          "selr_t2_fit")
+    return T2, M0

@@ -194,8 +194,8 @@ k_gram_tc(GroupSet gs, int mat_begin, const cf *B0, cf *Gp, const int *active, u
     const Group &g = gs.g[gi];
     pdl_release_dependents();
     if (active) {
-        if (g.kind == G_PE && active[mat / g.L] == 0) return;
-        if (g.kind == G_PARAM && active[mat / g.N] == 0) return;
+        if (g.kind == G_PE && active[g.aoff + mat / g.L] == 0) return;
+        if (g.kind == G_PARAM && active[g.aoff + mat / g.N] == 0) return;
     }
     const int n = g.s, len = g.len, K = 2 * len;
     const int N = (n + 15) & ~15;                  // MMA N (multiple of 16 for M = 128)

@@ -16,6 +16,8 @@ struct Inst {
     float lambda;
     long long nK, koff, mkoff;   // k-space elements; offsets in K-sized arrays and in the mask
     int poff;                    // offset of its [M][2] partial sums
+    int aoff;                    // offset of its FE positions in the activity flags (parameter models)
+    int roff;                    // offset of its block in `rel` (1 value, or 1 + M for parameter models)
     FftTable ftM, ftN;
     cf *twM, *twN, *wM, *wN;
     float *da, *db;
@@ -46,6 +48,8 @@ struct selr_plan {
     double *partial;
     float *rel;
     int *active, *active_next;
+    int Mact;                    // length of the activity flags: FE positions of all instances
+    int nrel;                    // length of `rel`
     unsigned *status;
     size_t bytes;
     float *h_rel;          // pinned host mirror
@@ -311,7 +315,6 @@ static selr_status check_batch(const selr_desc *ds, int n) {
     if (n == 1) return SELR_OK;
     for (int i = 0; i < n; ++i) {
         const selr_desc &a = ds[0], &b = ds[i];
-        if (b.model > SELR_SHLR_V) return SELR_ERR_UNSUPPORTED;
         if (b.model != a.model || b.weight != a.weight || b.beta != a.beta || b.tau != a.tau ||
             b.d_init != a.d_init || b.max_iter != a.max_iter || b.tol != a.tol || b.exec != a.exec ||
             b.svd_method != a.svd_method || b.gram_precision != a.gram_precision ||
@@ -341,28 +344,36 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
     GroupSet &gs = p->gs;
     gs.n = 0;
     long long koff = 0, mkoff = 0;
-    int poff = 0;
+    int poff = 0, aoff = 0, roff = 0;
     for (int i = 0; i < n_inst; ++i) {
         const selr_desc &di = ds[i];
         Inst &I = p->inst[i];
         I.J = di.J; I.M = di.M; I.N = di.N; I.L = di.L; I.p = di.window; I.lambda = di.lambda;
         I.nK = (long long)di.L * di.J * di.M * di.N;
-        I.koff = koff; I.mkoff = mkoff; I.poff = poff;
+        I.koff = koff; I.mkoff = mkoff; I.poff = poff; I.aoff = aoff; I.roff = roff;
         koff += I.nK;
         mkoff += (long long)di.L * di.M * di.N;
         poff += 2 * di.M;
+        aoff += p->model2d ? 0 : di.M;
+        roff += p->model2d ? 1 : 1 + di.M;
         if (p->model2d) {
             gs.g[gs.n] = make_group(G_ROW, di.M, di.N, di.window, di.J, p->vc, di.M, di.N, 1, t1);
             gs.g[gs.n++].inst = i;
             gs.g[gs.n] = make_group(G_COL, di.N, di.M, di.window, di.J, p->vc, di.M, di.N, 1, t1);
             gs.g[gs.n++].inst = i;
         } else {
-            gs.g[gs.n++] = make_group(G_PE, di.M * di.L, di.N, di.window, di.J, p->vc, di.M, di.N, di.L, t1);
-            gs.g[gs.n++] = make_group(G_PARAM, di.M * di.N, di.L, di.window_param, di.J, 0, di.M, di.N, di.L,
-                                      di.lambda2 / di.beta);
+            gs.g[gs.n] = make_group(G_PE, di.M * di.L, di.N, di.window, di.J, p->vc, di.M, di.N, di.L, t1);
+            gs.g[gs.n].inst = i;
+            gs.g[gs.n++].aoff = I.aoff;
+            gs.g[gs.n] = make_group(G_PARAM, di.M * di.N, di.L, di.window_param, di.J, 0, di.M, di.N, di.L,
+                                    di.lambda2 / di.beta);
+            gs.g[gs.n].inst = i;
+            gs.g[gs.n++].aoff = I.aoff;
         }
     }
     p->nK = koff;
+    p->Mact = p->model2d ? d->M : aoff;
+    p->nrel = roff;
     for (int k = 0; k < gs.n; ++k) {
         if (gs.g[k].len > 512 || gs.g[k].s > 1024) { delete p; return SELR_ERR_SHAPE; }
         if (d->svd_method == SELR_SVD_EIG && gs.g[k].s > 480) { delete p; return SELR_ERR_SHAPE; }
@@ -419,13 +430,13 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
             AL(p->f64work, 16 * (size_t)mx * SELR_FP64_SLOTS);
         }
     }
-    const size_t nrel = (size_t)(n_inst > 1 + d->M ? n_inst : 1 + d->M);
+    const size_t nrel = (size_t)p->nrel;
     AL(p->sigma, sizeof(float) * (size_t)p->vec_elems);
     AL(p->mat_status, sizeof(int) * (size_t)gs.total);
     AL(p->partial, sizeof(double) * (size_t)poff);
     AL(p->rel, sizeof(float) * nrel);
-    AL(p->active, sizeof(int) * (size_t)d->M);
-    AL(p->active_next, sizeof(int) * (size_t)d->M);
+    AL(p->active, sizeof(int) * (size_t)p->Mact);
+    AL(p->active_next, sizeof(int) * (size_t)p->Mact);
     AL(p->status, sizeof(unsigned));
     for (int i = 0; i < n_inst; ++i) {
         Inst &I = p->inst[i];
@@ -487,7 +498,7 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
         }
     }
     if (cudaMallocHost((void **)&p->h_rel, sizeof(float) * nrel) != cudaSuccess ||
-        cudaMallocHost((void **)&p->h_active, sizeof(int) * (size_t)d->M) != cudaSuccess) {
+        cudaMallocHost((void **)&p->h_active, sizeof(int) * (size_t)p->Mact) != cudaSuccess) {
         cudaGetLastError();
         selr_plan_destroy(p);
         return SELR_ERR_ALLOC;
@@ -726,11 +737,11 @@ static cudaError_t dc_step(selr_plan *p, const cf *Y, const uint8_t *mask, cf *a
         a.lambda = I.lambda;
         a.beta = p->d.beta;
         a.partial = p->partial + I.poff;
-        a.active = active;
+        a.active = active ? active + I.aoff : nullptr;
         a.status = p->status;
         if ((e = launch_dc(a, st)) != cudaSuccess) return e;
-        if ((e = launch_rel_finalize(p->partial + I.poff, I.M, !p->model2d, p->d.tol, p->rel + i, active_next, st)) !=
-            cudaSuccess)
+        if ((e = launch_rel_finalize(p->partial + I.poff, I.M, !p->model2d, p->d.tol, p->rel + I.roff,
+                                     active_next ? active_next + I.aoff : nullptr, st)) != cudaSuccess)
             return e;
     }
     return cudaSuccess;
@@ -789,7 +800,7 @@ static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_
                         return e;
                     if ((e = svd_apply(p, p->gs, m, 1, a, 7, st)) != cudaSuccess) return e;
                 }
-                if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->M, st);
+                if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->Mact, st);
                 return cudaSuccess;
             }
             return launch_lift(p->gs, 0, 0, total, p->D, 0, ib, lift_out, lift_out2, 0, act, st);
@@ -800,7 +811,7 @@ static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_
         default:
             if (plain) return cudaSuccess;
             if ((e = svd_apply(p, p->gs, 0, total, a, 4, st)) != cudaSuccess) return e;
-            if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->M, st);
+            if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->Mact, st);
             return cudaSuccess;
     }
 }
@@ -868,8 +879,8 @@ static StateLayout state_layout(const selr_plan *p) {
     L.d = al(L.k + sizeof(cf) * (size_t)p->nK);
     L.e = al(L.d + sizeof(cf) * (size_t)p->lift_elems);
     L.act = al(L.e + sizeof(cf) * (size_t)p->lift_elems);
-    L.act_next = al(L.act + sizeof(int) * (size_t)p->d.M);
-    L.total = al(L.act_next + sizeof(int) * (size_t)p->d.M);
+    L.act_next = al(L.act + sizeof(int) * (size_t)p->Mact);
+    L.total = al(L.act_next + sizeof(int) * (size_t)p->Mact);
     return L;
 }
 
@@ -883,8 +894,8 @@ static cudaError_t state_copy(selr_plan *p, unsigned char *state, int save, cuda
     const StateLayout L = state_layout(p);
     struct { void *plan; size_t off, bytes; } r[] = {
         {p->K, L.k, sizeof(cf) * (size_t)p->nK}, {p->D, L.d, sizeof(cf) * (size_t)p->lift_elems},
-        {p->E, L.e, sizeof(cf) * (size_t)p->lift_elems}, {p->active, L.act, sizeof(int) * (size_t)p->d.M},
-        {p->active_next, L.act_next, sizeof(int) * (size_t)p->d.M}};
+        {p->E, L.e, sizeof(cf) * (size_t)p->lift_elems}, {p->active, L.act, sizeof(int) * (size_t)p->Mact},
+        {p->active_next, L.act_next, sizeof(int) * (size_t)p->Mact}};
     for (auto &x : r) {
         cudaError_t e = save ? cudaMemcpyAsync(state + x.off, x.plan, x.bytes, cudaMemcpyDeviceToDevice, st)
                              : cudaMemcpyAsync(x.plan, state + x.off, x.bytes, cudaMemcpyDeviceToDevice, st);
@@ -898,8 +909,8 @@ static cudaError_t admm_init(selr_plan *p, const cf *Y, cudaStream_t st) {
     if ((e = cudaMemcpyAsync(p->K, Y, sizeof(cf) * p->nK, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
     if ((e = launch_fill(p->D, p->lift_elems, mk(p->d.d_init, 0.f), st)) != cudaSuccess) return e;
     if ((e = launch_fill(p->E, p->lift_elems, mk(-p->d.d_init / p->d.beta, 0.f), st)) != cudaSuccess) return e;
-    if ((e = launch_fill_i(p->active, p->M, 1, st)) != cudaSuccess) return e;
-    return launch_fill_i(p->active_next, p->M, 1, st);
+    if ((e = launch_fill_i(p->active, p->Mact, 1, st)) != cudaSuccess) return e;
+    return launch_fill_i(p->active_next, p->Mact, 1, st);
 }
 
 static cudaError_t output_image(selr_plan *p, cf *X, cudaStream_t st) {
@@ -967,16 +978,17 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
             }
             ++iters;
             if (!fixed) {
-                CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float) * p->n_inst, cudaMemcpyDeviceToHost, st));
-                if (!p->model2d) CK(cudaMemcpyAsync(p->h_active, p->active, sizeof(int) * p->M, cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float) * p->nrel, cudaMemcpyDeviceToHost, st));
+                if (!p->model2d)
+                    CK(cudaMemcpyAsync(p->h_active, p->active, sizeof(int) * p->Mact, cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
-                last_rel = p->h_rel[0];
-                for (int i = 1; i < p->n_inst; ++i) last_rel = fmaxf(last_rel, p->h_rel[i]);
+                last_rel = p->h_rel[p->inst[0].roff];
+                for (int i = 1; i < p->n_inst; ++i) last_rel = fmaxf(last_rel, p->h_rel[p->inst[i].roff]);
                 if (p->model2d) {
                     if (last_rel < p->d.tol) break;      // every instance meets the criterion
                 } else {
                     int any = 0;
-                    for (int m = 0; m < p->M; ++m) any |= p->h_active[m];
+                    for (int m = 0; m < p->Mact; ++m) any |= p->h_active[m];
                     if (!any) break;
                 }
             }
@@ -988,10 +1000,10 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
     CK(output_image(p, (cf *)X_out, st));
     if (rel_out || iters_out) {
         if (rel_out && fixed) {
-            CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float) * p->n_inst, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(p->h_rel, p->rel, sizeof(float) * p->nrel, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            last_rel = p->h_rel[0];
-            for (int i = 1; i < p->n_inst; ++i) last_rel = fmaxf(last_rel, p->h_rel[i]);
+            last_rel = p->h_rel[p->inst[0].roff];
+            for (int i = 1; i < p->n_inst; ++i) last_rel = fmaxf(last_rel, p->h_rel[p->inst[i].roff]);
         }
         if (rel_out) *rel_out = last_rel;
         if (iters_out) *iters_out = iters;

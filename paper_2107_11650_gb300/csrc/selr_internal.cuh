@@ -47,6 +47,7 @@ struct Group {
     long long poff;        // offset of matrix 0 in packed Gram storage (s (s+1) / 2 per matrix)
     int moff;              // index of matrix 0 among all matrices (status words)
     int inst;              // instance of a batched plan the family belongs to
+    int aoff;              // offset of the instance's FE positions in the activity flags
     const cf *w;           // weights (length nv) or nullptr (identity)
     const cf *src;         // lift source array
     cf *dst;               // adjoint destination array

@@ -43,8 +43,8 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Is the matrix `mat` of group g frozen (parameter models, converged FE position)?
 __device__ __forceinline__ bool frozen(const Group &g, int mat, const int *active) {
     if (!active) return false;
-    if (g.kind == G_PE) return active[mat / g.L] == 0;
-    if (g.kind == G_PARAM) return active[mat / g.N] == 0;
+    if (g.kind == G_PE) return active[g.aoff + mat / g.L] == 0;
+    if (g.kind == G_PARAM) return active[g.aoff + mat / g.N] == 0;
     return false;
 }
 

@@ -97,8 +97,8 @@ __device__ float bsum(float v, float *red) {
 
 __device__ __forceinline__ bool is_frozen(const Group &g, int mat, const int *active) {
     if (!active) return false;
-    if (g.kind == G_PE) return active[mat / g.L] == 0;
-    if (g.kind == G_PARAM) return active[mat / g.N] == 0;
+    if (g.kind == G_PE) return active[g.aoff + mat / g.L] == 0;
+    if (g.kind == G_PARAM) return active[g.aoff + mat / g.N] == 0;
     return false;
 }
 

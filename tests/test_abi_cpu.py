@@ -113,3 +113,10 @@ def test_null_arguments(lib):
     assert lib.selr_probe_fp32_peak(2, 16, ctypes.byref(tf), None) == 1
     assert lib.selr_probe_fp32_peak(0, 0, ctypes.byref(tf), None) == 1
     assert lib.selr_probe_fp32_peak(0, 16, None, None) == 1
+    # evaluation entry points
+    assert lib.selr_ssos(None, 1, 1, 1, None, None) == 1
+    assert lib.selr_rlne(None, None, 1, None, None) == 1
+    assert lib.selr_mssim(None, None, 16, 16, 1.0, None, None, None) == 1
+    assert lib.selr_max(None, 1, None, None) == 1
+    te = (ctypes.c_float * 1)(1.0)
+    assert lib.selr_t2_fit(None, te, 1, 1, 1.0, 10.0, None, None, None) == 1
