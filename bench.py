@@ -247,7 +247,7 @@ def run_gpu(args, rank, world):
     X = torch.empty_like(Y)
     stream = torch.cuda.Stream()
     results = {}
-    model2d = wl.model in ("SHLR", "SHLR_V")
+    model2d = wl.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV")
     modes = ["batched", "plain"] if args.exec == "both" else [args.exec]
     for mode in modes:
         plan = api.Plan(api.Desc.from_workload(wl, exec=mode, max_iter=max(args.warmup, 1), svd=args.svd,
@@ -402,7 +402,7 @@ def oracle_sample(wl, n_svt=64):
         _ORACLE_CACHE[wl.name] = synth.make_inputs(wl)
     inp = _ORACLE_CACHE[wl.name]
     b = wl.beta
-    if wl.model in ("SHLR", "SHLR_V"):
+    if wl.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV"):
         s = oadmm.Shlr2D(inp["Y"], inp["mask"], wl)
         st = s.init_state()
         t0 = time.perf_counter()
@@ -442,7 +442,7 @@ def cpu_baseline(wl, iters=2):
     if wl.name not in _ORACLE_CACHE:
         _ORACLE_CACHE[wl.name] = synth.make_inputs(wl)
     inp = _ORACLE_CACHE[wl.name]
-    two_d = wl.model in ("SHLR", "SHLR_V")
+    two_d = wl.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV")
     s = oadmm.Shlr2D(inp["Y"], inp["mask"], wl) if two_d else oadmm.ShlrParam(inp["Y"], inp["mask"], wl)
     st = s.init_state()
     act = None if two_d else np.ones(wl.M, bool)
@@ -758,7 +758,7 @@ def main():
         fp32_peak, fp32_src = 152 * 128 * 2 * smax * 1e6 / 1e12, "derived: 152 SMs x 128 lanes x 2 x max SM clock"
     tf32_peak = mp.get("tf32_tflops")
     achieved = jac["flops"] / (jac["ms"] / 1000.0) / 1e12
-    gram = (results.get("tuning") or {}).get("gram", gram_for(args, wl.model in ("SHLR", "SHLR_V")))
+    gram = (results.get("tuning") or {}).get("gram", gram_for(args, wl.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV")))
     fk = jac["flops_by_kind"]
     bf16 = peaks.get("bf16_tflops")
     p_tc = {"fp32": fp32_peak, "tf32": tf32_peak, "3xtf32": (tf32_peak / 3.0) if tf32_peak else None,
@@ -777,7 +777,7 @@ def main():
         "config": {"workload": wl.name, "coils": wl.J, "size": [wl.M, wl.N], "window": wl.window,
                    "model": wl.model, "mask": f"{wl.mask} R={wl.R} acs={wl.n_acs}",
                    "matrices_per_step": b["nmat"], "exec": "batched (graph-captured)", "svd": args.svd,
-                   "gram": (results.get("tuning") or {}).get("gram", gram_for(args, wl.model in ("SHLR", "SHLR_V"))),
+                   "gram": (results.get("tuning") or {}).get("gram", gram_for(args, wl.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV"))),
                    "l2": "per-step state (D, E, work copies: 760 MB) exceeds L2; no flush"},
         "plain": ({"value": whole_job_value(world, results["plain"]["steps"], results["plain"]["ms"]),
                    "ms_per_step": results["plain"]["ms"] / results["plain"]["steps"],

@@ -58,7 +58,9 @@ typedef enum {
     SELR_SHLR = 0,     /* Eq. 2: row + column lifts, H~ W~ F~                         */
     SELR_SHLR_V = 1,   /* Eq. 5: as SHLR with virtual coils H~_vc (Eq. 4)               */
     SELR_SHLR_P = 2,   /* Eq. 7: per FE position, PE lifts + parameter-dimension lifts  */
-    SELR_SHLR_VP = 3   /* Eq. 8: SHLR-P with virtual coils on the PE lifts              */
+    SELR_SHLR_VP = 3,  /* Eq. 8: SHLR-P with virtual coils on the PE lifts              */
+    SELR_SHLR_S = 4,   /* Eq. 3: SHLR + lambda1/2 ||X - G X||^2 (SPIRiT operator G)      */
+    SELR_SHLR_SV = 5   /* Eq. 6: SHLR-S with virtual coils                              */
 } selr_model;
 
 /* Lift families.  Each names the vectors that are lifted and their source array. */
@@ -118,6 +120,14 @@ typedef struct {
     int32_t exec;             /* selr_exec                                                */
     int32_t svd_method;       /* selr_svd_method                                          */
     int32_t gram_precision;   /* selr_gram_precision (SELR_SVD_EIG path)                   */
+    float lambda1;            /* SHLR-S / SHLR-SV: SPIRiT weight lambda_1 (Eq. 3; default 1e3)   */
+    int32_t spirit_ksize;     /* SPIRiT kernel size: 3, 5 (default) or 7                      */
+    int32_t spirit_acs;       /* ACS rows for the calibration: the spirit_acs centre rows of
+                                 k-space (all columns), which must be fully sampled (default 24) */
+    float spirit_reg;         /* Tikhonov weight of the calibration, relative to the mean
+                                 diagonal of the normal matrix (default 1e-3)                   */
+    int32_t cg_iters;         /* preconditioned CG iterations of the SHLR-S / SHLR-SV X-update
+                                 (default 30)                                                   */
     int32_t fp64_fallback;    /* SELR_SVD_EIG: 1 (default) = re-solve in FP64 every matrix whose
                                  thresholding is not determined in FP32 (t^2 below the FP32
                                  resolution 64 eps_32 lambda_max of its Gram eigenvalues, with
@@ -130,7 +140,8 @@ typedef struct selr_plan selr_plan;   /* opaque; owns its device workspace */
 
 /* Fill *desc with defaults (SHLR, weight 1, beta = tau = 20, lambda = 1e4,
  * lambda2 = 2, d_init = 1, max_iter = 30, tol = -1, 30 sweeps, tol 2e-6,
- * batched, SELR_SVD_EIG, SELR_GRAM_FP32, fp64_fallback = 1). */
+ * batched, SELR_SVD_EIG, SELR_GRAM_FP32, lambda1 = 1e3, SPIRiT kernel 5 x 5 on 24
+ * ACS rows with relative Tikhonov weight 1e-3, 30 CG iterations, fp64_fallback = 1). */
 void selr_desc_default(selr_desc *desc);
 
 /* Validate *desc and allocate the plan's device workspace on the current
@@ -155,7 +166,9 @@ selr_status selr_plan_create(const selr_desc *desc, selr_plan **out);
  * criterion (Algorithm S2) and stops when none is left.  The
  * single-operator entry points (selr_lift_shape, selr_transform, selr_lift,
  * selr_adjoint, selr_dc, selr_dc_vjp) return SELR_ERR_UNSUPPORTED on a plan
- * with more than one instance; selr_svt / selr_svt_vjp work on any plan. */
+ * with more than one instance; selr_svt / selr_svt_vjp work on any plan.
+ * SHLR-S / SHLR-SV plans hold one instance (SELR_ERR_UNSUPPORTED for a batch
+ * of them). */
 selr_status selr_plan_create_batch(const selr_desc *descs, int32_t n_inst, selr_plan **out);
 
 /* Element offsets of instance inst in the packed k-space / image arrays and in
@@ -230,6 +243,23 @@ selr_status selr_svt_noalloc(void *A, int32_t nmat, int32_t rows, int32_t cols, 
  * Allocates nothing. */
 selr_status selr_svt_noalloc_status(selr_stream stream);
 
+/* SPIRiT calibration (Eq. 3 / Eq. 6; SHLR-S and SHLR-SV plans): the kernel g
+ * [J][J][ks][ks] that predicts each k-space sample of coil j from the ks x ks
+ * neighbourhoods of all coils (the sample itself excluded, circular in
+ * k-space), fitted on every kernel position inside the spirit_acs centre rows
+ * of Y [J][M][N] by Tikhonov-regularised least squares per target coil in
+ * FP64 (the paper gives neither kernel size nor calibration: these are
+ * readings), and from it the image-domain operator G - I, a J x J matrix per
+ * pixel, kept in the plan.  selr_solve calibrates from its own Y before the
+ * first iteration; selr_dc on such a plan needs this call first.
+ * SELR_ERR_UNSUPPORTED for other models. */
+selr_status selr_spirit_calibrate(selr_plan *plan, const void *Y, selr_stream stream);
+
+/* Copy of the calibrated kernel g [J][J][ks][ks] complex64 into g_out (device),
+ * row j = target coil; g[j][j][ks/2][ks/2] = 0.  SELR_ERR_UNSUPPORTED before a
+ * calibration or on other models. */
+selr_status selr_spirit_kernel(selr_plan *plan, void *g_out, selr_stream stream);
+
 /* Real adjoint of the lift (the transpose appearing in Eq. 15 / S7):
  * x_out = L^T E for the family `axis`.  Plain channel j contributes
  * conj(w) * H*(E_j); virtual coil J+j contributes flip(w * conj(H*(E_{J+j}))),
@@ -238,9 +268,12 @@ selr_status selr_svt_noalloc_status(selr_stream stream);
 selr_status selr_adjoint(selr_plan *plan, int32_t axis, const void *E, void *x_out,
                          selr_stream stream);
 
-/* X-update of Eq. 15 (2D) / Eq. S7 (parameter models) without the SPIRiT term,
- * as a pointwise divide in k-space:
+/* X-update of Eq. 15 (2D) / Eq. S7 (parameter models).  Without the SPIRiT
+ * term a pointwise divide in k-space:
  *   K = (lambda U Y + beta (F a + F' b)) / (lambda U + beta (d_a + d_b)).
+ * SHLR-S / SHLR-SV: (lambda U + beta (d_a + d_b) + lambda_1 F (G - I)^H (G - I) F*) K
+ * = lambda U Y + beta (F a + F' b), by cg_iters conjugate-gradient iterations
+ * preconditioned with the k-space diagonal, from the K passed in.
  * 2D: adj_a = row-lift adjoint (F along M applied here), adj_b = column-lift
  *     adjoint (F along N applied here).
  * Parameter: adj_a = PE-lift adjoint (already in PE k-space), adj_b =

@@ -10,7 +10,9 @@ zero-filled reconstruction F* Y, which only enters the first value of the
 stopping ratio ||X^(k+1) - X^(k)||^2 / ||X^(k)||^2.
 
 Readings (the paper is silent or garbled at these points):
-* No SPIRiT term (lambda_1 = 0): SHLR / SHLR-V / SHLR-P / SHLR-VP only.
+* SHLR-S / SHLR-SV (Eq. 3 / Eq. 6) add lambda_1/2 ||X - G X||^2 with the
+  SPIRiT operator G of oracle/spirit.py; their X-update is solved by CG
+  (see there).  The other models have no G term.
 * Eq. 15 without the G term is diagonal in 2D k-space: the row-lift normal
   operator is diag(d_r(k_n)), the column-lift one diag(d_c(k_m)), with
   d(k) = c(k)|w(k)|^2 [+ c(N-1-k)|w(N-1-k)|^2 for the VC channels], and the
@@ -31,6 +33,7 @@ from .hankel import (lift_rows, lift_rows_adjoint, lift_cols, lift_cols_adjoint,
                      lift_pe, lift_pe_adjoint, lift_param, lift_param_adjoint,
                      lift_vectors)
 from .svt import svt, nuclear_norm
+from . import spirit
 
 
 def normal_weights(N, p, w, vc):
@@ -65,19 +68,27 @@ def _dc_divide(lam, U, Y, rhs_b, den_b):
 def _params(cfg):
     return dict(model=cfg.model, p=cfg.window, pP=cfg.window_param, weight=cfg.weight,
                 lam=float(cfg.lam), lam2=float(cfg.lam2), beta=float(cfg.beta),
-                tau=float(cfg.tau), d0=float(cfg.d_init))
+                tau=float(cfg.tau), d0=float(cfg.d_init), lam1=float(getattr(cfg, "lam1", 0.0)),
+                ks=int(getattr(cfg, "spirit_k", 5)), reg=float(getattr(cfg, "spirit_reg", 1e-3)),
+                n_acs=int(getattr(cfg, "n_acs", 0)))
 
 
 # =========================================================== Algorithm S1
 class Shlr2D:
-    """SHLR (Eq. 2) / SHLR-V (Eq. 5) solved by Algorithm S1 without G."""
+    """SHLR (Eq. 2) / SHLR-V (Eq. 5) / SHLR-S (Eq. 3) / SHLR-SV (Eq. 6) solved
+    by Algorithm S1."""
 
     def __init__(self, Y, U, cfg):
         self.Y = np.asarray(Y, dtype=np.complex128)
         self.U = np.asarray(U).astype(np.float64)
         P = _params(cfg)
         self.P = P
-        self.vc = P["model"] == "SHLR_V"
+        self.vc = P["model"] in ("SHLR_V", "SHLR_SV")
+        self.spirit = P["model"] in ("SHLR_S", "SHLR_SV")
+        if self.spirit:
+            if not P["lam"] > 0:
+                raise ValueError("SHLR-S / SHLR-SV need a finite lambda")
+            self.g = spirit.calibrate(self.Y, P["n_acs"], P["ks"], P["reg"])
         J, M, N = self.Y.shape
         self.J, self.M, self.N = J, M, N
         p = P["p"]
@@ -103,8 +114,9 @@ class Shlr2D:
         Cc = ifftc(K, axis=2)         # F^1D along m of each image column
         return lift_rows(R, self.wN, p, self.vc), lift_cols(Cc, self.wM, p, self.vc)
 
-    def x_update(self, Zr, Zc, Dr, Dc):
-        """Eq. 15 without G, as a pointwise divide in 2D k-space."""
+    def x_update(self, Zr, Zc, Dr, Dc, K0=None):
+        """Eq. 15: without G a pointwise divide in 2D k-space; with G (SHLR-S /
+        SHLR-SV) conjugate gradients on the normal equations from K0."""
         P = self.P
         b, lam, p = P["beta"], P["lam"], P["p"]
         a_row = lift_rows_adjoint(Zr - Dr / b, self.wN, p, self.vc, self.J, self.N)
@@ -112,7 +124,13 @@ class Shlr2D:
         rhs_b = b * (fftc(a_row, axis=1) + fftc(a_col, axis=2))
         den_b = b * (self.d_r[None, None, :] + self.d_c[None, :, None])
         U = self.U[None]
-        return _dc_divide(lam, U, self.Y, rhs_b, den_b)
+        if not self.spirit:
+            return _dc_divide(lam, U, self.Y, rhs_b, den_b)
+        diag = lam * U + den_b
+        rhs = lam * U * self.Y + rhs_b
+        x0 = self.Y.copy() if K0 is None else K0
+        K, _ = spirit.cg(lambda x: spirit.normal_op(x, diag, P["lam1"], self.g), rhs, x0)
+        return K
 
     def z_update(self, LXr, LXc, Dr, Dc):
         t = 1.0 / self.P["beta"]
@@ -129,6 +147,8 @@ class Shlr2D:
         b, lam = P["beta"], P["lam"]
         LXr, LXc = self.lifts(K)
         val = 0.5 * lam * np.sum(np.abs(self.U[None] * (self.Y - K)) ** 2) if lam > 0 else 0.0
+        if self.spirit:
+            val += 0.5 * P["lam1"] * np.sum(np.abs(spirit.apply_g(K, self.g) - K) ** 2)
         val += nuclear_norm(Zr).sum() + nuclear_norm(Zc).sum()
         val += 0.5 * b * np.sum(np.abs(LXr - Zr + Dr / b) ** 2)
         val += 0.5 * b * np.sum(np.abs(LXc - Zc + Dc / b) ** 2)
@@ -140,12 +160,14 @@ class Shlr2D:
         val = nuclear_norm(LXr).sum() + nuclear_norm(LXc).sum()
         if self.P["lam"] > 0:
             val += 0.5 * self.P["lam"] * np.sum(np.abs(self.U[None] * (self.Y - K)) ** 2)
+        if self.spirit:
+            val += 0.5 * self.P["lam1"] * np.sum(np.abs(spirit.apply_g(K, self.g) - K) ** 2)
         return float(val)
 
     # -- Algorithm S1 -----------------------------------------------------
     def step(self, st):
         """One pass of the while-loop body: X, then Z, then D."""
-        K = self.x_update(st["Zr"], st["Zc"], st["Dr"], st["Dc"])
+        K = self.x_update(st["Zr"], st["Zc"], st["Dr"], st["Dc"], K0=st["K"])
         rel = np.sum(np.abs(K - st["K"]) ** 2) / np.sum(np.abs(st["K"]) ** 2)
         LXr, LXc = self.lifts(K)
         Zr, Zc = self.z_update(LXr, LXc, st["Dr"], st["Dc"])
@@ -257,7 +279,7 @@ def shlr_p(Yp, U, cfg, n_iter=None, tol=-1.0):
 
 
 # ============================================ dense cross-check (tiny sizes)
-def dense_x_update_2d(Y, U, Er, Ec, cfg):
+def dense_x_update_2d(Y, U, Er, Ec, cfg, g=None):
     """Solve the X-subproblem of Eq. 10 (no G) by dense normal equations.
 
     Built from the literal image-domain operators: for every row m,
@@ -268,7 +290,7 @@ def dense_x_update_2d(Y, U, Er, Ec, cfg):
     k-space of the minimiser.  Intended for J*M*N <= ~200.
     """
     P = _params(cfg)
-    vc = P["model"] == "SHLR_V"
+    vc = P["model"] in ("SHLR_V", "SHLR_SV")
     lam, b, p = P["lam"], P["beta"], P["p"]
     Y = np.asarray(Y, dtype=np.complex128)
     J, M, N = Y.shape
@@ -293,23 +315,34 @@ def dense_x_update_2d(Y, U, Er, Ec, cfg):
     def realify(z):
         return np.concatenate([z.real, z.imag])
 
-    cols_L, cols_A = [], []
+    def spirit_res(X):
+        # (G - I) X with G applied in the image domain as F2D* G_k F2D (the k-space correlation)
+        K = np.stack([fftc(fftc(X[j], axis=1), axis=0) for j in range(J)])
+        R = spirit.apply_g(K, g) - K
+        return np.stack([ifftc(ifftc(R[j], axis=1), axis=0) for j in range(J)]).ravel()
+
+    cols_L, cols_A, cols_G = [], [], []
     for k in range(2 * n):
         e = np.zeros(n, dtype=np.complex128)
         e[k % n] = 1.0 if k < n else 1.0j
         X = e.reshape(J, M, N)
         cols_L.append(realify(lift_all(X)))
         cols_A.append(realify(data(X)))
+        if g is not None:
+            cols_G.append(realify(spirit_res(X)))
     Lm = np.stack(cols_L, axis=1)
     Am = np.stack(cols_A, axis=1)
     tgt = realify(np.concatenate([Er.ravel(), Ec.ravel()]))
     y = realify((U[None] * Y).ravel())
     H = b * Lm.T @ Lm
-    g = b * Lm.T @ tgt
+    rhs = b * Lm.T @ tgt
     if lam > 0:
         H = H + lam * Am.T @ Am
-        g = g + lam * Am.T @ y
-    x = np.linalg.solve(H, g)
+        rhs = rhs + lam * Am.T @ y
+    if g is not None:
+        Gm = np.stack(cols_G, axis=1)
+        H = H + P["lam1"] * Gm.T @ Gm
+    x = np.linalg.solve(H, rhs)
     X = (x[:n] + 1j * x[n:]).reshape(J, M, N)
     return np.stack([fftc(fftc(X[j], axis=1), axis=0) for j in range(J)])
 

@@ -16,7 +16,7 @@ SELR_OK = 0
 STATUS_NAMES = {0: "SELR_OK", 1: "SELR_ERR_INVALID_ARG", 2: "SELR_ERR_SHAPE", 3: "SELR_ERR_CUDA",
                 4: "SELR_ERR_NO_CONVERGENCE", 5: "SELR_ERR_NONFINITE", 6: "SELR_ERR_TIMEOUT",
                 7: "SELR_ERR_UNSUPPORTED", 8: "SELR_ERR_ALLOC"}
-MODELS = {"SHLR": 0, "SHLR_V": 1, "SHLR_P": 2, "SHLR_VP": 3}
+MODELS = {"SHLR": 0, "SHLR_V": 1, "SHLR_P": 2, "SHLR_VP": 3, "SHLR_S": 4, "SHLR_SV": 5}
 AXES = {"row": 0, "col": 1, "pe": 2, "param": 3}
 EXEC = {"batched": 0, "plain": 1}
 SVD = {"eig": 0, "jacobi": 1}
@@ -32,7 +32,9 @@ class SelrDesc(ctypes.Structure):
                 ("lambda_", c_float), ("lambda2", c_float), ("beta", c_float), ("tau", c_float),
                 ("d_init", c_float), ("max_iter", c_int32), ("tol", c_float),
                 ("jacobi_max_sweeps", c_int32), ("jacobi_tol", c_float), ("exec_", c_int32),
-                ("svd_method", c_int32), ("gram_precision", c_int32), ("fp64_fallback", c_int32)]
+                ("svd_method", c_int32), ("gram_precision", c_int32), ("lambda1", c_float),
+                ("spirit_ksize", c_int32), ("spirit_acs", c_int32), ("spirit_reg", c_float), ("cg_iters", c_int32),
+                ("fp64_fallback", c_int32)]
 
 
 SIGNATURES = {
@@ -49,6 +51,8 @@ SIGNATURES = {
                                    c_void_p]),
     "selr_svt_noalloc_status": (c_int32, [c_void_p]),
     "selr_adjoint": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "selr_spirit_calibrate": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "selr_spirit_kernel": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "selr_dc": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "selr_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                              ctypes.POINTER(c_int32), ctypes.POINTER(c_float), c_void_p]),

@@ -40,13 +40,19 @@ class Desc:
     exec: str = "batched"
     svd: str = "eig"
     gram: str = "fp32"
+    lam1: float = 1.0e3
+    spirit_k: int = 5
+    spirit_acs: int = 24
+    spirit_reg: float = 1.0e-3
+    cg_iters: int = 30
     fp64_fallback: int = 1
 
     @classmethod
     def from_workload(cls, w, **over):
         kw = dict(model=w.model, J=w.J, M=w.M, N=w.N, L=w.L, window=w.window, window_param=w.window_param,
                   weight=w.weight, lam=w.lam, lam2=w.lam2, beta=w.beta, tau=w.tau, d_init=w.d_init,
-                  max_iter=w.n_iter)
+                  max_iter=w.n_iter, lam1=w.lam1, spirit_k=w.spirit_k, spirit_acs=w.n_acs,
+                  spirit_reg=w.spirit_reg, cg_iters=w.cg_iters)
         kw.update(over)
         return cls(**kw)
 
@@ -61,6 +67,8 @@ class Desc:
         d.exec_ = EXEC[self.exec]
         d.svd_method = SVD[self.svd]
         d.gram_precision = GRAM[self.gram]
+        d.lambda1, d.spirit_ksize, d.spirit_acs = self.lam1, self.spirit_k, self.spirit_acs
+        d.spirit_reg, d.cg_iters = self.spirit_reg, self.cg_iters
         d.fp64_fallback = int(self.fp64_fallback)
         return d
 
@@ -322,7 +330,7 @@ def selr_solve(plan: Plan, Y, mask, X_out, state=None, resume=False, stream=None
 def selr_plan_rank_sums(plan: Plan, stream=None):
     """(per-matrix rank sums over the last solve as a numpy int64 array, iterations)."""
     import numpy as np
-    fams = ("row", "col") if plan.desc.model in ("SHLR", "SHLR_V") else ("pe", "param")
+    fams = ("row", "col") if plan.desc.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV") else ("pe", "param")
     n = sum(plan.lift_shape(a)[0] for a in fams) if not isinstance(plan, BatchPlan) else None
     if n is None:
         raise ValueError("rank sums of a batch plan: use the instance plans")
@@ -451,3 +459,18 @@ def selr_t2_fit(S, te_ms, t2_min=1.0, t2_max=1000.0, stream=None):
                           _ptr(T2, torch.float32, "T2"), _ptr(M0, torch.float32, "M0"), _stream(stream)),
           "selr_t2_fit")
     return T2, M0
+
+
+def selr_spirit_calibrate(plan: Plan, Y, stream=None):
+    """Calibrate the plan's SPIRiT kernel from the ACS rows of Y [J][M][N] (SHLR-S / SHLR-SV plans)."""
+    check(plan.lib.selr_spirit_calibrate(plan.handle, _ptr(Y, torch.complex64, "Y", plan.nK), _stream(stream)),
+          "selr_spirit_calibrate")
+
+
+def selr_spirit_kernel(plan: Plan, stream=None):
+    """The calibrated SPIRiT kernel [J][J][ks][ks] complex64."""
+    d = plan.desc
+    g = torch.empty((d.J, d.J, d.spirit_k, d.spirit_k), dtype=torch.complex64, device="cuda")
+    check(plan.lib.selr_spirit_kernel(plan.handle, _ptr(g, torch.complex64, "g"), _stream(stream)),
+          "selr_spirit_kernel")
+    return g

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libselr.so")
 SOURCES = ["fft.cu", "lift.cu", "svt.cu", "svt_eig.cu", "svt_small.cu", "gram_tc.cu", "dc.cu", "grad.cu",
-           "selr.cu", "svt_noalloc.cu", "probe.cu", "svt_fp64.cu", "metrics.cu"]
+           "selr.cu", "svt_noalloc.cu", "probe.cu", "svt_fp64.cu", "metrics.cu", "spirit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(HERE, "..", "include")]

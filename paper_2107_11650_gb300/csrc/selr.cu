@@ -37,6 +37,12 @@ struct selr_plan {
     cf *Gp, *V;              // packed Gram matrices / Householder vectors; eigenvectors
     float *lam, *tri;
     int *rank;
+    int spirit;                          // SHLR-S / SHLR-SV: SPIRiT term and CG X-update
+    int spirit_ready;                    // the kernel has been calibrated (host flag)
+    cf *sp_Gm, *sp_g, *sp_vec;           // image-domain G - I, kernel, six CG vectors
+    float *sp_cj;
+    double *sp_part;
+    double2 *sp_C, *sp_work;
     unsigned *gready, *ready, *vready;   // kernel hand-off flags, one per matrix (see EigArgs)
     unsigned long long *rank_acc;        // per-matrix sum of eigensolver ranks over the last solve
     void *f64work;                       // FP64 re-solve slots (SELR_FP64_SLOTS x f64slot double2)
@@ -121,6 +127,11 @@ extern "C" void selr_desc_default(selr_desc *d) {
     d->svd_method = SELR_SVD_EIG;
     d->gram_precision = SELR_GRAM_FP32;
     d->fp64_fallback = 1;
+    d->lambda1 = 1.0e3f;
+    d->spirit_ksize = 5;
+    d->spirit_acs = 24;
+    d->spirit_reg = 1.0e-3f;
+    d->cg_iters = 30;
 }
 
 extern "C" const char *selr_status_string(selr_status s) {
@@ -181,7 +192,7 @@ static void finish_set(GroupSet *gs) {
 
 static selr_status validate(const selr_desc *d) {
     if (!d) return SELR_ERR_INVALID_ARG;
-    if (d->model < SELR_SHLR || d->model > SELR_SHLR_VP) return SELR_ERR_INVALID_ARG;
+    if (d->model < SELR_SHLR || d->model > SELR_SHLR_SV) return SELR_ERR_INVALID_ARG;
     if (d->J < 1 || d->M < 1 || d->N < 1 || d->L < 1 || d->window < 1) return SELR_ERR_INVALID_ARG;
     if (!(d->beta > 0.f) || !(d->tau > 0.f) || d->max_iter < 1 || d->jacobi_max_sweeps < 1 ||
         !(d->jacobi_tol > 0.f) || !isfinite(d->lambda) || !isfinite(d->beta) || !isfinite(d->tau) ||
@@ -195,7 +206,15 @@ static selr_status validate(const selr_desc *d) {
         d->gram_precision != SELR_GRAM_3XTF32 && d->gram_precision != SELR_GRAM_BF16X3 &&
         d->gram_precision != SELR_GRAM_BF16X6)
         return SELR_ERR_INVALID_ARG;
-    const bool two_d = d->model <= SELR_SHLR_V;
+    const bool two_d = d->model <= SELR_SHLR_V || d->model >= SELR_SHLR_S;
+    if (d->model >= SELR_SHLR_S) {
+        if (!(d->lambda > 0.f) || !(d->lambda1 >= 0.f) || !isfinite(d->lambda1) || !(d->spirit_reg > 0.f) ||
+            d->cg_iters < 1 || d->cg_iters > 200)
+            return SELR_ERR_INVALID_ARG;
+        if ((d->spirit_ksize != 3 && d->spirit_ksize != 5 && d->spirit_ksize != 7) || d->J > 32)
+            return SELR_ERR_INVALID_ARG;
+        if (d->spirit_acs < d->spirit_ksize || d->spirit_acs > d->M || d->spirit_ksize > d->N) return SELR_ERR_SHAPE;
+    }
     if (two_d) {
         if (d->L != 1) return SELR_ERR_SHAPE;
         if (!smooth_even(d->M) || !smooth_even(d->N) || d->M > 1024 || d->N > 1024) return SELR_ERR_SHAPE;
@@ -272,7 +291,8 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
-                    p->rank, p->gready, p->ready, p->vready, p->rank_acc, p->f64work, p->sigma,
+                    p->rank, p->gready, p->ready, p->vready, p->rank_acc, p->f64work, p->sp_Gm, p->sp_g,
+                    p->sp_vec, p->sp_cj, p->sp_part, p->sp_C, p->sp_work, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -315,6 +335,7 @@ static selr_status check_batch(const selr_desc *ds, int n) {
     if (n == 1) return SELR_OK;
     for (int i = 0; i < n; ++i) {
         const selr_desc &a = ds[0], &b = ds[i];
+        if (b.model >= SELR_SHLR_S) return SELR_ERR_UNSUPPORTED;    // SPIRiT plans hold one instance
         if (b.model != a.model || b.weight != a.weight || b.beta != a.beta || b.tau != a.tau ||
             b.d_init != a.d_init || b.max_iter != a.max_iter || b.tol != a.tol || b.exec != a.exec ||
             b.svd_method != a.svd_method || b.gram_precision != a.gram_precision ||
@@ -337,8 +358,9 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
     const selr_desc *d = &ds[0];
     p->d = *d;
     p->n_inst = n_inst;
-    p->model2d = d->model <= SELR_SHLR_V;
-    p->vc = d->model == SELR_SHLR_V || d->model == SELR_SHLR_VP;
+    p->model2d = d->model <= SELR_SHLR_V || d->model >= SELR_SHLR_S;
+    p->vc = d->model == SELR_SHLR_V || d->model == SELR_SHLR_VP || d->model == SELR_SHLR_SV;
+    p->spirit = d->model >= SELR_SHLR_S;
     p->L = d->L; p->J = d->J; p->M = d->M; p->N = d->N;
     const float t1 = 1.0f / d->beta;
     GroupSet &gs = p->gs;
@@ -438,6 +460,16 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
     AL(p->active, sizeof(int) * (size_t)p->Mact);
     AL(p->active_next, sizeof(int) * (size_t)p->Mact);
     AL(p->status, sizeof(unsigned));
+    if (p->spirit) {
+        const long long J = d->J, ks = d->spirit_ksize, nu = J * ks * ks, ns = nu - 1;
+        AL(p->sp_Gm, sizeof(cf) * (size_t)(J * J * d->M * d->N));
+        AL(p->sp_g, sizeof(cf) * (size_t)(J * J * ks * ks));
+        AL(p->sp_vec, 6 * sizeof(cf) * (size_t)p->nK);
+        AL(p->sp_cj, sizeof(float) * (size_t)J);
+        AL(p->sp_part, 3 * sizeof(double) * SP_NB);
+        AL(p->sp_C, sizeof(double2) * (size_t)(nu * nu));
+        AL(p->sp_work, sizeof(double2) * (size_t)(SELR_SPIRIT_SLOTS * (ns * ns + ns)));
+    }
     for (int i = 0; i < n_inst; ++i) {
         Inst &I = p->inst[i];
         AL(I.wN, sizeof(cf) * I.N);
@@ -714,8 +746,28 @@ extern "C" selr_status selr_svt(selr_plan *p, void *A, int32_t nmat, int32_t row
     return SELR_OK;
 }
 
-// FFTs of the adjoints to k-space, the pointwise solve and the reduction, per
-// instance (arrays are the packed ones; each instance works on its slices).
+// Arguments of the SPIRiT kernels of a single-instance SHLR-S / SHLR-SV plan.
+static SpiritArgs spirit_args(selr_plan *p, const cf *Y, const uint8_t *mask, const cf *adj_a, const cf *adj_b,
+                              cf *K) {
+    SpiritArgs s;
+    memset(&s, 0, sizeof(s));
+    const Inst &I = p->inst[0];
+    s.J = I.J; s.M = I.M; s.N = I.N;
+    s.ks = p->d.spirit_ksize; s.acs = p->d.spirit_acs; s.cg_iters = p->d.cg_iters;
+    s.nK = I.nK;
+    s.lambda = I.lambda; s.beta = p->d.beta; s.lambda1 = p->d.lambda1; s.reg = p->d.spirit_reg;
+    s.da = I.da; s.db = I.db; s.mask = mask; s.Y = Y; s.K = K; s.adjA = adj_a; s.adjB = adj_b;
+    s.Gm = p->sp_Gm; s.g = p->sp_g; s.cj = p->sp_cj;
+    s.x = p->sp_vec; s.r = s.x + I.nK; s.z = s.r + I.nK; s.p = s.z + I.nK; s.q = s.p + I.nK; s.t = s.q + I.nK;
+    s.part = p->sp_part; s.partial = p->partial + I.poff; s.status = p->status;
+    s.cal_C = p->sp_C; s.cal_work = p->sp_work;
+    s.ftM = I.ftM; s.ftN = I.ftN;
+    return s;
+}
+
+// FFTs of the adjoints to k-space, the pointwise solve (or, with the SPIRiT
+// term, the CG solve) and the reduction, per instance (arrays are the packed
+// ones; each instance works on its slices).
 static cudaError_t dc_step(selr_plan *p, const cf *Y, const uint8_t *mask, cf *adj_a, cf *adj_b, cf *K,
                            const int *active, int *active_next, cudaStream_t st) {
     cudaError_t e;
@@ -739,7 +791,9 @@ static cudaError_t dc_step(selr_plan *p, const cf *Y, const uint8_t *mask, cf *a
         a.partial = p->partial + I.poff;
         a.active = active ? active + I.aoff : nullptr;
         a.status = p->status;
-        if ((e = launch_dc(a, st)) != cudaSuccess) return e;
+        if (p->spirit) e = launch_spirit_x_update(spirit_args(p, Y, mask, aa, ab, K), st);
+        else e = launch_dc(a, st);
+        if (e != cudaSuccess) return e;
         if ((e = launch_rel_finalize(p->partial + I.poff, I.M, !p->model2d, p->d.tol, p->rel + I.roff,
                                      active_next ? active_next + I.aoff : nullptr, st)) != cudaSuccess)
             return e;
@@ -747,10 +801,28 @@ static cudaError_t dc_step(selr_plan *p, const cf *Y, const uint8_t *mask, cf *a
     return cudaSuccess;
 }
 
+extern "C" selr_status selr_spirit_calibrate(selr_plan *p, const void *Y, selr_stream stream) {
+    if (!p || !Y) return SELR_ERR_INVALID_ARG;
+    if (!p->spirit) return SELR_ERR_UNSUPPORTED;
+    CK(launch_spirit_calibrate(spirit_args(p, (const cf *)Y, nullptr, nullptr, nullptr, nullptr), (const cf *)Y,
+                               (cudaStream_t)stream));
+    p->spirit_ready = 1;
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_spirit_kernel(selr_plan *p, void *g_out, selr_stream stream) {
+    if (!p || !g_out) return SELR_ERR_INVALID_ARG;
+    if (!p->spirit || !p->spirit_ready) return SELR_ERR_UNSUPPORTED;
+    const size_t bytes = sizeof(cf) * (size_t)p->d.J * p->d.J * p->d.spirit_ksize * p->d.spirit_ksize;
+    CK(cudaMemcpyAsync(g_out, p->sp_g, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SELR_OK;
+}
+
 extern "C" selr_status selr_dc(selr_plan *p, const void *Y, const uint8_t *mask, void *adj_a, void *adj_b,
                                void *K, float *rel_out, selr_stream stream) {
     if (!p || !Y || !mask || !adj_a || !adj_b || !K) return SELR_ERR_INVALID_ARG;
     if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
+    if (p->spirit && !p->spirit_ready) return SELR_ERR_UNSUPPORTED;    // selr_spirit_calibrate first
     cudaStream_t st = (cudaStream_t)stream;
     CK(dc_step(p, (const cf *)Y, mask, (cf *)adj_a, (cf *)adj_b, (cf *)K, nullptr, nullptr, st));
     if (rel_out) CK(cudaMemcpyAsync(rel_out, p->rel, sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -930,6 +1002,10 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
         return SELR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const cf *Y = (const cf *)Yv;
+    if (p->spirit) {       // SPIRiT kernel from this data's ACS rows (before the iteration graph)
+        CK(launch_spirit_calibrate(spirit_args(p, Y, mask, nullptr, nullptr, nullptr), Y, st));
+        p->spirit_ready = 1;
+    }
     if (resume) CK(state_copy(p, (unsigned char *)state_inout, 0, st));
     else CK(admm_init(p, Y, st));
     if (p->rank_acc) CK(cudaMemsetAsync(p->rank_acc, 0, sizeof(unsigned long long) * (size_t)p->gs.total, st));
@@ -1171,7 +1247,7 @@ extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zba
 extern "C" selr_status selr_dc_vjp(selr_plan *p, const uint8_t *mask, const void *Kbar, void *adj_out, void *Ybar,
                                    selr_stream stream) {
     if (!p || !mask || !Kbar || !adj_out) return SELR_ERR_INVALID_ARG;
-    if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
+    if (p->n_inst != 1 || p->spirit) return SELR_ERR_UNSUPPORTED;
     DcArgs a;
     memset(&a, 0, sizeof(a));
     a.model2d = p->model2d;

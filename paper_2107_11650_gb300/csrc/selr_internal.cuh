@@ -345,5 +345,30 @@ cudaError_t launch_dc_vjp(const DcArgs &a, const cf *Kbar, cf *out, cf *ybar, cu
 cudaError_t launch_rel_finalize(const double *partial, int M, int per_m, float tol, float *rel,
                                 int *active_next, cudaStream_t st);
 cudaError_t launch_fill(cf *p, long long n, cf v, cudaStream_t st);
+
+// spirit.cu: SPIRiT calibration and the CG X-update of SHLR-S / SHLR-SV
+#define SP_NB 304                 // CTAs of the CG kernels (fixed: deterministic partial sums)
+#define SELR_SPIRIT_SLOTS 4       // coil systems solved concurrently in the calibration
+struct SpiritArgs {
+    int J, M, N, ks, acs, cg_iters;
+    long long nK;
+    float lambda, beta, lambda1, reg;
+    const float *da, *db;         // lift normal diagonals d_r(k_n), d_c(k_m)
+    const uint8_t *mask;          // [M][N]
+    const cf *Y;                  // [J][M][N] data
+    cf *K;                        // iterate, overwritten by the X-update
+    const cf *adjA, *adjB;        // transformed lift adjoints (k-space)
+    cf *Gm;                       // [J][J][M][N] image-domain G - I
+    cf *g;                        // [J][J][ks][ks] kernel
+    float *cj;                    // [J] preconditioner constants
+    cf *x, *r, *z, *p, *q, *t;    // CG vectors [J][M][N]
+    double *part;                 // [3][SP_NB]
+    double *partial;              // [M][2] stopping-ratio partials
+    unsigned *status;
+    double2 *cal_C, *cal_work;    // calibration: C = A^H A, SELR_SPIRIT_SLOTS Cholesky slots
+    FftTable ftM, ftN;
+};
+cudaError_t launch_spirit_calibrate(const SpiritArgs &s, const cf *Y, cudaStream_t st);
+cudaError_t launch_spirit_x_update(const SpiritArgs &s, cudaStream_t st);
 cudaError_t launch_fill_i(int *p, long long n, int v, cudaStream_t st);
 cudaError_t launch_copy_active(const int *src, int *dst, int n, cudaStream_t st);

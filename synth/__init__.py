@@ -279,7 +279,7 @@ def make_inputs(cfg, small=None):
     if small is not None:
         J, M, N = small
     rng_mask = np.random.default_rng(cfg.seed + 101)
-    if cfg.model in ("SHLR", "SHLR_V"):
+    if cfg.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV"):
         x = multicoil_image(J, M, N, cfg.seed)
         if cfg.mask == "gauss1d":
             mask = mask_1d_gaussian(M, N, cfg.R, cfg.n_acs, rng_mask)

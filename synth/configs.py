@@ -30,6 +30,10 @@ class Workload:
     n_iter: int = 30
     lam: float = 1.0e4    # data-term weight lambda (<= 0 : hard data consistency)
     lam2: float = 2.0     # parameter-dimension weight lambda_2
+    lam1: float = 1000.0  # SPIRiT weight lambda_1 (SHLR-S / SHLR-SV)
+    spirit_k: int = 5     # SPIRiT kernel size
+    spirit_reg: float = 1e-3   # SPIRiT calibration Tikhonov weight (relative)
+    cg_iters: int = 30    # CG iterations of the SHLR-S / SHLR-SV X-update on the GPU
     beta: float = 1.0
     tau: float = 1.0
     d_init: float = 1.0

@@ -28,7 +28,7 @@ def make(name, n_iter):
     wl = synth.unrolled_instance(name) if name.startswith("unrolled_") else synth.get_config(name)
     inp = synth.make_inputs(wl)
     t0 = time.time()
-    if wl.model in ("SHLR", "SHLR_V"):
+    if wl.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV"):
         X, K, rels = admm.shlr(inp["Y"], inp["mask"], wl, n_iter=n_iter)
     else:
         X, K, iters = admm.shlr_p(inp["Y"], inp["mask"], wl, n_iter=n_iter)

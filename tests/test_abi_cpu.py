@@ -54,6 +54,8 @@ def _desc(lib, **kw):
     (dict(weight=3), 1), (dict(exec_=5), 1), (dict(jacobi_tol=0.0), 1), (dict(lambda2=-1.0), 1),
     (dict(svd_method=2), 1), (dict(gram_precision=2), 1), (dict(gram_precision=-1), 1),
     (dict(fp64_fallback=2), 1), (dict(gram_precision=5), 1),
+    (dict(model=6), 1), (dict(model=4, lambda_=0.0), 1), (dict(model=4, spirit_ksize=4), 1),
+    (dict(model=5, cg_iters=0), 1), (dict(model=4, spirit_acs=2), 2), (dict(model=4, J=33), 1),
     (dict(M=63), 2), (dict(N=14 * 7), 2), (dict(window=65), 2), (dict(L=2), 2),
     (dict(model=3, L=8, window_param=9, N=64), 2), (dict(model=2, L=8, window_param=4, N=66 * 7), 2),
 ])
@@ -69,7 +71,8 @@ def test_descriptor_defaults(lib):
     assert (d.model, d.J, d.M, d.N, d.L, d.window) == (0, 4, 64, 64, 1, 8)
     assert (d.svd_method, d.gram_precision, d.exec_) == (0, 0, 0)
     assert d.fp64_fallback == 1
-    assert ctypes.sizeof(_lib.SelrDesc) == 21 * 4
+    assert (d.spirit_ksize, d.spirit_acs, d.cg_iters) == (5, 24, 30) and abs(d.lambda1 - 1e3) < 1e-3
+    assert ctypes.sizeof(_lib.SelrDesc) == 26 * 4
 
 
 def test_batch_descriptor_validation(lib):
@@ -116,6 +119,8 @@ def test_null_arguments(lib):
     # evaluation entry points
     assert lib.selr_ssos(None, 1, 1, 1, None, None) == 1
     assert lib.selr_rlne(None, None, 1, None, None) == 1
+    assert lib.selr_spirit_calibrate(None, None, None) == 1
+    assert lib.selr_spirit_kernel(None, None, None) == 1
     assert lib.selr_mssim(None, None, 16, 16, 1.0, None, None, None) == 1
     assert lib.selr_max(None, 1, None, None) == 1
     te = (ctypes.c_float * 1)(1.0)
