@@ -39,6 +39,7 @@
 #include "selr_internal.cuh"
 
 #include <float.h>
+#include <type_traits>
 
 #define EIG_THREADS 512
 #define EIG_WARPS (EIG_THREADS / 32)
@@ -417,6 +418,12 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
         cf pa[RPL];
 #pragma unroll
         for (int t = 0; t < RPL; ++t) pa[t] = mk(0.f, 0.f);
+        // The sweep is instantiated twice (with and without the deferred update, which only
+        // the first step lacks) so that the column loop carries no update branch, and every
+        // complex multiply-add is an explicit FMA chain (a - b c - d e ... does not contract
+        // into FMAs): 16 FMAs per element and step (1.43 -> 1.36 M cycles per matrix, s = 192).
+        auto sweep = [&](auto UPDC) {
+        constexpr bool UPD = decltype(UPDC)::value;
         // TB columns per pass (j, j + 16, ...): their 2 TB column sums are reduced together
         // by a transpose-reduce butterfly (9 shuffles instead of 10 TB)
         for (int j0 = k + 1 + warp; j0 < n; j0 += TB * EIG_WARPS) {
@@ -434,16 +441,26 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                             const int i = lane + 32 * t;
                             if (i >= j && (FULL || i < n)) {
                                 cf gv = colj[i];
-                                if (upd) {
-                                    gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
-                                    gv.y -= vo[t].y * woj.x - vo[t].x * woj.y + wo[t].y * voj.x - wo[t].x * voj.y;
+                                if (UPD) {
+                                    gv.x = fmaf(-vo[t].x, woj.x, gv.x);
+                                    gv.x = fmaf(-vo[t].y, woj.y, gv.x);
+                                    gv.x = fmaf(-wo[t].x, voj.x, gv.x);
+                                    gv.x = fmaf(-wo[t].y, voj.y, gv.x);
+                                    gv.y = fmaf(-vo[t].y, woj.x, gv.y);
+                                    gv.y = fmaf(vo[t].x, woj.y, gv.y);
+                                    gv.y = fmaf(-wo[t].y, voj.x, gv.y);
+                                    gv.y = fmaf(wo[t].x, voj.y, gv.y);
                                     colj[i] = gv;
                                 }
-                                pa[t].x += gv.x * vnj.x - gv.y * vnj.y;
-                                pa[t].y += gv.x * vnj.y + gv.y * vnj.x;
+                                pa[t].x = fmaf(gv.x, vnj.x, pa[t].x);
+                                pa[t].x = fmaf(-gv.y, vnj.y, pa[t].x);
+                                pa[t].y = fmaf(gv.x, vnj.y, pa[t].y);
+                                pa[t].y = fmaf(gv.y, vnj.x, pa[t].y);
                                 if (i > j) {                       // conj(G(i,j)) v_i -> p_j
-                                    cr += gv.x * vn[t].x + gv.y * vn[t].y;
-                                    ci += gv.x * vn[t].y - gv.y * vn[t].x;
+                                    cr = fmaf(gv.x, vn[t].x, cr);
+                                    cr = fmaf(gv.y, vn[t].y, cr);
+                                    ci = fmaf(gv.x, vn[t].y, ci);
+                                    ci = fmaf(-gv.y, vn[t].x, ci);
                                 }
                             }
                         }
@@ -483,6 +500,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                 if (j < n) ((float *)Cs)[2 * j + (v & 1)] = s1;
             }
         }
+        };
+        if (upd) sweep(std::integral_constant<bool, true>());
+        else sweep(std::integral_constant<bool, false>());
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
