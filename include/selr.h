@@ -203,7 +203,17 @@ selr_status selr_lift(selr_plan *plan, int32_t axis, const void *x, const void *
 
 /* Singular value thresholding S_t (Eqs. 16-17, S8-S9) of nmat complex64
  * matrices [nmat][rows][cols], in place: A <- U diag(max(sigma - t, 0)) V^H.
- * Computed by one-sided Jacobi on the shorter dimension in FP32.
+ * Computed as the plan's svd_method says: SELR_SVD_EIG (default) forms
+ * G = B^H B (B the matrix with its shorter side as columns) in the plan's Gram
+ * precision, finds the eigenpairs of G above t^2 by Householder
+ * tridiagonalisation, multisection and inverse iteration in FP32 (matrices that
+ * FP32 cannot resolve at the threshold are re-solved in FP64, see
+ * selr_desc.fp64_fallback), and writes sum (1 - t / sigma_i) (B v_i) v_i^H;
+ * SELR_SVD_JACOBI runs one-sided Jacobi on B in FP32.
+ * thresh: one t for all nmat matrices.  The paper's thresholds are per lift
+ * family (1/beta for row / column / PE lifts, lambda2/beta for the
+ * parameter-dimension lifts, Eqs. 16-17 and S8-S9), so a scalar per call is
+ * the reading; matrices with different thresholds take separate calls.
  * rank_out: device int32[nmat] receiving #{sigma > t}, or NULL.
  * Requires nmat*rows*cols within the plan's workspace capacity
  * (SELR_ERR_SHAPE otherwise) and t >= 0. */
