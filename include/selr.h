@@ -320,6 +320,34 @@ selr_status selr_solve(selr_plan *plan, const void *Y, const uint8_t *mask, void
                        void *state_inout, int32_t resume, int32_t *iters_out, float *rel_out,
                        selr_stream stream);
 
+/* Forward pass of an unrolled reconstruction (differentiation through
+ * Algorithm S1; the paper fixes t and tau): n_iter iterations on the plan's
+ * instances (2D models without the SPIRiT term; any number of instances),
+ * iteration k with SVT threshold ts[k] (Eqs. 16-17) and multiplier step taus[k]
+ * (Eqs. 13-14) instead of 1/beta and tau.  ts, taus: HOST float [n_iter]
+ * (ts[k] >= 0).  X_out: the image of the last X-update ([L][J][M][N], packed as
+ * for selr_solve).  ckpt_K (device, may be NULL): [n_iter][nK] complex64, the
+ * k-space iterate after the X-update of each iteration; ckpt_D (device, may be
+ * NULL): [n_iter][selr_lifted_elems] complex64, the multipliers entering that
+ * iteration's Z / D steps, in the plan's internal layout (selr_lifted_unpack).
+ * On a non-default stream in batched execution the whole pass is one CUDA
+ * graph, captured on every call (the parameters change) and updated in place
+ * of the previous call's executable graph.  Errors: SELR_ERR_INVALID_ARG,
+ * SELR_ERR_UNSUPPORTED (parameter or SPIRiT models), SELR_ERR_CUDA. */
+selr_status selr_solve_unrolled(selr_plan *plan, const void *Y, const uint8_t *mask, void *X_out, const float *ts,
+                                const float *taus, int32_t n_iter, void *ckpt_K, void *ckpt_D, selr_stream stream);
+
+/* Number of complex64 elements of all lifted matrices of the plan (one
+ * multiplier array; host output). */
+selr_status selr_lifted_elems(const selr_plan *plan, int64_t *elems);
+
+/* The lifted matrices of family `axis` (selr_axis) of instance `inst` out of a
+ * multiplier array in the plan's internal layout (packed: selr_lifted_elems
+ * elements, e.g. one checkpoint of selr_solve_unrolled), written to `out` as
+ * [nmat][rows][cols] complex64 (device). */
+selr_status selr_lifted_unpack(const selr_plan *plan, const void *packed, int32_t inst, int32_t axis, void *out,
+                               selr_stream stream);
+
 /* Bytes of a solver state buffer for selr_solve's state_inout (host output). */
 selr_status selr_state_bytes(const selr_plan *plan, size_t *bytes);
 

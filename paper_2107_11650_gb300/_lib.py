@@ -57,6 +57,10 @@ SIGNATURES = {
     "selr_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                              ctypes.POINTER(c_int32), ctypes.POINTER(c_float), c_void_p]),
     "selr_state_bytes": (c_int32, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "selr_solve_unrolled": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_float),
+                                      ctypes.POINTER(c_float), c_int32, c_void_p, c_void_p, c_void_p]),
+    "selr_lifted_elems": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "selr_lifted_unpack": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     "selr_plan_rank_sums": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_int64), c_int32, ctypes.POINTER(c_int32),
                                       c_void_p]),
     "selr_probe_fp32_peak": (c_int32, [c_int32, c_int32, ctypes.POINTER(c_float), ctypes.POINTER(c_float)]),

@@ -474,3 +474,32 @@ def selr_spirit_kernel(plan: Plan, stream=None):
     check(plan.lib.selr_spirit_kernel(plan.handle, _ptr(g, torch.complex64, "g"), _stream(stream)),
           "selr_spirit_kernel")
     return g
+
+
+# ------------------------------------------------------- unrolled forward
+def selr_lifted_elems(plan: Plan) -> int:
+    n = ctypes.c_int64()
+    check(plan.lib.selr_lifted_elems(plan.handle, ctypes.byref(n)), "selr_lifted_elems")
+    return int(n.value)
+
+
+def selr_solve_unrolled(plan: Plan, Y, mask, X_out, ts, taus, ckpt_K=None, ckpt_D=None, stream=None):
+    """Unrolled forward with per-iteration thresholds ts and steps taus (host sequences)."""
+    n = len(ts)
+    if len(taus) != n:
+        raise ValueError("ts and taus must have the same length")
+    nm = plan.n_mask if isinstance(plan, BatchPlan) else plan.desc.L * plan.desc.M * plan.desc.N
+    tsa = (ctypes.c_float * n)(*[float(t) for t in ts])
+    taa = (ctypes.c_float * n)(*[float(t) for t in taus])
+    le = selr_lifted_elems(plan)
+    check(plan.lib.selr_solve_unrolled(plan.handle, _ptr(Y, torch.complex64, "Y", plan.nK),
+                                       _ptr(mask, torch.uint8, "mask", nm), _ptr(X_out, torch.complex64, "X", plan.nK),
+                                       tsa, taa, n, _ptr(ckpt_K, torch.complex64, "ckpt_K", n * plan.nK, True),
+                                       _ptr(ckpt_D, torch.complex64, "ckpt_D", n * le, True), _stream(stream)),
+          "selr_solve_unrolled")
+
+
+def selr_lifted_unpack(plan: Plan, packed, inst: int, axis: str, out, stream=None):
+    """Family `axis` of instance `inst` out of a packed multiplier array into out [nmat][rows][cols]."""
+    check(plan.lib.selr_lifted_unpack(plan.handle, _ptr(packed, torch.complex64, "packed"), int(inst), AXES[axis],
+                                      _ptr(out, torch.complex64, "out"), _stream(stream)), "selr_lifted_unpack")

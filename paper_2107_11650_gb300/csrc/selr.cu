@@ -65,6 +65,11 @@ struct selr_plan {
     const uint8_t *graph_mask;
     cudaStream_t graph_stream;
     int graph_iters;          // 1: `graph` holds one iteration; 0: per-stage graphs (profiling)
+    cudaGraphExec_t ugraph;   // the last unrolled forward (selr_solve_unrolled), updated in place
+    cudaStream_t ugraph_stream;
+    int ovr_on;               // per-iteration threshold / step override (unrolled forward)
+    float ovr_tau;
+    GroupSet ovr_gs;          // gs with the overriding threshold
     // stage profiling
     int prof_on;
     int prof_cap;             // iterations with events allocated
@@ -846,6 +851,8 @@ static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_
     a.D = p->D;
     a.E = p->E;
     a.active = act;
+    if (p->ovr_on) a.tau = p->ovr_tau;
+    const GroupSet &G = p->ovr_on ? p->ovr_gs : p->gs;    // thresholds of this iteration
     const float ib = 1.0f / p->d.beta;
     cf *lift_out = jac ? p->W : p->B0;
     cf *lift_out2 = jac ? p->B0 : nullptr;
@@ -870,19 +877,19 @@ static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_
                 for (int m = 0; m < total; ++m) {
                     if ((e = launch_lift(p->gs, 0, m, 1, p->D, 0, ib, lift_out, lift_out2, 0, act, st)) != cudaSuccess)
                         return e;
-                    if ((e = svd_apply(p, p->gs, m, 1, a, 7, st)) != cudaSuccess) return e;
+                    if ((e = svd_apply(p, G, m, 1, a, 7, st)) != cudaSuccess) return e;
                 }
                 if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->Mact, st);
                 return cudaSuccess;
             }
             return launch_lift(p->gs, 0, 0, total, p->D, 0, ib, lift_out, lift_out2, 0, act, st);
         case 4:
-            return plain ? cudaSuccess : svd_apply(p, p->gs, 0, total, a, 1, st);
+            return plain ? cudaSuccess : svd_apply(p, G, 0, total, a, 1, st);
         case 5:
-            return plain ? cudaSuccess : svd_apply(p, p->gs, 0, total, a, 2, st);
+            return plain ? cudaSuccess : svd_apply(p, G, 0, total, a, 2, st);
         default:
             if (plain) return cudaSuccess;
-            if ((e = svd_apply(p, p->gs, 0, total, a, 4, st)) != cudaSuccess) return e;
+            if ((e = svd_apply(p, G, 0, total, a, 4, st)) != cudaSuccess) return e;
             if (!p->model2d) return launch_copy_active(p->active_next, p->active, p->Mact, st);
             return cudaSuccess;
     }
@@ -917,6 +924,7 @@ static cudaError_t prof_reserve(selr_plan *p, int iters) {
 
 static void drop_graphs(selr_plan *p) {
     if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+    if (p->ugraph) { cudaGraphExecDestroy(p->ugraph); p->ugraph = nullptr; }
     for (int s = 0; s < 8; ++s)
         if (p->stage_graph[s]) { cudaGraphExecDestroy(p->stage_graph[s]); p->stage_graph[s] = nullptr; }
 }
@@ -1088,6 +1096,107 @@ extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *m
 }
 
 extern "C" const char *selr_last_error_string(void) { return cudaGetErrorString(g_last_error); }
+
+// ------------------------------------------------------ unrolled forward
+// n iterations of Algorithm S1 with threshold ts[k] and step taus[k] in iteration k;
+// checkpoint k = (K after the X-update of iteration k, D entering its Z / D steps).
+static cudaError_t unrolled_forward(selr_plan *p, const cf *Y, const uint8_t *mask, const float *ts,
+                                    const float *taus, int n, cf *ckK, cf *ckD, cf *X, cudaStream_t st) {
+    cudaError_t e = admm_init(p, Y, st);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        p->ovr_on = 0;
+        if ((e = admm_stage(p, 0, Y, mask, st)) != cudaSuccess) break;
+        if ((e = admm_stage(p, 1, Y, mask, st)) != cudaSuccess) break;
+        if (ckK && (e = cudaMemcpyAsync(ckK + (long long)k * p->nK, p->K, sizeof(cf) * p->nK, cudaMemcpyDeviceToDevice,
+                                        st)) != cudaSuccess)
+            break;
+        if (ckD && (e = cudaMemcpyAsync(ckD + (long long)k * p->lift_elems, p->D, sizeof(cf) * p->lift_elems,
+                                        cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            break;
+        if (k == n - 1) break;
+        p->ovr_gs = p->gs;
+        for (int g = 0; g < p->ovr_gs.n; ++g) p->ovr_gs.g[g].thresh = ts[k];
+        p->ovr_tau = taus[k];
+        p->ovr_on = 1;
+        for (int s = 2; s < NSTAGE && e == cudaSuccess; ++s) e = admm_stage(p, s, Y, mask, st);
+    }
+    p->ovr_on = 0;
+    if (e != cudaSuccess) return e;
+    return output_image(p, X, st);
+}
+
+extern "C" selr_status selr_solve_unrolled(selr_plan *p, const void *Y, const uint8_t *mask, void *X_out,
+                                           const float *ts, const float *taus, int32_t n_iter, void *ckpt_K,
+                                           void *ckpt_D, selr_stream stream) {
+    if (!p || !Y || !mask || !X_out || !ts || !taus || n_iter < 1) return SELR_ERR_INVALID_ARG;
+    if (!p->model2d || p->spirit) return SELR_ERR_UNSUPPORTED;
+    for (int k = 0; k < n_iter; ++k)
+        if (!(ts[k] >= 0.f) || !isfinite(ts[k]) || !isfinite(taus[k])) return SELR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const cf *Yc = (const cf *)Y;
+    cf *ckK = (cf *)ckpt_K, *ckD = (cf *)ckpt_D, *X = (cf *)X_out;
+    if (st == 0 || p->d.exec != SELR_EXEC_BATCHED) {
+        CK(unrolled_forward(p, Yc, mask, ts, taus, n_iter, ckK, ckD, X, st));
+        return SELR_OK;
+    }
+    // the whole forward as one CUDA graph; the parameters change every call, so it is captured
+    // each time and the executable graph of the previous call updated in place when possible
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = unrolled_forward(p, Yc, mask, ts, taus, n_iter, ckK, ckD, X, st);
+    cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (e2 == cudaSuccess) cudaGraphDestroy(g);
+        g_last_error = e != cudaSuccess ? e : e2;
+        return SELR_ERR_CUDA;
+    }
+    bool updated = false;
+    if (p->ugraph && p->ugraph_stream == st) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(p->ugraph, g, &info) == cudaSuccess;
+        if (!updated) cudaGetLastError();
+    }
+    if (!updated) {
+        if (p->ugraph) { cudaGraphExecDestroy(p->ugraph); p->ugraph = nullptr; }
+        e = cudaGraphInstantiate(&p->ugraph, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            p->ugraph = nullptr;
+            g_last_error = e;
+            return SELR_ERR_CUDA;
+        }
+        p->ugraph_stream = st;
+    }
+    cudaGraphDestroy(g);
+    CK(cudaGraphLaunch(p->ugraph, st));
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_lifted_unpack(const selr_plan *p, const void *packed, int32_t inst, int32_t axis,
+                                          void *out, selr_stream stream) {
+    if (!p || !packed || !out || inst < 0 || inst >= p->n_inst) return SELR_ERR_INVALID_ARG;
+    const int kind = axis == SELR_AXIS_ROW ? G_ROW : axis == SELR_AXIS_COL ? G_COL : axis == SELR_AXIS_PE ? G_PE
+                   : axis == SELR_AXIS_PARAM ? G_PARAM : -1;
+    if (kind < 0) return SELR_ERR_INVALID_ARG;
+    for (int k = 0; k < p->gs.n; ++k) {
+        const Group &g = p->gs.g[k];
+        if (g.inst != inst || g.kind != kind) continue;
+        GroupSet s;
+        memset(&s, 0, sizeof(s));
+        s.n = 1;
+        s.g[0] = g;
+        finish_set(&s);
+        CK(launch_vm_to_natural(s, (const cf *)packed + g.off, (cf *)out, (cudaStream_t)stream));
+        return SELR_OK;
+    }
+    return SELR_ERR_INVALID_ARG;
+}
+
+extern "C" selr_status selr_lifted_elems(const selr_plan *p, int64_t *elems) {
+    if (!p || !elems) return SELR_ERR_INVALID_ARG;
+    *elems = p->lift_elems;
+    return SELR_OK;
+}
 
 extern "C" selr_status selr_plan_rank_sums(selr_plan *p, int64_t *out, int32_t n, int32_t *iterations,
                                            selr_stream stream) {

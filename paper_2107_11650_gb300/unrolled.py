@@ -225,10 +225,78 @@ class UnrolledSHLR(torch.nn.Module):
         return UnrolledFunction.apply(Y, self.ts, self.taus, self.engine)
 
 
+class _BatchCheckpoints:
+    """Checkpoints of one instance of a batched unrolled forward: (K_k, {axis: D_k}),
+    the multipliers unpacked from the batch plan's layout when an iteration is
+    reached in the reverse pass."""
+
+    def __init__(self, bplan, ckK, ckD, inst, engine):
+        self.bplan, self.ckK, self.ckD, self.inst, self.engine = bplan, ckK, ckD, inst, engine
+
+    def __len__(self):
+        return self.ckK.shape[0]
+
+    def __getitem__(self, k):
+        K = self.bplan.unpack(self.ckK[k], self.inst)
+        D = {}
+        for ax in ("row", "col"):
+            D[ax] = torch.empty(self.engine.lift[ax], dtype=_C64, device=self.engine.dev)
+            api.selr_lifted_unpack(self.bplan, self.ckD[k], self.inst, ax, D[ax])
+        return K, D
+
+
+class UnrolledBatchFunction(torch.autograd.Function):
+    """(X_1, ..., X_B) = unrolled reconstruction of B instances (shared t_k, tau_k)
+    in one batched plan; reverse pass per instance."""
+
+    @staticmethod
+    def forward(ctx, ts, taus, module, *Ys):
+        bp = module.bplan
+        n = module.n_iter
+        Yp = bp.pack([y.detach().to(_C64).contiguous() for y in Ys], _C64)
+        Xp = torch.empty_like(Yp)
+        ckK = torch.empty((n, bp.nK), dtype=_C64, device=Yp.device)
+        ckD = torch.empty((n, api.selr_lifted_elems(bp)), dtype=_C64, device=Yp.device)
+        tv = [float(x) for x in ts.detach().cpu().tolist()]
+        tauv = [float(x) for x in taus.detach().cpu().tolist()]
+        if min(tv) < 0.0:
+            raise ValueError("thresholds must be >= 0")
+        api.selr_solve_unrolled(bp, Yp, module.mask_p, Xp, tv, tauv, ckK, ckD, stream=module.stream)
+        torch.cuda.current_stream().wait_stream(module.stream)
+        ctx.module = module
+        ctx.ck = (ckK, ckD)
+        ctx.Ys = [y.detach().to(_C64).contiguous() for y in Ys]
+        ctx.save_for_backward(ts.detach(), taus.detach())
+        return tuple(bp.unpack(Xp, i).clone() for i in range(len(Ys)))
+
+    @staticmethod
+    def backward(ctx, *Xbars):
+        ts, taus = ctx.saved_tensors
+        m = ctx.module
+        ckK, ckD = ctx.ck
+        tbar = torch.zeros_like(ts)
+        taubar = torch.zeros_like(taus)
+        Ybars = []
+        for i, (e, Xb) in enumerate(zip(m.engines, Xbars)):
+            if Xb is None:
+                Ybars.append(None)
+                continue
+            ck = _BatchCheckpoints(m.bplan, ckK, ckD, i, e)
+            Yb, tb, taub = e.backward(ck, ctx.Ys[i], ts, taus, Xb)
+            tbar += tb.to(ts.dtype)
+            taubar += taub.to(taus.dtype)
+            Ybars.append(Yb)
+        ctx.ck = None
+        return (tbar, taubar, None, *Ybars)
+
+
 class UnrolledBatch(torch.nn.Module):
-    """A batch of unrolled reconstructions of uneven sizes sharing t_k and tau_k
-    (one engine and one plan per instance; the gradients of the shared
-    parameters are summed over the instances by autograd)."""
+    """A batch of unrolled reconstructions of uneven sizes sharing t_k and tau_k.
+
+    The forward runs every instance in one batched plan (selr_plan_create_batch:
+    the lifted matrices of all instances share the SVT launches) as one
+    CUDA graph (selr_solve_unrolled) and keeps (K_k, D_k) per iteration; the
+    reverse pass runs per instance on its own plan from those checkpoints."""
 
     def __init__(self, descs, masks, n_iter: int):
         super().__init__()
@@ -236,12 +304,17 @@ class UnrolledBatch(torch.nn.Module):
             raise ValueError("one mask per description is required")
         if len({(d.beta, d.tau) for d in descs}) != 1:
             raise ValueError("instances sharing t_k, tau_k must share beta and tau")
+        self.n_iter = int(n_iter)
         self.engines = [Unrolled2D(d, m, n_iter) for d, m in zip(descs, masks)]
+        self.bplan = api.BatchPlan(list(descs))
+        self.mask_p = self.bplan.pack([e.mask for e in self.engines], torch.uint8, mask=True)
         dev = self.engines[0].dev
+        self.stream = torch.cuda.Stream(device=dev)
         self.ts = torch.nn.Parameter(torch.full((n_iter,), 1.0 / descs[0].beta, dtype=torch.float32, device=dev))
         self.taus = torch.nn.Parameter(torch.full((n_iter,), descs[0].tau, dtype=torch.float32, device=dev))
 
     def forward(self, Ys):
         if len(Ys) != len(self.engines):
             raise ValueError("one k-space array per instance is required")
-        return [UnrolledFunction.apply(Y, self.ts, self.taus, e) for Y, e in zip(Ys, self.engines)]
+        self.stream.wait_stream(torch.cuda.current_stream())
+        return list(UnrolledBatchFunction.apply(self.ts, self.taus, self, *Ys))

@@ -120,6 +120,9 @@ def test_null_arguments(lib):
     assert lib.selr_ssos(None, 1, 1, 1, None, None) == 1
     assert lib.selr_rlne(None, None, 1, None, None) == 1
     assert lib.selr_spirit_calibrate(None, None, None) == 1
+    assert lib.selr_solve_unrolled(None, None, None, None, None, None, 1, None, None, None) == 1
+    assert lib.selr_lifted_unpack(None, None, 0, 0, None, None) == 1
+    assert lib.selr_lifted_elems(None, None) == 1
     assert lib.selr_spirit_kernel(None, None, None) == 1
     assert lib.selr_mssim(None, None, 16, 16, 1.0, None, None, None) == 1
     assert lib.selr_max(None, 1, None, None) == 1
