@@ -283,16 +283,22 @@ __device__ __forceinline__ cf shfl_cf(cf v, int src) {
 // Householder reduction G = Q T Q^H (lower, packed G in shared memory,
 // n <= 32 * RPL).  Lane l of every warp owns rows l, l + 32, ... and keeps
 // their entries of the current reflector v and of the previous step's v and
-// w in registers.  Step k:
-//   1. warp 0 applies the previous step's rank-2 update to column k, forms
-//      the reflector from G[k+1:, k] and publishes v;
+// w in registers; for the per-row phases thread i owns row i.  Step k, with
+// the reflector v_k of column k already formed (by step k - 1, or before the
+// first step for column 0):
+//   1. every lane loads v_k for its rows;
 //   2. every warp sweeps its share of the trailing columns j > k once,
 //      applying the previous update G -= v w^H + w v^H and accumulating
 //      p = G v with the updated values: stored entry G(i, j) adds G(i, j) v_j
 //      to the row sum of p_i (registers, per-warp partials in shared memory)
 //      and conj(G(i, j)) v_i to p_j (warp reduction, one column per warp, so
 //      no atomics);
-//   3. all threads: p = tau (sum of partials), K = tau/2 Re(v^H p), w = p - K v.
+//   3. thread per row: p = tau (sum of partials), K = tau/2 Re(v^H p)
+//      (block sum), w = p - K v;
+//   4. thread per row: column k + 1 with this step's update applied, its
+//      norm (block sum) and the next reflector v_{k+1}.
+// Four barriers per step; the reflector is formed by all threads at once
+// instead of by one warp while the others wait.
 // Reflector: x = G[k+1:, k], alpha = -e^{i arg x0} ||x||, v = x - alpha e1,
 // tau = 2 / v^H v, so (I - tau v v^H) x = alpha e1.
 // Columns [0, c0) of the packed matrix stay in global memory and [c0, n) are held in
@@ -300,7 +306,7 @@ __device__ __forceinline__ cf shfl_cf(cf v, int src) {
 // k_tridiag and alignment fit in `budget` bytes (0 when everything fits).
 __host__ __device__ inline size_t tridiag_smem_c0(int n, int c0) {
     const long long pk = (long long)n * (n + 1) / 2, c0s = (long long)c0 * (2 * n - c0 + 1) / 2;
-    return al16((size_t)(pk - c0s) * 8) + (size_t)(EIG_WARPS + 5) * n * 8 + (size_t)n * 4 + 16;
+    return al16((size_t)(pk - c0s) * 8) + (size_t)(EIG_WARPS + 4) * n * 8 + (size_t)n * 4 + 16;
 }
 __host__ __device__ inline int tridiag_c0(int n, size_t budget) {
     int c0 = 0;
@@ -311,8 +317,8 @@ __host__ __device__ inline int tridiag_c0(int n, size_t budget) {
 template <int RPL, bool HYB, bool FULL>
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat_begin, EigArgs a, int budget) {
     extern __shared__ __align__(16) unsigned char tsm[];
-    __shared__ float s_tau;
-    __shared__ float red[EIG_WARPS];
+    __shared__ float red[EIG_WARPS], redk[EIG_WARPS], redx[EIG_WARPS];
+    __shared__ cf s_x0, s_p1;
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
@@ -329,8 +335,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     cf *Pw = Gs + al16((size_t)(pk - c0s) * 8) / 8;      // [EIG_WARPS][n] row-sum partials
     cf *Cs = Pw + (long long)EIG_WARPS * n;               // [n] column sums
     cf *vbuf0 = Cs + n, *vbuf1 = vbuf0 + n;               // v of this / previous step
-    cf *wbuf0 = vbuf1 + n, *wbuf1 = wbuf0 + n;            // w of this / previous step
-    int *cst = (int *)(wbuf1 + n);                        // [n] column offsets (global for j < c0)
+    cf *wbuf0 = vbuf1 + n;                                // w of the previous step, then of this one
+    int *cst = (int *)(wbuf0 + n);                        // [n] column offsets (global for j < c0)
     float *td = tri_d(a, g, mat), *ttau = td + n;
     cf *te = (cf *)(td + 2 * n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     auto colp = [&](int j) -> cf * { return (HYB && j < c0) ? Gglob + cst[j] : Gs + cst[j]; };
     for (int j = tid; j < n; j += EIG_THREADS) {
         cst[j] = (int)(colstart(j, n) - (j >= c0 ? c0s : 0));
-        vbuf1[j] = wbuf1[j] = mk(0.f, 0.f);
+        vbuf0[j] = vbuf1[j] = wbuf0[j] = mk(0.f, 0.f);
     }
     for (long long i = c0s + tid; i < pk; i += EIG_THREADS) Gs[i - c0s] = Gglob[i];
     __syncthreads();
@@ -348,80 +354,69 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
     cf vo[RPL], wo[RPL], vn[RPL];
 #pragma unroll
     for (int t = 0; t < RPL; ++t) vo[t] = wo[t] = vn[t] = mk(0.f, 0.f);
-    float tau_old = 0.f;
-    cf *vb = vbuf0, *vp = vbuf1, *wb = wbuf0, *wp = wbuf1;
-    for (int k = 0; k + 2 < n; ++k) {
-        // ---- 1. column k and the reflector (warp 0)
-        if (warp == 0) {
-            const cf vk = vp[k], wk = wp[k];
-            cf colv[RPL];
-            float xn2 = 0.f;
-            cf *colk = colp(k) - k;
-#pragma unroll
-            for (int t = 0; t < RPL; ++t) {
-                const int i = lane + 32 * t;
-                colv[t] = mk(0.f, 0.f);
-                if (32 * t + 31 >= k && (FULL || 32 * t < n) && i >= k && (FULL || i < n)) {
-                    cf gv = colk[i];
-                    if (tau_old != 0.f) {
-                        gv.x -= vo[t].x * wk.x + vo[t].y * wk.y + wo[t].x * vk.x + wo[t].y * vk.y;
-                        gv.y -= vo[t].y * wk.x - vo[t].x * wk.y + wo[t].y * vk.x - wo[t].x * vk.y;
-                        colk[i] = gv;
-                    }
-                    colv[t] = gv;
-                    if (i > k) xn2 += cabs2(gv);
-                }
-            }
-            xn2 = wsum(xn2);
-            const cf x0 = shfl_cf(pick(colv, (k + 1) >> 5), (k + 1) & 31);
-            const float ax0 = sqrtf(cabs2(x0));
-            const float rest = xn2 - ax0 * ax0;
-            float tau = 0.f;
-            cf alpha = x0, v0 = mk(0.f, 0.f);
-            if (rest > 1e-30f * xn2 && xn2 > floor2) {
-                const float xnorm = sqrtf(xn2);
-                const cf phs = ax0 > 0.f ? mk(x0.x / ax0, x0.y / ax0) : mk(1.f, 0.f);
-                alpha = mk(-phs.x * xnorm, -phs.y * xnorm);
-                tau = 1.f / (xn2 + xnorm * ax0);
-                v0 = mk(phs.x * (ax0 + xnorm), phs.y * (ax0 + xnorm));
-            }
-            cf *hv = Gglob + colstart(k, n) + 1;              // Householder vector k (global)
-#pragma unroll
-            for (int t = 0; t < RPL; ++t) {
-                const int i = lane + 32 * t;
-                if ((FULL || 32 * t < n)) {
-                    cf v = mk(0.f, 0.f);
-                    if (i >= k + 1 && (FULL || i < n)) {
-                        v = tau == 0.f ? mk(0.f, 0.f) : (i == k + 1 ? v0 : colv[t]);
-                        hv[i - k - 1] = v;
-                    }
-                    if ((FULL || i < n)) vb[i] = v;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) {
-                s_tau = tau;
-                ttau[k] = tau;
-                te[k] = alpha;
-                td[k] = colk[k].x;
-            }
-        }
+    cf *vcur = vbuf0, *vprev = vbuf1, *wv = wbuf0;
+    // Thread-per-row phases: thread tid owns row ir = tid (n <= EIG_THREADS) and keeps its entry of
+    // the current reflector in vr.
+    const int ir = tid;
+    cf vr = mk(0.f, 0.f);
+    // Reflector of column c from its updated entries x (thread ir holds x_ir for ir >= c):
+    // ||x[c+1:]||^2 and x_{c+1} are reduced over the block (one barrier), every thread forms tau,
+    // alpha and its own v_ir in the same order, and v goes to vdst (all rows, zero above c + 1) and
+    // to the Householder storage of column c in global memory.
+    auto reflect = [&](int c, cf x, cf *vdst) -> float {
+        float xn2 = (ir > c && ir < n) ? cabs2(x) : 0.f;
+        xn2 = wsum(xn2);
+        if (lane == 0) redx[warp] = xn2;
+        if (ir == c + 1) s_x0 = x;
         __syncthreads();
-        const float tau = s_tau;
+        xn2 = 0.f;
+#pragma unroll
+        for (int w2 = 0; w2 < EIG_WARPS; ++w2) xn2 += redx[w2];
+        const cf x0 = s_x0;
+        const float ax0 = sqrtf(cabs2(x0));
+        const float rest = xn2 - ax0 * ax0;
+        float tau = 0.f;
+        cf alpha = x0, v0 = mk(0.f, 0.f);
+        if (rest > 1e-30f * xn2 && xn2 > floor2) {
+            const float xnorm = sqrtf(xn2);
+            const cf phs = ax0 > 0.f ? mk(x0.x / ax0, x0.y / ax0) : mk(1.f, 0.f);
+            alpha = mk(-phs.x * xnorm, -phs.y * xnorm);
+            tau = 1.f / (xn2 + xnorm * ax0);
+            v0 = mk(phs.x * (ax0 + xnorm), phs.y * (ax0 + xnorm));
+        }
+        cf v = mk(0.f, 0.f);
+        if (ir > c && ir < n && tau != 0.f) v = ir == c + 1 ? v0 : x;
+        if (ir < n) vdst[ir] = v;
+        if (ir > c && ir < n) Gglob[colstart(c, n) + (ir - c)] = v;
+        if (ir == c) {
+            ttau[c] = tau;
+            te[c] = alpha;
+            td[c] = x.x;
+        }
+        vr = v;
+        return tau;
+    };
+    float tau = 0.f, tau_prev = 0.f;
+    if (n >= 3) {
+        tau = reflect(0, ir < n ? colp(0)[ir] : mk(0.f, 0.f), vcur);
+        __syncthreads();
+    }
+    for (int k = 0; k + 2 < n; ++k) {
+        // ---- 1. this step's reflector v_k in the lanes' row slots
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
-            vn[t] = ((FULL || i < n)) ? vb[i] : mk(0.f, 0.f);
+            vn[t] = ((FULL || i < n)) ? vcur[i] : mk(0.f, 0.f);
         }
         // ---- 2. fused update + symv over the trailing columns
-        const bool upd = tau_old != 0.f;
+        const bool upd = tau_prev != 0.f;
         cf pa[RPL];
 #pragma unroll
         for (int t = 0; t < RPL; ++t) pa[t] = mk(0.f, 0.f);
         // The sweep is instantiated twice (with and without the deferred update, which only
         // the first step lacks) so that the column loop carries no update branch, and every
         // complex multiply-add is an explicit FMA chain (a - b c - d e ... does not contract
-        // into FMAs): 16 FMAs per element and step (1.43 -> 1.36 M cycles per matrix, s = 192).
+        // into FMAs): 16 FMAs per element and step.
         auto sweep = [&](auto UPDC) {
         constexpr bool UPD = decltype(UPDC)::value;
         // TB columns per pass (j, j + 16, ...): their 2 TB column sums are reduced together
@@ -433,7 +428,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
                 const int j = j0 + c * EIG_WARPS;
                 float cr = 0.f, ci = 0.f;
                 if (j < n) {                                       // warp-uniform
-                    const cf voj = vp[j], woj = wp[j], vnj = vb[j];
+                    const cf voj = vprev[j], woj = wv[j], vnj = vcur[j];
                     cf *colj = colp(j) - j;
 #pragma unroll
                     for (int t = 0; t < RPL; ++t) {
@@ -509,44 +504,63 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag(GroupSet gs, int mat
             if ((FULL || 32 * t < n) && i >= k + 1 && (FULL || i < n)) Pw[(long long)warp * n + i] = pa[t];
         }
         __syncthreads();
-        // ---- 3. p = tau * (row partials + column sum), K, w (all threads)
-        cf pi = mk(0.f, 0.f), vi = mk(0.f, 0.f);
+        // ---- 3. p_ir = tau (row partials + column sum) and K = tau/2 Re(v^H p) (thread per row)
+        cf p = mk(0.f, 0.f);
         float kv = 0.f;
-        const int i3 = k + 1 + tid;
-        if (i3 < n) {
-            float sr = Cs[i3].x, si = Cs[i3].y;
+        if (ir > k && ir < n) {
+            float sr = Cs[ir].x, si = Cs[ir].y;
             for (int w2 = 0; w2 < EIG_WARPS; ++w2) {
-                const cf q = Pw[(long long)w2 * n + i3];
+                const cf q = Pw[(long long)w2 * n + ir];
                 sr += q.x;
                 si += q.y;
             }
-            pi = mk(tau * sr, tau * si);
-            vi = vb[i3];
-            kv = vi.x * pi.x + vi.y * pi.y;
+            p = mk(tau * sr, tau * si);
+            kv = vr.x * p.x + vr.y * p.y;
+            if (ir == k + 1) s_p1 = p;
         }
-        kv = bsum(kv, red);
-        const float K = 0.5f * tau * kv;
-        if (i3 < n) wb[i3] = mk(pi.x - K * vi.x, pi.y - K * vi.y);
-        if (tid <= k && tid < n) wb[tid] = mk(0.f, 0.f);
+        kv = wsum(kv);
+        if (lane == 0) redk[warp] = kv;
         __syncthreads();
+        float kvs = 0.f;
+#pragma unroll
+        for (int w2 = 0; w2 < EIG_WARPS; ++w2) kvs += redk[w2];
+        const float K = 0.5f * tau * kvs;
+        const cf w = (ir > k && ir < n) ? mk(p.x - K * vr.x, p.y - K * vr.y) : mk(0.f, 0.f);
+        if (ir < n) wv[ir] = w;
+        // ---- 4. column k + 1 after this step's update G -= v w^H + w v^H, and its reflector
+        float tau_next = 0.f;
+        if (k + 3 < n) {                                           // block-uniform
+            const cf p1 = s_p1, v1 = vcur[k + 1];
+            const cf w1 = mk(p1.x - K * v1.x, p1.y - K * v1.y);
+            cf x = mk(0.f, 0.f);
+            if (ir > k && ir < n) {
+                x = (colp(k + 1) - (k + 1))[ir];
+                x.x -= vr.x * w1.x + vr.y * w1.y + w.x * v1.x + w.y * v1.y;
+                x.y -= vr.y * w1.x - vr.x * w1.y + w.y * v1.x - w.x * v1.y;
+            }
+            tau_next = reflect(k + 1, x, vprev);
+        } else {
+            __syncthreads();
+        }
 #pragma unroll
         for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
-            wo[t] = ((FULL || i < n)) ? wb[i] : mk(0.f, 0.f);
+            wo[t] = ((FULL || i < n)) ? wv[i] : mk(0.f, 0.f);
             vo[t] = vn[t];
         }
-        tau_old = tau;
-        cf *tv = vp; vp = vb; vb = tv;
-        cf *tw = wp; wp = wb; wb = tw;
+        __syncthreads();
+        tau_prev = tau;
+        tau = tau_next;
+        cf *tv = vprev; vprev = vcur; vcur = tv;
     }
     // ---- last step's update on the final 2x2 block, then the remaining d, e
     if (warp == 0) {
         for (int j = (n >= 2 ? n - 2 : 0); j < n; ++j) {
-            const cf voj = vp[j], woj = wp[j];
+            const cf voj = vprev[j], woj = wv[j];
 #pragma unroll
             for (int t = 0; t < RPL; ++t) {
                 const int i = lane + 32 * t;
-                if (tau_old != 0.f && (FULL || 32 * t < n) && i >= j && (FULL || i < n)) {
+                if (tau_prev != 0.f && (FULL || 32 * t < n) && i >= j && (FULL || i < n)) {
                     cf *cj = colp(j) - j;
                     cf gv = cj[i];
                     gv.x -= vo[t].x * woj.x + vo[t].y * woj.y + wo[t].x * voj.x + wo[t].y * voj.y;
@@ -1567,7 +1581,7 @@ cudaError_t eig_init_attributes() {
 }
 
 static size_t tridiag_smem(int n) {
-    return al16((size_t)n * (n + 1) / 2 * 8) + (size_t)(EIG_WARPS + 5) * n * 8 + (size_t)n * 4 + 16;
+    return al16((size_t)n * (n + 1) / 2 * 8) + (size_t)(EIG_WARPS + 4) * n * 8 + (size_t)n * 4 + 16;
 }
 static size_t tridiag_g_smem(int n) { return 2 * (size_t)n * 8 + (size_t)n * 4 + 16; }
 static int ev_chunk(int nmax) { return nmax <= 352 ? 16 : 8; }
