@@ -111,6 +111,42 @@ __device__ __forceinline__ void cp_async8(void *dst_smem, const void *src, int s
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Transpose-reduce over the lanes: lane L ends with the lane total of value (L >> 1) & 15 of
+// a[16] (four halving exchanges, then one plain one: 16 shuffles for 16 sums).
+__device__ __forceinline__ float treduce16(const float (&a)[16], int lane) {
+    float b8[8], b4[4], b2[2];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const bool hi = lane & 16;
+        b8[q] = (hi ? a[q + 8] : a[q]) + __shfl_xor_sync(0xffffffffu, hi ? a[q] : a[q + 8], 16);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool hi = lane & 8;
+        b4[q] = (hi ? b8[q + 4] : b8[q]) + __shfl_xor_sync(0xffffffffu, hi ? b8[q] : b8[q + 4], 8);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const bool hi = lane & 4;
+        b2[q] = (hi ? b4[q + 2] : b4[q]) + __shfl_xor_sync(0xffffffffu, hi ? b4[q] : b4[q + 2], 4);
+    }
+    const bool hi = lane & 2;
+    const float s = (hi ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, hi ? b2[0] : b2[1], 2);
+    return s + __shfl_xor_sync(0xffffffffu, s, 1);
+}
+
+// Lane L ends with the lane total of value (L >> 3) & 3 of a[4].
+__device__ __forceinline__ float treduce4(const float (&a)[4], int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8;
+    const float b0 = (h16 ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, h16 ? a[0] : a[2], 16);
+    const float b1 = (h16 ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, h16 ? a[1] : a[3], 16);
+    float s = (h8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h8 ? b0 : b1, 8);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    return s + __shfl_xor_sync(0xffffffffu, s, 1);
+}
 
 // ------------------------------------------------------------------- Gram
 // One CTA computes a 64x64 block (I >= J) of G = B^H B for one matrix.
@@ -208,8 +244,10 @@ __device__ __forceinline__ int sturm_lt(const float *d, const float *f2, int n, 
 // The factorisation is done once (factor = true) and reused.  A zero pivot is
 // replaced by `tiny` (inverse iteration wants a huge, not infinite, growth).
 template <int ST>
-__device__ void tri_solve(const float *d, const float *f, int n, float lam, float *z, float *u0, float *u1,
-                          float *u2, float *lm, unsigned char *piv, float tiny, bool factor) {
+__device__ void tri_solve(const float *__restrict__ d, const float *__restrict__ f, int n, float lam,
+                          float *__restrict__ z, float *__restrict__ u0, float *__restrict__ u1,
+                          float *__restrict__ u2, float *__restrict__ lm, unsigned char *__restrict__ piv, float tiny,
+                          bool factor) {
     if (factor) {
         float c0 = d[0] - lam, c1 = n > 1 ? f[0] : 0.f;
         for (int k = 0; k < n - 1; ++k) {
@@ -802,6 +840,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
     __shared__ float red[4];
     __shared__ int s_r, s_cst, s_wend;
     __shared__ cf s_cm[EV_HB * EV_HB];    // C_ji of the current batch of reflectors
+    __shared__ float s_dv[16 * 2 * EV_HB];  // per warp: the batch's dot products u_j^H y
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
@@ -831,20 +870,28 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
     int *rank_out = a.rank + g.moff + mat;
     tri_real_setup(td, ttau, te, n, dd, taus, ff, f2, ph, tid, lane, warp, NT);
     __syncthreads();
-    if (tid == 0) {
-        float gl, gu, pivmin;
-        gershgorin(dd, ff, f2, n, &gl, &gu, &pivmin);
-        red[0] = gl; red[1] = gu; red[2] = pivmin;
-        s_r = allp ? n : n - ((t2 >= gu) ? n : sturm_lt(dd, f2, n, t2, pivmin));
+    if (warp == 0) {
+        float gl = 0.f, gu = 0.f, pivmin = 0.f;
+        if (lane == 0) gershgorin(dd, ff, f2, n, &gl, &gu, &pivmin);
+        gl = __shfl_sync(0xffffffffu, gl, 0);
+        gu = __shfl_sync(0xffffffffu, gu, 0);
+        pivmin = __shfl_sync(0xffffffffu, pivmin, 0);
         // near-degenerate at the threshold: t^2 below the FP32 resolution floor
-        // F = 64 eps_32 lambda_max of the Gram eigenvalues, with eigenvalues between t^2
-        // and F, so the count above t^2 is not determined in FP32 -> FP64 re-solve
-        if (!allp && a.fp64_fallback && s_r > 0) {
-            const float F = 32.f * FLT_EPSILON * fmaxf(fabsf(gl), fabsf(gu));
-            if (t2 < F) {
-                const int cF = n - ((F >= gu) ? n : sturm_lt(dd, f2, n, F, pivmin));
-                if (cF != s_r) s_r = -1;
-            }
+        // F = 32 eps_32 max(|gl|, |gu|) of the Gram eigenvalues, with eigenvalues between t^2
+        // and F, so the count above t^2 is not determined in FP32 -> FP64 re-solve.  Lane 0
+        // counts the eigenvalues below t^2 and lane 1 those below F, side by side.
+        const float F = 32.f * FLT_EPSILON * fmaxf(fabsf(gl), fabsf(gu));
+        int c = 0;
+        if (lane < 2) {
+            const float x = lane == 0 ? t2 : F;
+            c = (x >= gu) ? n : sturm_lt(dd, f2, n, x, pivmin);
+        }
+        const int ct = __shfl_sync(0xffffffffu, c, 0), cF = __shfl_sync(0xffffffffu, c, 1);
+        if (lane == 0) {
+            red[0] = gl; red[1] = gu; red[2] = pivmin;
+            int rr = allp ? n : n - ct;
+            if (!allp && a.fp64_fallback && rr > 0 && t2 < F && n - cF != rr) rr = -1;
+            s_r = rr;
         }
     }
     __syncthreads();
@@ -959,74 +1006,103 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
             Yc[idx] = cscale(ph[i], zv[i * IV_ST + w]);
         }
         __syncthreads();
-        // Reflectors are applied in batches of EV_HB, u_j = v_{kb-j} (j = 0 .. nbat-1, in the order
-        // of application), staged in shared memory by absolute row (zero on rows <= kb - j).
-        // With d_j = u_j^H y and C_ji = u_j^H u_i, applying them one after the other is
+        // Reflectors are applied in batches of EV_HB, u_j = v_{kb-j} (j = 0 .. EV_HB-1, in the order
+        // of application), staged in shared memory by absolute row (zero on rows <= kb - j, and
+        // wholly zero past reflector 0).  With d_j = u_j^H y and C_ji = u_j^H u_i, applying them
+        // one after the other is
         //   s_j = d_j - sum_{i<j} tau_i C_ji s_i,   y <- y - sum_j tau_j u_j s_j,
-        // so each vector needs one round of independent reductions per batch instead of one
-        // reduction per reflector; C (independent of y) is formed by all warps after staging.
-        // Batches are double-buffered in the inverse-iteration arrays (free from here on: zv was
-        // copied to Yc above) and copied with cp.async while the previous batch is applied.
-        cf *hbuf[2] = {(cf *)(vsm + LY.zv), (cf *)(vsm + LY.zv) + (long long)EV_HB * n};
-        auto issue_batch = [&](int kb, cf *buf) {
-            for (int j = 0; j < EV_HB; ++j) {
-                const int k = kb - j;
-                for (int row = tid; row < n; row += NT) {
-                    const bool ok = k >= 0 && row > k;
-                    cp_async8(buf + (long long)j * n + row, ok ? Gglob + colstart(k, n) + (row - k) : Gglob, ok ? 8 : 0);
+        // so each vector needs one round of reductions per batch instead of one per reflector:
+        // its 2 EV_HB dot-product sums are reduced over the lanes by one transpose-reduce and
+        // exchanged through shared memory.  C (independent of y) is formed by all warps after
+        // staging, two entries per warp and round with one 4-value transpose-reduce.  Batches
+        // are staged nbuf - 1 ahead (nbuf = 3 buffers where they fit, else 2) in the
+        // inverse-iteration arrays (free from here on: zv was copied to Yc above) with cp.async,
+        // one commit group per batch index.
+        static_assert(EV_HB == 8, "the batch's 2 EV_HB dot products per vector are reduced by treduce16");
+        const size_t hb_elems = (size_t)EV_HB * n;
+        const int nbuf = 3 * hb_elems * 8 <= LY.yc - LY.zv ? 3 : 2;
+        cf *hbuf0 = (cf *)(vsm + LY.zv);
+        const int nbatch = n >= 3 ? (n - 3) / EV_HB + 1 : 0;   // batch b: kb = n - 3 - b EV_HB
+        auto issue_batch = [&](int b) {
+            if (b < nbatch) {
+                const int kb = n - 3 - b * EV_HB;
+                cf *buf = hbuf0 + (long long)(b % nbuf) * hb_elems;
+                for (int j = 0; j < EV_HB; ++j) {
+                    const int k = kb - j;
+                    for (int row = tid; row < n; row += NT) {
+                        const bool ok = k >= 0 && row > k;
+                        cp_async8(buf + (long long)j * n + row, ok ? Gglob + colstart(k, n) + (row - k) : Gglob,
+                                  ok ? 8 : 0);
+                    }
                 }
             }
             cp_async_commit();
         };
-        issue_batch(n - 3, hbuf[0]);
-        int bsel = 0;
-        for (int kb = n - 3; kb >= 0; kb -= EV_HB, bsel ^= 1) {
+        for (int b = 0; b + 1 < nbuf; ++b) issue_batch(b);
+        for (int b = 0; b < nbatch; ++b) {
+            const int kb = n - 3 - b * EV_HB;
             const int nbat = min(EV_HB, kb + 1);
             const int r0 = kb - nbat + 2;                    // first row any u_j of the batch touches
-            cf *hb = hbuf[bsel];
-            cp_async_wait_all();
-            __syncthreads();                                 // batch kb staged; the other buffer is free
-            if (kb - EV_HB >= 0) issue_batch(kb - EV_HB, hbuf[bsel ^ 1]);
+            const cf *hb = hbuf0 + (long long)(b % nbuf) * hb_elems;
+            if (nbuf == 3) cp_async_wait_1();                // every group but the newest (batch b + 1)
+            else cp_async_wait_all();
+            __syncthreads();                                 // batch b staged; the buffer of b - 1 is free
+            issue_batch(b + nbuf - 1);
             // C_ji = u_j^H u_i, i < j, over the rows of u_i (rows > kb - i)
-            for (int pq = warp; pq < nbat * (nbat - 1) / 2; pq += NW) {
-                int j = 1, i = pq;
-                while (i >= j) { i -= j; ++j; }
-                const cf *uj = hb + (long long)j * n, *ui = hb + (long long)i * n;
-                float cr = 0.f, ci = 0.f;
-                for (int row = kb - i + 1 + lane; row < n; row += 32) {
-                    const cf x = uj[row], z = ui[row];
-                    cr += x.x * z.x + x.y * z.y;
-                    ci += x.x * z.y - x.y * z.x;
+            for (int pq0 = 2 * warp; pq0 < EV_HB * (EV_HB - 1) / 2; pq0 += 2 * NW) {   // warp-uniform
+                float cv[4];
+                int jj[2], ii[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    int j = 1, i = pq0 + e;
+                    while (i >= j) { i -= j; ++j; }
+                    jj[e] = j;
+                    ii[e] = i;
+                    float cr = 0.f, ci = 0.f;
+                    if (pq0 + e < EV_HB * (EV_HB - 1) / 2) {
+                        const cf *uj = hb + (long long)j * n, *ui = hb + (long long)i * n;
+                        for (int row = kb - i + 1 + lane; row < n; row += 32) {
+                            const cf x = uj[row], z = ui[row];
+                            cr += x.x * z.x + x.y * z.y;
+                            ci += x.x * z.y - x.y * z.x;
+                        }
+                    }
+                    cv[2 * e] = cr;
+                    cv[2 * e + 1] = ci;
                 }
-                cr = wsum(cr);
-                ci = wsum(ci);
-                if (lane == 0) s_cm[j * EV_HB + i] = mk(cr, ci);
+                const float s = treduce4(cv, lane);          // lane L: total of value (L >> 3) & 3
+                if ((lane & 7) == 0) {
+                    const int v = (lane >> 3) & 3, e = v >> 1;
+                    if (pq0 + e < EV_HB * (EV_HB - 1) / 2)
+                        ((float *)s_cm)[2 * ((e ? jj[1] : jj[0]) * EV_HB + (e ? ii[1] : ii[0])) + (v & 1)] = s;
+                }
             }
             __syncthreads();
             for (int w = warp; w < qc; w += NW) {
                 cf *y = Yc + (long long)w * n;
-                float dr[EV_HB], di[EV_HB], tj[EV_HB];
+                float dv[2 * EV_HB], dr[EV_HB], di[EV_HB], tj[EV_HB];
 #pragma unroll
-                for (int j = 0; j < EV_HB; ++j) {
-                    dr[j] = di[j] = 0.f;
-                    tj[j] = j < nbat ? taus[kb - j] : 0.f;
-                }
+                for (int j = 0; j < 2 * EV_HB; ++j) dv[j] = 0.f;
                 for (int row = r0 + lane; row < n; row += 32) {
                     const cf yy = y[row];
 #pragma unroll
                     for (int j = 0; j < EV_HB; ++j) {
-                        if (j < nbat) {
-                            const cf u = hb[(long long)j * n + row];
-                            dr[j] += u.x * yy.x + u.y * yy.y;
-                            di[j] += u.x * yy.y - u.y * yy.x;
-                        }
+                        const cf u = hb[(long long)j * n + row];
+                        dv[2 * j] += u.x * yy.x + u.y * yy.y;
+                        dv[2 * j + 1] += u.x * yy.y - u.y * yy.x;
                     }
                 }
+                const float sred = treduce16(dv, lane);      // lane L: total of value (L >> 1) & 15
+                float *sd = s_dv + warp * 2 * EV_HB;
+                if ((lane & 1) == 0) sd[(lane >> 1) & 15] = sred;
+                __syncwarp();
 #pragma unroll
                 for (int j = 0; j < EV_HB; ++j) {
-                    dr[j] = wsum(dr[j]);
-                    di[j] = wsum(di[j]);
+                    dr[j] = sd[2 * j];
+                    di[j] = sd[2 * j + 1];
+                    tj[j] = j < nbat ? taus[kb - j] : 0.f;
                 }
+                __syncwarp();
                 // forward substitution (every lane), then dr, di <- tau_j s_j
 #pragma unroll
                 for (int j = 0; j < EV_HB; ++j) {
@@ -1044,11 +1120,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
                     float ar = 0.f, ai = 0.f;
 #pragma unroll
                     for (int j = 0; j < EV_HB; ++j) {
-                        if (j < nbat) {
-                            const cf u = hb[(long long)j * n + row];
-                            ar += u.x * dr[j] - u.y * di[j];
-                            ai += u.x * di[j] + u.y * dr[j];
-                        }
+                        const cf u = hb[(long long)j * n + row];
+                        ar += u.x * dr[j] - u.y * di[j];
+                        ai += u.x * di[j] + u.y * dr[j];
                     }
                     y[row] = mk(y[row].x - ar, y[row].y - ai);
                 }
