@@ -131,7 +131,21 @@ def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
     else:
         nmat = sum(nm for nm, _, _ in fams)
         per = nmat + fft_a + 2 + fft_a + sum(nm * (1 + svt_kernels(r, c)) for nm, r, c in fams)
+    desc = getattr(plan, "desc", None)
+    if desc is not None and desc.model in ("SHLR_S", "SHLR_SV"):
+        # the SPIRiT X-update (spirit.cu) replaces the pointwise divide: copy, one operator
+        # application (4 FFTs, pixel kernel, combine), init, then per CG iteration one
+        # application, the update and (but the last) the direction update, and the finish
+        per += 7 + 8 * desc.cg_iters
     return per + (0 if model2d else 1)
+
+
+def calibration_launches(plan):
+    """Kernels of the SPIRiT calibration that opens every SHLR-S / SHLR-SV solve: Gram of
+    the ACS rows, one Cholesky launch per 4 target coils, placement, 2 FFTs, finish."""
+    if plan.desc.model not in ("SHLR_S", "SHLR_SV"):
+        return 0
+    return 5 + (plan.desc.J + 3) // 4
 
 
 def gram_for(args, model2d):
@@ -294,7 +308,8 @@ def run_gpu(args, rank, world):
         plan.profile(False)
         st3 = api.selr_sync_status(plan, stream)
         results[mode] = dict(ms=ms, steps=steps, status=max(st, st2, st3), nmat=nmat, clocks=clocks, stages=prof,
-                             launches=steps * kernel_launches_per_iteration(plan, model2d, mode, args.svd) + 6)
+                             launches=steps * kernel_launches_per_iteration(plan, model2d, mode, args.svd) + 6
+                             + calibration_launches(plan))
         if mode == "batched":
             results["plan"] = plan
         else:
@@ -708,6 +723,136 @@ def run_batch(args, rank, world):
     return line
 
 
+def run_quality(args):
+    """Reconstruction quality on the synthetic stand-ins, computed with the library's own
+    metric kernels (SSOS, RLNE, MSSIM, T2 fit): the model ablation on one data set and
+    mask (SHLR, SHLR-S, SHLR-V, SHLR-SV), the sampling patterns, an ACS-line sweep at a
+    fixed sampling rate and the T2 map of the parameter model, each against the
+    zero-filled reconstruction.  One JSON line per experiment; not a throughput line."""
+    import torch
+    from paper_2107_11650_gb300 import api
+    from paper_2107_11650_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n_iter = 30
+
+    def solve(wl, Y, mask):
+        plan = api.Plan(api.Desc.from_workload(wl, max_iter=n_iter, gram="3xtf32"))
+        X = torch.empty_like(Y)
+        with torch.cuda.stream(stream):
+            api.selr_solve(plan, Y, mask, X, stream=stream)           # first call captures the graph
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            api.selr_solve(plan, Y, mask, X, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        st = api.selr_sync_status(plan, stream)
+        return plan, X, n_iter * 1000.0 / e0.elapsed_time(e1), st
+
+    def zero_filled(plan, Y, two_d):
+        with torch.cuda.stream(stream):
+            Z = Y.clone()
+            if two_d:
+                api.selr_transform(plan, 0, True, Z, Z, stream=stream)
+            api.selr_transform(plan, 1, True, Z, Z, stream=stream)
+        return Z
+
+    def scores(ref_img, X):
+        with torch.cuda.stream(stream):
+            rec = api.selr_ssos(X, stream=stream)
+            rl = api.selr_rlne(ref_img, rec, stream=stream)
+            ms, _ = api.selr_mssim(ref_img, rec, stream=stream)
+        stream.synchronize()
+        return float(rl.item()), float(ms.item())
+
+    def case(wl, Y=None, mask=None, truth=None):
+        if Y is None:
+            inp = synth.make_inputs(wl)
+            Y, mask, truth = inp["Y"], inp["mask"], inp["truth"]
+        Yd = torch.from_numpy(Y.astype(np.complex64)).cuda()
+        md = torch.from_numpy(mask.astype(np.uint8)).cuda()
+        with torch.cuda.stream(stream):
+            ref = api.selr_ssos(torch.from_numpy(truth.astype(np.complex64)).cuda(), stream=stream)
+        plan, X, its, st = solve(wl, Yd, md)
+        rl, ms = scores(ref, X)
+        zr, zm = scores(ref, zero_filled(plan, Yd, True))
+        plan.close()
+        return {"model": wl.model, "rlne": rl, "mssim": ms, "zero_filled_rlne": zr, "zero_filled_mssim": zm,
+                "iters_per_s": its, "status": st, "sampling": float(mask.mean())}
+
+    base = synth.get_config("shlr_12c_256")
+    lam1 = {"SHLR_S": 1e3, "SHLR_SV": 1e2}
+    rows = []
+    for model in ("SHLR", "SHLR_S", "SHLR_V", "SHLR_SV"):
+        r = case(base.with_(model=model, lam1=lam1.get(model, base.lam1)))
+        if model in lam1:
+            r["lambda1"] = lam1[model]
+        rows.append(r)
+    print(json.dumps({"quality": "model_ablation", "workload": "12-coil 256x256, 1D random R=4 + 24 ACS lines",
+                      "iterations": n_iter, "rows": rows}))
+
+    rows = []
+    for name in ("shlr_12c_256_uniform6", "shlr_12c_256_uniform6_pf34", "shlr_12c_256_gauss_pf34",
+                 "shlrv_12c_256", "shlrv_12c_256_poisson_pf45"):
+        wl = synth.get_config(name)
+        r = case(wl)
+        r["workload"] = name
+        r["mask"] = f"{wl.mask} R={wl.R} acs={wl.n_acs}" + (f" pf={wl.pf}" if wl.pf < 1.0 else "")
+        rows.append(r)
+    print(json.dumps({"quality": "sampling_patterns", "iterations": n_iter, "rows": rows}))
+
+    sw = synth.ACS_SWEEP
+    x = synth.multicoil_image(base.J, base.M, base.N, base.seed)
+    rows = []
+    for n_acs, mask in synth.acs_sweep_masks(base.M, base.N, sw["rate"], sw["acs_lines"], base.seed + 101).items():
+        Y = synth.acquire_2d(x, mask, base.sigma_n, base.seed)
+        sc = 1.0 / np.abs(Y).max()
+        for model in ("SHLR", "SHLR_SV"):
+            wl = base.with_(model=model, n_acs=n_acs, mask="gauss1d", lam1=lam1.get(model, base.lam1))
+            r = case(wl, Y * sc, mask, x * sc)
+            r["acs_lines"] = n_acs
+            rows.append(r)
+    print(json.dumps({"quality": "acs_sweep", "rate": sw["rate"], "iterations": n_iter, "rows": rows}))
+
+    wl = synth.get_config("shlrvp_8c_192_8e")
+    inp = synth.make_inputs(wl)
+    te = [wl.te_ms * (l + 1) for l in range(wl.L)]
+    _, t2_true, m0 = synth.t2_series(wl.J, wl.M, wl.N, wl.L, te, wl.seed)
+    Yd = torch.from_numpy(inp["Y"].astype(np.complex64)).cuda()
+    md = torch.from_numpy(inp["mask"].astype(np.uint8)).cuda()
+    plan, X, its, st = solve(wl, Yd, md)
+    support = m0 > 0.1 * m0.max()
+
+    def t2_rlne(Ximg):
+        with torch.cuda.stream(stream):
+            S = api.selr_ssos(Ximg, stream=stream)
+            T2, _ = api.selr_t2_fit(S, te, stream=stream)
+        stream.synchronize()
+        t2 = T2.cpu().numpy()
+        ok = support & np.isfinite(t2)
+        fit_frac = float(ok.sum() / support.sum())
+        err = float(np.linalg.norm((t2 - t2_true)[ok]) / np.linalg.norm(t2_true[ok]))
+        return err, fit_frac
+
+    with torch.cuda.stream(stream):
+        ref = api.selr_ssos(torch.from_numpy(inp["truth"].astype(np.complex64)).cuda(), stream=stream)
+        rec = api.selr_ssos(X, stream=stream)
+        rl = api.selr_rlne(ref, rec, stream=stream)
+        Z = zero_filled(plan, Yd, False)
+        zr = api.selr_rlne(ref, api.selr_ssos(Z, stream=stream), stream=stream)
+    stream.synchronize()
+    (t2e, t2f), (zt2e, zt2f) = t2_rlne(X), t2_rlne(Z)
+    print(json.dumps({"quality": "t2_map", "workload": "shlrvp_8c_192_8e", "model": wl.model, "iterations": n_iter,
+                      "t2_rlne": t2e, "t2_fitted_fraction": t2f, "zero_filled_t2_rlne": zt2e,
+                      "zero_filled_t2_fitted_fraction": zt2f, "series_rlne": float(rl.item()),
+                      "zero_filled_series_rlne": float(zr.item()), "iters_per_s": its, "status": st,
+                      "support": "pixels with M0 > 0.1 max M0 and a fitted T2 in range",
+                      "t2_fit_range_ms": [1.0, 1000.0]}))
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -723,6 +868,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--allow-tf32", action="store_true")
+    ap.add_argument("--quality", action="store_true",
+                    help="reconstruction-quality experiments (RLNE / MSSIM / T2) instead of the throughput line")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -733,6 +880,10 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.quality:
+        if rank == 0:
+            run_quality(args)
         return
     if args.config == "unrolled_16_uneven":
         run_unrolled(args, rank, world)

@@ -62,6 +62,14 @@ CONFIGS = {
     "shlrvp_8c_192_8e": Workload(name="shlrvp_8c_192_8e", model="SHLR_VP", J=8, M=192, N=192, L=8,
                                  window=12, window_param=4, mask="random1d", R=6.0, n_acs=8,
                                  sigma_n=1e-3, seed=4, te_ms=10.0, beta=20.0, tau=20.0, lam2=2.0),
+    # the bench workload's data and mask with the SPIRiT term (Eq. 3 / Eq. 6): SHLR-S and
+    # SHLR-SV, 5x5 kernel calibrated on the 24 ACS lines, X-update by 30 CG iterations
+    "shlrs_12c_256": Workload(name="shlrs_12c_256", model="SHLR_S", J=12, M=256, N=256, window=16,
+                              mask="random1d", R=4.0, n_acs=24, sigma_n=1e-3, seed=2,
+                              beta=20.0, tau=20.0, lam1=1e3),
+    "shlrsv_12c_256": Workload(name="shlrsv_12c_256", model="SHLR_SV", J=12, M=256, N=256, window=16,
+                               mask="random1d", R=4.0, n_acs=24, sigma_n=1e-3, seed=2,
+                               beta=20.0, tau=20.0, lam1=1e2),
     # the paper's further parallel-imaging patterns on the 12-coil 256x256 data:
     # uniform R = 6 with 20 ACS lines; that pattern with 3/4 partial Fourier; the
     # Gaussian Cartesian pattern (rate ~0.34) with 3/4 partial Fourier; the 2D

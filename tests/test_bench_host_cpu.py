@@ -13,9 +13,16 @@ reduction.
 import bench
 
 
+class _Desc:
+    def __init__(self, model, J=12, cg_iters=30):
+        self.model, self.J, self.cg_iters = model, J, cg_iters
+
+
 class _Plan:
-    def __init__(self, fams):
+    def __init__(self, fams, desc=None):
         self._f = fams
+        if desc is not None:
+            self.desc = desc
 
     def lift_shape(self, axis):
         return self._f[axis]
@@ -43,3 +50,15 @@ def test_plain_mode_counts_per_matrix():
     p = _Plan({"row": (4, 57, 32), "col": (4, 57, 32)})
     # per matrix: its lift and its seven eigensolver kernels
     assert bench.kernel_launches_per_iteration(p, True, "plain") == 8 + 2 + 2 + 2 + 8 * 8
+
+
+def test_spirit_models_count_the_cg_x_update_and_the_calibration():
+    # SHLR-S: the pointwise divide (1 kernel) becomes the CG X-update: copy, operator
+    # (4 FFTs + pixel + combine), init, 30 x (operator, update, direction update) less the
+    # last direction update, finish = 8 + 8 * 30 kernels
+    fams = {"row": (256, 241, 192), "col": (256, 241, 192)}
+    p = _Plan(fams, _Desc("SHLR_S", J=12, cg_iters=30))
+    assert bench.kernel_launches_per_iteration(p, True, "batched") == 15 - 1 + 8 + 8 * 30
+    # calibration once per solve: Gram, 3 Cholesky launches (4 coils each), place, 2 FFTs, finish
+    assert bench.calibration_launches(p) == 5 + 3
+    assert bench.calibration_launches(_Plan(fams, _Desc("SHLR"))) == 0
