@@ -40,7 +40,9 @@ struct selr_plan {
     int spirit;                          // SHLR-S / SHLR-SV: SPIRiT term and CG X-update
     int spirit_ready;                    // the kernel has been calibrated (host flag)
     cf *sp_Gm, *sp_g, *sp_vec;           // image-domain G - I, kernel, six CG vectors
+    cf *sp_Hm;                           // per pixel (G - I)^H (G - I), packed upper triangle
     float *sp_cj;
+    float *sp_diag;                      // diagonal of the X-update operator and preconditioner
     double *sp_part;
     double2 *sp_C, *sp_work;
     unsigned *gready, *ready, *vready;   // kernel hand-off flags, one per matrix (see EigArgs)
@@ -297,7 +299,7 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
                     p->rank, p->gready, p->ready, p->vready, p->rank_acc, p->f64work, p->sp_Gm, p->sp_g,
-                    p->sp_vec, p->sp_cj, p->sp_part, p->sp_C, p->sp_work, p->sigma,
+                    p->sp_vec, p->sp_Hm, p->sp_cj, p->sp_diag, p->sp_part, p->sp_C, p->sp_work, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -468,8 +470,10 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
     if (p->spirit) {
         const long long J = d->J, ks = d->spirit_ksize, nu = J * ks * ks, ns = nu - 1;
         AL(p->sp_Gm, sizeof(cf) * (size_t)(J * J * d->M * d->N));
+        AL(p->sp_Hm, sizeof(cf) * (size_t)(J * (J + 1) / 2 * d->M * d->N));
         AL(p->sp_g, sizeof(cf) * (size_t)(J * J * ks * ks));
         AL(p->sp_vec, 6 * sizeof(cf) * (size_t)p->nK);
+        AL(p->sp_diag, 2 * sizeof(float) * (size_t)p->nK);
         AL(p->sp_cj, sizeof(float) * (size_t)J);
         AL(p->sp_part, 3 * sizeof(double) * SP_NB);
         AL(p->sp_C, sizeof(double2) * (size_t)(nu * nu));
@@ -610,6 +614,7 @@ static GroupSet single_group(const selr_plan *p, int gi) {
 
 extern "C" selr_status selr_lift(selr_plan *p, int32_t axis, const void *x, const void *D, void *A_out,
                                  selr_stream stream) {
+    NvtxRange nvtx_range("selr_lift");
     if (!p || !x || !A_out) return SELR_ERR_INVALID_ARG;
     if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     const int gi = group_index(p, axis);
@@ -622,6 +627,7 @@ extern "C" selr_status selr_lift(selr_plan *p, int32_t axis, const void *x, cons
 }
 
 extern "C" selr_status selr_adjoint(selr_plan *p, int32_t axis, const void *E, void *x_out, selr_stream stream) {
+    NvtxRange nvtx_range("selr_adjoint");
     if (!p || !E || !x_out) return SELR_ERR_INVALID_ARG;
     if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     const int gi = group_index(p, axis);
@@ -720,6 +726,7 @@ static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, c
 
 extern "C" selr_status selr_svt(selr_plan *p, void *A, int32_t nmat, int32_t rows, int32_t cols, float thresh,
                                 int32_t *rank_out, selr_stream stream) {
+    NvtxRange nvtx_range("selr_svt");
     if (!p || !A || nmat < 1 || rows < 1 || cols < 1 || !(thresh >= 0.f) || !isfinite(thresh))
         return SELR_ERR_INVALID_ARG;
     GroupSet s;
@@ -762,8 +769,9 @@ static SpiritArgs spirit_args(selr_plan *p, const cf *Y, const uint8_t *mask, co
     s.nK = I.nK;
     s.lambda = I.lambda; s.beta = p->d.beta; s.lambda1 = p->d.lambda1; s.reg = p->d.spirit_reg;
     s.da = I.da; s.db = I.db; s.mask = mask; s.Y = Y; s.K = K; s.adjA = adj_a; s.adjB = adj_b;
-    s.Gm = p->sp_Gm; s.g = p->sp_g; s.cj = p->sp_cj;
+    s.Gm = p->sp_Gm; s.Hm = p->sp_Hm; s.g = p->sp_g; s.cj = p->sp_cj;
     s.x = p->sp_vec; s.r = s.x + I.nK; s.z = s.r + I.nK; s.p = s.z + I.nK; s.q = s.p + I.nK; s.t = s.q + I.nK;
+    s.dv = p->sp_diag; s.pdv = s.dv + I.nK;
     s.part = p->sp_part; s.partial = p->partial + I.poff; s.status = p->status;
     s.cal_C = p->sp_C; s.cal_work = p->sp_work;
     s.ftM = I.ftM; s.ftN = I.ftN;
@@ -807,6 +815,7 @@ static cudaError_t dc_step(selr_plan *p, const cf *Y, const uint8_t *mask, cf *a
 }
 
 extern "C" selr_status selr_spirit_calibrate(selr_plan *p, const void *Y, selr_stream stream) {
+    NvtxRange nvtx_range("selr_spirit_calibrate");
     if (!p || !Y) return SELR_ERR_INVALID_ARG;
     if (!p->spirit) return SELR_ERR_UNSUPPORTED;
     CK(launch_spirit_calibrate(spirit_args(p, (const cf *)Y, nullptr, nullptr, nullptr, nullptr), (const cf *)Y,
@@ -825,6 +834,7 @@ extern "C" selr_status selr_spirit_kernel(selr_plan *p, void *g_out, selr_stream
 
 extern "C" selr_status selr_dc(selr_plan *p, const void *Y, const uint8_t *mask, void *adj_a, void *adj_b,
                                void *K, float *rel_out, selr_stream stream) {
+    NvtxRange nvtx_range("selr_dc");
     if (!p || !Y || !mask || !adj_a || !adj_b || !K) return SELR_ERR_INVALID_ARG;
     if (p->n_inst != 1) return SELR_ERR_UNSUPPORTED;
     if (p->spirit && !p->spirit_ready) return SELR_ERR_UNSUPPORTED;    // selr_spirit_calibrate first
@@ -839,7 +849,17 @@ extern "C" selr_status selr_dc(selr_plan *p, const void *Y, const uint8_t *mask,
 //   (hybrid transforms), 3 lifts, 4 Gram matrices, 5 eigensolver / Jacobi SVD,
 //   6 SVT apply + D update.  In plain mode stage 3 runs lift and the whole SVT
 //   one matrix at a time and stages 4-6 are empty.
+static cudaError_t admm_stage_body(selr_plan *p, int stage, const cf *Y, const uint8_t *mask, cudaStream_t st);
+
+// One ADMM stage (0 adjoint, 1 X-update, 2 hybrid transforms, 3 lift, 4 Gram, 5 eigensolver,
+// 6 apply and multiplier update) inside an NVTX range named after it.
 static cudaError_t admm_stage(selr_plan *p, int stage, const cf *Y, const uint8_t *mask, cudaStream_t st) {
+    static const char *const names[] = {"adjoint", "dc", "hybrid_fft", "lift", "gram", "svd", "apply"};
+    NvtxRange r(stage >= 0 && stage < 7 ? names[stage] : "stage");
+    return admm_stage_body(p, stage, Y, mask, st);
+}
+
+static cudaError_t admm_stage_body(selr_plan *p, int stage, const cf *Y, const uint8_t *mask, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     const bool plain = p->d.exec == SELR_EXEC_PLAIN;
     const bool jac = p->d.svd_method == SELR_SVD_JACOBI;
@@ -1006,6 +1026,7 @@ static cudaError_t output_image(selr_plan *p, cf *X, cudaStream_t st) {
 extern "C" selr_status selr_solve(selr_plan *p, const void *Yv, const uint8_t *mask, void *X_out,
                                   void *state_inout, int32_t resume, int32_t *iters_out, float *rel_out,
                                   selr_stream stream) {
+    NvtxRange nvtx_range("selr_solve");
     if (!p || !Yv || !mask || !X_out || (resume != 0 && resume != 1) || (resume && !state_inout))
         return SELR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1128,6 +1149,7 @@ static cudaError_t unrolled_forward(selr_plan *p, const cf *Y, const uint8_t *ma
 extern "C" selr_status selr_solve_unrolled(selr_plan *p, const void *Y, const uint8_t *mask, void *X_out,
                                            const float *ts, const float *taus, int32_t n_iter, void *ckpt_K,
                                            void *ckpt_D, selr_stream stream) {
+    NvtxRange nvtx_range("selr_solve_unrolled");
     if (!p || !Y || !mask || !X_out || !ts || !taus || n_iter < 1) return SELR_ERR_INVALID_ARG;
     if (!p->model2d || p->spirit) return SELR_ERR_UNSUPPORTED;
     for (int k = 0; k < n_iter; ++k)
@@ -1248,6 +1270,7 @@ static selr_status grad_workspace(selr_plan *p) {
 extern "C" selr_status selr_svt_vjp(selr_plan *p, const void *A, const void *Zbar, int32_t nmat, int32_t rows,
                                     int32_t cols, float thresh, void *Abar, float *tbar, void *Z_out,
                                     selr_stream stream) {
+    NvtxRange nvtx_range("selr_svt_vjp");
     if (!p || !A || !Zbar || !Abar || !tbar || nmat < 1 || rows < 1 || cols < 1 || !(thresh >= 0.f) ||
         !isfinite(thresh))
         return SELR_ERR_INVALID_ARG;

@@ -2,10 +2,20 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stddef.h>
 
 #include "../../include/selr.h"
+
+// NVTX range for the lifetime of a scope (host side: API calls and the issue of each ADMM
+// stage, recorded once while a graph is captured); header-only NVTX, inert without a tool.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---------------------------------------------------------------- complex
 struct __align__(8) cf {
@@ -348,7 +358,7 @@ cudaError_t launch_fill(cf *p, long long n, cf v, cudaStream_t st);
 
 // spirit.cu: SPIRiT calibration and the CG X-update of SHLR-S / SHLR-SV
 #define SP_NB 304                 // CTAs of the CG kernels (fixed: deterministic partial sums)
-#define SELR_SPIRIT_SLOTS 4       // coil systems solved concurrently in the calibration
+#define SELR_SPIRIT_SLOTS 16      // coil systems solved concurrently in the calibration
 struct SpiritArgs {
     int J, M, N, ks, acs, cg_iters;
     long long nK;
@@ -359,9 +369,11 @@ struct SpiritArgs {
     cf *K;                        // iterate, overwritten by the X-update
     const cf *adjA, *adjB;        // transformed lift adjoints (k-space)
     cf *Gm;                       // [J][J][M][N] image-domain G - I
+    cf *Hm;                       // [J (J + 1) / 2][M][N] (G - I)^H (G - I), upper triangle per pixel
     cf *g;                        // [J][J][ks][ks] kernel
     float *cj;                    // [J] preconditioner constants
     cf *x, *r, *z, *p, *q, *t;    // CG vectors [J][M][N]
+    float *dv, *pdv;              // [J][M][N] diagonal of the operator and the preconditioner
     double *part;                 // [3][SP_NB]
     double *partial;              // [M][2] stopping-ratio partials
     unsigned *status;

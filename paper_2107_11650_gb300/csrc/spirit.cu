@@ -34,26 +34,37 @@ __device__ __forceinline__ double2 dmulc(double2 a, double2 b) {     // conj(a) 
 
 // ------------------------------------------------------------ calibration
 // C[q1][q2] = sum over kernel positions of conj(A[pos][q1]) A[pos][q2],
-// q = j' ks^2 + a ks + b <-> Y[j'][m + a - h][n + b - h].
+// q = j' ks^2 + a ks + b <-> Y[j'][m + a - h][n + b - h].  C is Hermitian: the entries
+// q2 <= q1 are summed (the products of two FP32 values are exact in the FP64 FMAs) and
+// mirrored, in two interleaved chains (even and odd n) added at the end.
 __global__ void __launch_bounds__(SP_GT) k_sp_gram(const cf *Y, int J, int M, int N, int ks, int r0, int r1,
                                                    double2 *C) {
     const int nu = J * ks * ks, h = ks / 2;
     const int q1 = blockIdx.x, q2 = blockIdx.y * SP_GT + threadIdx.x;
-    if (q2 >= nu) return;
+    if (q2 > q1 || q2 >= nu) return;
     const int j1 = q1 / (ks * ks), a1 = (q1 / ks) % ks, b1 = q1 % ks;
     const int j2 = q2 / (ks * ks), a2 = (q2 / ks) % ks, b2 = q2 % ks;
-    double2 acc = make_double2(0.0, 0.0);
+    double ar0 = 0.0, ai0 = 0.0, ar1 = 0.0, ai1 = 0.0;
     for (int m = r0 + h; m < r1 - h; ++m) {
         const cf *y1 = Y + ((long long)j1 * M + (m + a1 - h)) * N + (b1 - h);
         const cf *y2 = Y + ((long long)j2 * M + (m + a2 - h)) * N + (b2 - h);
-        for (int n = h; n < N - h; ++n) {
-            const double2 u = make_double2(y1[n].x, y1[n].y), v = make_double2(y2[n].x, y2[n].y);
-            const double2 p = dmulc(u, v);
-            acc.x += p.x;
-            acc.y += p.y;
+        int n = h;
+        for (; n + 1 < N - h; n += 2) {
+            const cf u0 = y1[n], v0 = y2[n], u1 = y1[n + 1], v1 = y2[n + 1];
+            ar0 = fma((double)u0.x, (double)v0.x, fma((double)u0.y, (double)v0.y, ar0));
+            ai0 = fma((double)u0.x, (double)v0.y, fma(-(double)u0.y, (double)v0.x, ai0));
+            ar1 = fma((double)u1.x, (double)v1.x, fma((double)u1.y, (double)v1.y, ar1));
+            ai1 = fma((double)u1.x, (double)v1.y, fma(-(double)u1.y, (double)v1.x, ai1));
+        }
+        if (n < N - h) {
+            const cf u0 = y1[n], v0 = y2[n];
+            ar0 = fma((double)u0.x, (double)v0.x, fma((double)u0.y, (double)v0.y, ar0));
+            ai0 = fma((double)u0.x, (double)v0.y, fma(-(double)u0.y, (double)v0.x, ai0));
         }
     }
+    const double2 acc = make_double2(ar0 + ar1, ai0 + ai1);
     C[(long long)q1 * nu + q2] = acc;
+    C[(long long)q2 * nu + q1] = make_double2(acc.x, -acc.y);
 }
 
 // One CTA per target coil j0 + blockIdx.x: S = C without (t, t) row/column
@@ -104,16 +115,18 @@ __global__ void __launch_bounds__(SP_ST) k_sp_solve(const double2 *C, int J, int
             S[(long long)r * ns + k] = make_double2(v.x / dk, v.y / dk);
         }
         __syncthreads();
-        const long long rem = ns - k - 1;
-        for (long long e = threadIdx.x; e < rem * rem; e += SP_ST) {
-            const int r = k + 1 + (int)(e / rem), c = k + 1 + (int)(e % rem);
-            if (c > r) continue;
-            const double2 lr = S[(long long)r * ns + k], lc = S[(long long)c * ns + k];
-            // S[r][c] -= L[r][k] conj(L[c][k])
-            double2 v = S[(long long)r * ns + c];
-            v.x -= lr.x * lc.x + lr.y * lc.y;
-            v.y -= lr.y * lc.x - lr.x * lc.y;
-            S[(long long)r * ns + c] = v;
+        // trailing lower triangle: warp per row r, lanes over its columns c <= r
+        for (int r = k + 1 + (int)(threadIdx.x >> 5); r < ns; r += SP_ST / 32) {
+            const double2 lr = S[(long long)r * ns + k];
+            double2 *Sr = S + (long long)r * ns;
+            for (int c = k + 1 + (int)(threadIdx.x & 31); c <= r; c += 32) {
+                const double2 lc = S[(long long)c * ns + k];
+                // S[r][c] -= L[r][k] conj(L[c][k])
+                double2 v = Sr[c];
+                v.x -= lr.x * lc.x + lr.y * lc.y;
+                v.y -= lr.y * lc.x - lr.x * lc.y;
+                Sr[c] = v;
+            }
         }
         __syncthreads();
     }
@@ -188,6 +201,8 @@ __global__ void k_sp_finish_g(cf *Gm, int J, int M, int N) {
     }
 }
 
+__global__ void k_sp_hpix(const cf *Gm, int J, long long MN, cf *Hm);
+
 static int sp_blocks(long long n) { return (int)min((n + SP_T - 1) / SP_T, (long long)SP_NB); }
 
 cudaError_t launch_spirit_calibrate(const SpiritArgs &s, const cf *Y, cudaStream_t st) {
@@ -207,32 +222,74 @@ cudaError_t launch_spirit_calibrate(const SpiritArgs &s, const cf *Y, cudaStream
     if ((e = launch_fft(s.Gm, s.Gm, s.ftN, (long long)s.J * s.J * s.M, 1, 0, st)) != cudaSuccess) return e;
     if ((e = launch_fft(s.Gm, s.Gm, s.ftM, (long long)s.J * s.J, s.N, 0, st)) != cudaSuccess) return e;
     k_sp_finish_g<<<sp_blocks(tot), SP_T, 0, st>>>(s.Gm, s.J, s.M, s.N);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long MN = (long long)s.M * s.N;
+    k_sp_hpix<<<(int)min((MN + 127) / 128, (long long)152 * 16), 128, 0, st>>>(s.Gm, s.J, MN, s.Hm);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ CG X-update
-// Every pixel: t <- Gm^H (Gm t) (J x J, both applied from registers).
-__global__ void __launch_bounds__(128) k_sp_pix(cf *t, const cf *Gm, int J, long long MN) {
+// Every pixel: H = (Ghat - I)^H (Ghat - I), the J x J Hermitian operator of the SPIRiT term in
+// the image domain, stored as its upper triangle (j1 <= j2, row by row) with pixels
+// contiguous: Hm[idx][pix], idx = 0 .. J (J + 1) / 2 - 1.  Once per calibration.
+__global__ void __launch_bounds__(128) k_sp_hpix(const cf *Gm, int J, long long MN, cf *Hm) {
     for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < MN; pix += (long long)gridDim.x * blockDim.x) {
-        cf v[SP_MAXJ], u[SP_MAXJ];
-        for (int j = 0; j < J; ++j) v[j] = t[(long long)j * MN + pix];
-        for (int j = 0; j < J; ++j) {
-            cf a = mk(0.f, 0.f);
-            for (int jp = 0; jp < J; ++jp) a = cadd(a, cmul(Gm[((long long)j * J + jp) * MN + pix], v[jp]));
-            u[j] = a;
-        }
-        for (int jp = 0; jp < J; ++jp) {
-            cf a = mk(0.f, 0.f);
-            for (int j = 0; j < J; ++j) a = cadd(a, cmulc(Gm[((long long)j * J + jp) * MN + pix], u[j]));
-            t[(long long)jp * MN + pix] = a;
-        }
+        long long idx = 0;
+        for (int j1 = 0; j1 < J; ++j1)
+            for (int j2 = j1; j2 < J; ++j2, ++idx) {
+                cf a = mk(0.f, 0.f);
+                for (int j = 0; j < J; ++j)
+                    a = cadd(a, cmulc(Gm[((long long)j * J + j1) * MN + pix], Gm[((long long)j * J + j2) * MN + pix]));
+                Hm[idx * MN + pix] = a;
+            }
     }
 }
 
-__device__ __forceinline__ float sp_diag(const SpiritArgs &s, long long i) {
-    const int n = (int)(i % s.N), m = (int)((i / s.N) % s.M);
-    const float u = s.mask[(long long)m * s.N + n] ? 1.f : 0.f;
-    return s.lambda * u + s.beta * (s.da[n] + s.db[m]);
+// Every pixel: t <- H t (J <= JM coils; the vectors in registers, each stored entry of H read
+// once: H[j1][j2] v[j2] into u[j1] and conj(H[j1][j2]) v[j1] into u[j2]).
+template <int JM>
+__global__ void __launch_bounds__(128) k_sp_pix(cf *t, const cf *Hm, int J, long long MN) {
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < MN; pix += (long long)gridDim.x * blockDim.x) {
+        cf v[JM], u[JM];
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+            v[j] = j < J ? t[(long long)j * MN + pix] : mk(0.f, 0.f);
+            u[j] = mk(0.f, 0.f);
+        }
+        const cf *h = Hm + pix;
+#pragma unroll
+        for (int j1 = 0; j1 < JM; ++j1) {
+            if (j1 < J) {
+#pragma unroll
+                for (int j2 = j1; j2 < JM; ++j2) {
+                    if (j2 < J) {
+                        const cf hv = *h;
+                        h += MN;
+                        u[j1] = cadd(u[j1], cmul(hv, v[j2]));
+                        if (j2 != j1) u[j2] = cadd(u[j2], cmulc(hv, v[j1]));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < JM; ++j)
+            if (j < J) t[(long long)j * MN + pix] = u[j];
+    }
+}
+
+// First kernel of an X-update: x = K (the CG starts from the previous iterate), and the
+// diagonals of this solve per element i = (j M + m) N + n: dv = lambda U + beta (d_r(n) + d_c(m))
+// and the preconditioner pdv = dv + lambda_1 c_j (32-bit index arithmetic: nK < 2^32).
+__global__ void __launch_bounds__(SP_T) k_sp_begin(SpiritArgs s) {
+    const unsigned MN = (unsigned)s.M * (unsigned)s.N;
+    for (long long i = blockIdx.x * (long long)SP_T + threadIdx.x; i < s.nK; i += (long long)SP_NB * SP_T) {
+        const unsigned ui = (unsigned)i, pix = ui % MN, j = ui / MN, m = pix / (unsigned)s.N;
+        const unsigned n = pix - m * (unsigned)s.N;
+        const float d = s.lambda * (s.mask[pix] ? 1.f : 0.f) + s.beta * (s.da[n] + s.db[m]);
+        s.dv[i] = d;
+        s.pdv[i] = d + s.lambda1 * s.cj[j];
+        s.x[i] = s.K[i];
+    }
 }
 
 // fixed-order sum of this CTA's values into part[blockIdx.x]
@@ -249,10 +306,19 @@ __device__ __forceinline__ void sp_partial(double v, double *part) {
     }
 }
 
-__device__ __forceinline__ double sp_sum(const double *part) {
-    double s = 0.0;
-    for (int k = 0; k < SP_NB; ++k) s += part[k];
-    return s;
+// Sum of the SP_NB per-CTA partials in one fixed order (lane l adds entries l, l + 32, ...,
+// then a butterfly whose partners add the same two values), formed once per CTA by warp 0
+// and broadcast through shared memory: every thread of every CTA gets the same bits.
+__device__ __forceinline__ double sp_block_sum(const double *part, double *slot) {
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int k = threadIdx.x; k < SP_NB; k += 32) v += part[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) *slot = v;
+    }
+    __syncthreads();
+    return *slot;
 }
 
 // q = diag v + lambda_1 t; optional partial of Re <v, q>.
@@ -260,7 +326,7 @@ __global__ void __launch_bounds__(SP_T) k_sp_combine(SpiritArgs s, const cf *v, 
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)SP_T + threadIdx.x; i < s.nK; i += (long long)SP_NB * SP_T) {
         const cf vi = v[i], ti = s.t[i];
-        const float d = sp_diag(s, i);
+        const float d = s.dv[i];
         const cf qi = mk(d * vi.x + s.lambda1 * ti.x, d * vi.y + s.lambda1 * ti.y);
         s.q[i] = qi;
         acc += (double)vi.x * qi.x + (double)vi.y * qi.y;
@@ -271,12 +337,12 @@ __global__ void __launch_bounds__(SP_T) k_sp_combine(SpiritArgs s, const cf *v, 
 // r = lambda U Y + beta (a + b) - q;  z = r / P;  p = z;  partial r.z
 __global__ void __launch_bounds__(SP_T) k_sp_init(SpiritArgs s, double *part) {
     double acc = 0.0;
+    const unsigned MN = (unsigned)s.M * (unsigned)s.N;
     for (long long i = blockIdx.x * (long long)SP_T + threadIdx.x; i < s.nK; i += (long long)SP_NB * SP_T) {
-        const int n = (int)(i % s.N), m = (int)((i / s.N) % s.M), j = (int)(i / ((long long)s.M * s.N));
-        const float u = s.mask[(long long)m * s.N + n] ? 1.f : 0.f;
+        const float u = s.mask[(unsigned)i % MN] ? 1.f : 0.f;
         const cf ab = cadd(s.adjA[i], s.adjB[i]), y = s.Y[i], qi = s.q[i];
         const cf ri = mk(s.lambda * u * y.x + s.beta * ab.x - qi.x, s.lambda * u * y.y + s.beta * ab.y - qi.y);
-        const float pd = sp_diag(s, i) + s.lambda1 * s.cj[j];
+        const float pd = s.pdv[i];
         const cf zi = mk(ri.x / pd, ri.y / pd);
         s.r[i] = ri;
         s.z[i] = zi;
@@ -289,16 +355,17 @@ __global__ void __launch_bounds__(SP_T) k_sp_init(SpiritArgs s, double *part) {
 // alpha = rz / pq;  x += alpha p;  r -= alpha q;  z = r / P;  partial of the new r.z
 __global__ void __launch_bounds__(SP_T) k_sp_update(SpiritArgs s, const double *rz_old, const double *pq,
                                                     double *rz_new) {
-    const double den = sp_sum(pq);
-    const float alpha = den != 0.0 ? (float)(sp_sum(rz_old) / den) : 0.f;
+    __shared__ double s_sums[2];
+    const double den = sp_block_sum(pq, &s_sums[0]);
+    const double num = sp_block_sum(rz_old, &s_sums[1]);
+    const float alpha = den != 0.0 ? (float)(num / den) : 0.f;
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)SP_T + threadIdx.x; i < s.nK; i += (long long)SP_NB * SP_T) {
-        const int j = (int)(i / ((long long)s.M * s.N));
         const cf pi = s.p[i], qi = s.q[i];
         cf xi = s.x[i], ri = s.r[i];
         xi = mk(xi.x + alpha * pi.x, xi.y + alpha * pi.y);
         ri = mk(ri.x - alpha * qi.x, ri.y - alpha * qi.y);
-        const float pd = sp_diag(s, i) + s.lambda1 * s.cj[j];
+        const float pd = s.pdv[i];
         const cf zi = mk(ri.x / pd, ri.y / pd);
         s.x[i] = xi;
         s.r[i] = ri;
@@ -310,17 +377,14 @@ __global__ void __launch_bounds__(SP_T) k_sp_update(SpiritArgs s, const double *
 
 // p = z + (rz_new / rz_old) p
 __global__ void __launch_bounds__(SP_T) k_sp_pupdate(SpiritArgs s, const double *rz_old, const double *rz_new) {
-    const double o = sp_sum(rz_old);
-    const float bcg = o != 0.0 ? (float)(sp_sum(rz_new) / o) : 0.f;
+    __shared__ double s_sums[2];
+    const double o = sp_block_sum(rz_old, &s_sums[0]);
+    const double nw = sp_block_sum(rz_new, &s_sums[1]);
+    const float bcg = o != 0.0 ? (float)(nw / o) : 0.f;
     for (long long i = blockIdx.x * (long long)SP_T + threadIdx.x; i < s.nK; i += (long long)SP_NB * SP_T) {
         const cf zi = s.z[i], pi = s.p[i];
         s.p[i] = mk(zi.x + bcg * pi.x, zi.y + bcg * pi.y);
     }
-}
-
-__global__ void k_sp_copy(const cf *a, cf *b, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = a[i];
 }
 
 // Per row m: ||x - K||^2 and ||K||^2 over (j, n) in a fixed order (the partials of
@@ -361,7 +425,11 @@ static cudaError_t sp_apply(const SpiritArgs &s, const cf *v, double *part, cuda
     if ((e = launch_fft(v, s.t, s.ftN, (long long)s.J * s.M, 1, 1, st)) != cudaSuccess) return e;
     if ((e = launch_fft(s.t, s.t, s.ftM, s.J, s.N, 1, st)) != cudaSuccess) return e;
     const long long MN = (long long)s.M * s.N;
-    k_sp_pix<<<(int)min((MN + 127) / 128, (long long)152 * 16), 128, 0, st>>>(s.t, s.Gm, s.J, MN);
+    const int nb = (int)min((MN + 127) / 128, (long long)152 * 16);
+    if (s.J <= 4) k_sp_pix<4><<<nb, 128, 0, st>>>(s.t, s.Hm, s.J, MN);
+    else if (s.J <= 8) k_sp_pix<8><<<nb, 128, 0, st>>>(s.t, s.Hm, s.J, MN);
+    else if (s.J <= 16) k_sp_pix<16><<<nb, 128, 0, st>>>(s.t, s.Hm, s.J, MN);
+    else k_sp_pix<SP_MAXJ><<<nb, 128, 0, st>>>(s.t, s.Hm, s.J, MN);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_fft(s.t, s.t, s.ftN, (long long)s.J * s.M, 1, 0, st)) != cudaSuccess) return e;
     if ((e = launch_fft(s.t, s.t, s.ftM, s.J, s.N, 0, st)) != cudaSuccess) return e;
@@ -372,7 +440,7 @@ static cudaError_t sp_apply(const SpiritArgs &s, const cf *v, double *part, cuda
 cudaError_t launch_spirit_x_update(const SpiritArgs &s, cudaStream_t st) {
     cudaError_t e;
     double *rz0 = s.part, *rz1 = s.part + SP_NB, *pq = s.part + 2 * SP_NB;
-    k_sp_copy<<<sp_blocks(s.nK), SP_T, 0, st>>>(s.K, s.x, s.nK);
+    k_sp_begin<<<SP_NB, SP_T, 0, st>>>(s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = sp_apply(s, s.x, nullptr, st)) != cudaSuccess) return e;
     k_sp_init<<<SP_NB, SP_T, 0, st>>>(s, rz0);
