@@ -853,6 +853,27 @@ def run_quality(args):
     plan.close()
 
 
+def run_iteration_log(args):
+    """--steps iterations of --config, one JSON line per iteration (paper_2107_11650_gb300.iterlog)."""
+    import torch
+    from paper_2107_11650_gb300 import api, iterlog
+    from paper_2107_11650_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+    wl = synth.get_config(args.config)
+    inp = synth.make_inputs(wl)
+    Y = torch.from_numpy(inp["Y"].astype(np.complex64)).cuda()
+    mask = torch.from_numpy(inp["mask"].astype(np.uint8)).cuda()
+    model2d = wl.model in ("SHLR", "SHLR_V", "SHLR_S", "SHLR_SV")
+    plan = api.Plan(api.Desc.from_workload(wl, svd=args.svd, gram=gram_for(args, model2d)))
+    X = torch.empty_like(Y)
+    stream = torch.cuda.Stream()
+    recs = iterlog.run_logged(plan, Y, mask, X, args.steps, args.iteration_log, stream=stream)
+    print(json.dumps({"iteration_log": args.iteration_log, "workload": wl.name, "iterations": len(recs),
+                      "last": recs[-1]}))
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -870,6 +891,9 @@ def main():
     ap.add_argument("--allow-tf32", action="store_true")
     ap.add_argument("--quality", action="store_true",
                     help="reconstruction-quality experiments (RLNE / MSSIM / T2) instead of the throughput line")
+    ap.add_argument("--iteration-log", default=None, metavar="PATH",
+                    help="write a per-iteration JSONL log of --steps iterations of --config to PATH "
+                         "instead of the throughput line")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -884,6 +908,10 @@ def main():
     if args.quality:
         if rank == 0:
             run_quality(args)
+        return
+    if args.iteration_log:
+        if rank == 0:
+            run_iteration_log(args)
         return
     if args.config == "unrolled_16_uneven":
         run_unrolled(args, rank, world)
