@@ -330,6 +330,7 @@ def work_model(plan, model2d, svd, rank_sums, stages):
     fams = ("row", "col") if model2d else ("pe", "param")
     tot = {"gram": 0.0, "tridiag": 0.0, "eigvec": 0.0, "apply": 0.0, "small_svt": 0.0}
     ranks = {}
+    eig_shapes = []
     m0 = 0
     for ax in fams:
         nm_, r_, c_ = plan.lift_shape(ax)
@@ -344,13 +345,28 @@ def work_model(plan, model2d, svd, rank_sums, stages):
                 sums, it = rank_sums
                 rbar = float(sums[m0:m0 + nm_].sum()) / max(it * nm_, 1)
             ranks[ax] = rbar
+            eig_shapes.append((nm_, s))
             for k, v in method_flops(l, s, rbar).items():
                 tot[k] += nm_ * v
         m0 += nm_
     st_ = stages
     ms_svd = st_["svd"][0] / max(st_["svd"][1], 1)
     return dict(ms=ms_svd, flops=tot["tridiag"] + tot["eigvec"], stage="svd", flops_by_kind=tot, mean_rank=ranks,
-                bytes=step_bytes(plan, model2d))
+                bytes=step_bytes(plan, model2d), eig_shapes=eig_shapes)
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per matrix of k_tridiag + k_eigvec,
+# by order s, from one full-size ncu capture of each kernel on the 12-coil 256x256 workload
+# (k_tridiag 75.9 + 19.4 MB, k_eigvec 77.6 + 1.8 MB per launch of 512 matrices): the packed
+# Gram read once, the Householder vectors written once and read once.  Orders without a
+# capture report no traffic.
+NCU_SVD_BYTES_PER_MATRIX = {192: (75.9e6 + 19.4e6 + 77.6e6 + 1.8e6) / 512}
+
+
+def svd_traffic(eig_shapes):
+    if not eig_shapes or any(s not in NCU_SVD_BYTES_PER_MATRIX for _, s in eig_shapes):
+        return None
+    return sum(nm * NCU_SVD_BYTES_PER_MATRIX[s] for nm, s in eig_shapes)
 
 
 def accuracy_vs_oracle(plan, wl, Y, mask, stream):
@@ -966,7 +982,9 @@ def main():
                                 "k_tridiag + k_eigvec (Householder tridiagonalisation, multisection, inverse "
                                 "iteration and back-transformation of the pairs above t^2)"),
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": None, "peak_source": fp32_src,
+                     "traffic": svd_traffic(jac.get("eig_shapes")) if args.svd == "eig" else None,
+                     "traffic_unit": "bytes per launch (ncu capture of the same kernels, scaled per matrix)",
+                     "peak_source": fp32_src,
                      "flops_per_launch": jac["flops"], "launch_ms": jac["ms"],
                      "flop_model": "(16/3) s^3 + (8 s^2 + 1626 s) r per matrix, r = mean rank over the timed "
                                    "iterations", "mean_rank": jac["mean_rank"]},

@@ -62,3 +62,10 @@ def test_spirit_models_count_the_cg_x_update_and_the_calibration():
     # calibration once per solve: Gram, 3 Cholesky launches (4 coils each), place, 2 FFTs, finish
     assert bench.calibration_launches(p) == 5 + 3
     assert bench.calibration_launches(_Plan(fams, _Desc("SHLR"))) == 0
+
+
+def test_svd_traffic_scales_the_captured_bytes_per_matrix():
+    # the full-size capture of k_tridiag + k_eigvec at order 192 covers 512 matrices
+    assert abs(bench.svd_traffic([(256, 192), (256, 192)]) - (75.9e6 + 19.4e6 + 77.6e6 + 1.8e6)) < 1.0
+    assert bench.svd_traffic([(256, 241)]) is None
+    assert bench.svd_traffic([]) is None
