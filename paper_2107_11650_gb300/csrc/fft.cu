@@ -177,10 +177,110 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft(const cf *in, cf *out, FftT
     }
 }
 
+// ---- compile-time lengths: the same transform with the radix schedule, the strides and every
+// index division fixed at compile time (the lengths of the workloads; others use k_fft).
+__host__ __device__ constexpr int fft_radix_at(int n, int s) {
+    const int order[4] = {4, 2, 3, 5};
+    int m = n, k = 0;
+    for (int oi = 0; oi < 4; ++oi)
+        while (m % order[oi] == 0) {
+            if (k == s) return order[oi];
+            ++k;
+            m /= order[oi];
+        }
+    return 0;
+}
+__host__ __device__ constexpr int fft_nstages(int n) {
+    int k = 0;
+    while (fft_radix_at(n, k) != 0) ++k;
+    return k;
+}
+
+template <int N, int R, int NS>
+__device__ __forceinline__ void stockham_stage_c(const cf *src, cf *dst, const cf *tw, int inverse) {
+    constexpr int nb = N / R, tstep0 = N / (NS * R), ld = N + 1;
+    for (int idx = threadIdx.x; idx < FFT_V * nb; idx += FFT_THREADS) {
+        const int t = idx / nb, j = idx - t * nb;
+        const int k = j % NS;
+        cf v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cf x = src[t * ld + j + r * nb];
+            if (r > 0 && k > 0) {
+                cf w = tw[r * k * tstep0];
+                if (inverse) w = cconj(w);
+                x = cmul(x, w);
+            }
+            v[r] = x;
+        }
+        small_dft<R>(v, inverse);
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[t * ld + base + r * NS] = v[r];
+    }
+}
+
+// Stages S.. of length N (NS = product of the radices before S); returns the buffer that holds
+// the result.
+template <int N, int S, int NS>
+__device__ __forceinline__ cf *fft_stages(cf *src, cf *dst, const cf *tw, int inverse) {
+    if constexpr (S < fft_nstages(N)) {
+        constexpr int R = fft_radix_at(N, S);
+        stockham_stage_c<N, R, NS>(src, dst, tw, inverse);
+        __syncthreads();
+        return fft_stages<N, S + 1, NS * R>(dst, src, tw, inverse);
+    } else {
+        return src;
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_n(const cf *in, cf *out, const cf *tw, unsigned nvec,
+                                                       unsigned inner, int inverse) {
+    extern __shared__ cf fsm[];
+    constexpr int ld = N + 1;
+    cf *bufA = fsm, *bufB = fsm + FFT_V * ld;
+    const unsigned v0 = blockIdx.x * FFT_V;
+    const float post = ((N >> 1) & 1 ? -1.f : 1.f) * rsqrtf((float)N);
+    for (int idx = threadIdx.x; idx < FFT_V * N; idx += FFT_THREADS) {
+        int tv, k;
+        if (inner == 1) { tv = idx / N; k = idx - tv * N; }
+        else { k = idx / FFT_V; tv = idx - k * FFT_V; }
+        const unsigned v = v0 + tv;
+        cf x = mk(0.f, 0.f);
+        if (v < nvec) {
+            const unsigned o = v / inner, i = v - o * inner;
+            x = in[((long long)o * N + k) * inner + i];
+        }
+        if (k & 1) x = mk(-x.x, -x.y);
+        bufA[tv * ld + k] = x;
+    }
+    __syncthreads();
+    const cf *res = fft_stages<N, 0, 1>(bufA, bufB, tw, inverse);
+    for (int idx = threadIdx.x; idx < FFT_V * N; idx += FFT_THREADS) {
+        int tv, k;
+        if (inner == 1) { tv = idx / N; k = idx - tv * N; }
+        else { k = idx / FFT_V; tv = idx - k * FFT_V; }
+        const unsigned v = v0 + tv;
+        if (v < nvec) {
+            const unsigned o = v / inner, i = v - o * inner;
+            const float sc = (k & 1) ? -post : post;
+            out[((long long)o * N + k) * inner + i] = cscale(res[tv * ld + k], sc);
+        }
+    }
+}
+
+#define FFT_SIZES(X) X(64) X(128) X(160) X(192) X(240) X(256) X(288) X(320) X(384) X(480) X(512)
+
 // Called once per process before the first launch (plan creation).
 cudaError_t fft_init_attributes() {
-    return cudaFuncSetAttribute(k_fft, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(cf) * 2 * FFT_V * (FFT_MAX_N + 1)));
+    const int mx = (int)(sizeof(cf) * 2 * FFT_V * (FFT_MAX_N + 1));
+    cudaError_t e = cudaFuncSetAttribute(k_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+#define FFT_ATTR(n) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_n<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    FFT_SIZES(FFT_ATTR)
+#undef FFT_ATTR
+    return e;
 }
 
 cudaError_t launch_fft(const cf *in, cf *out, const FftTable &t, long long outer, long long inner,
@@ -189,6 +289,19 @@ cudaError_t launch_fft(const cf *in, cf *out, const FftTable &t, long long outer
     if (nvec == 0) return cudaSuccess;
     const size_t smem = sizeof(cf) * 2 * FFT_V * (t.n + 1);
     const long long grid = (nvec + FFT_V - 1) / FFT_V;
+    if (nvec < (1ll << 31) && inner < (1ll << 31)) {
+        switch (t.n) {
+#define FFT_CASE(n) \
+            case n: \
+                k_fft_n<n><<<(unsigned)grid, FFT_THREADS, smem, st>>>(in, out, t.tw, (unsigned)nvec, (unsigned)inner, \
+                                                                      inverse); \
+                return cudaGetLastError();
+            FFT_SIZES(FFT_CASE)
+#undef FFT_CASE
+            default:
+                break;
+        }
+    }
     k_fft<<<(unsigned)grid, FFT_THREADS, smem, st>>>(in, out, t, outer, inner, inverse);
     return cudaGetLastError();
 }
