@@ -270,7 +270,10 @@ def run_gpu(args, rank, world):
         with torch.cuda.stream(stream):
             api.selr_solve(plan, Y, mask, X, stream=stream)           # W warm-up iterations
         st = api.selr_sync_status(plan, stream)
-        if mode == "batched" and not args.no_autotune:
+        if mode == "batched" and args.ev_chunk:
+            plan.set_tuning(plan.desc.gram, args.ev_chunk)
+            results["tuning"] = plan.tuning()
+        elif mode == "batched" and not args.no_autotune:
             with torch.cuda.stream(stream):
                 results["tuning"] = plan.autotune(Y, mask, allow_tf32=args.allow_tf32, stream=stream)
         steps = args.steps if mode == "batched" else max(1, min(args.steps, args.plain_steps))
@@ -904,6 +907,8 @@ def main():
                     help="Gram precision before autotuning (default: 3xtf32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--ev-chunk", type=int, default=0, choices=[0, 8, 16],
+                    help="eigenvectors per k_eigvec pass (replaces the autotuner; 0: autotune)")
     ap.add_argument("--allow-tf32", action="store_true")
     ap.add_argument("--quality", action="store_true",
                     help="reconstruction-quality experiments (RLNE / MSSIM / T2) instead of the throughput line")

@@ -381,6 +381,12 @@ selr_status selr_plan_autotune(selr_plan *plan, const void *Y, const uint8_t *ma
 selr_status selr_plan_tuning(const selr_plan *plan, int32_t *gram_precision, int32_t *ev_chunk,
                              int32_t *jacobi_max_sweeps);
 
+/* Sets what the autotuner would: the Gram precision (any SELR_GRAM_* mode) and the number
+ * of eigenvectors refined per inverse-iteration pass (8 or 16; 0 = chosen by order; 16 falls
+ * back to 8 for orders whose 16-vector layout exceeds shared memory).  Cached CUDA graphs
+ * are dropped.  SELR_ERR_INVALID_ARG for other values. */
+selr_status selr_plan_set_tuning(selr_plan *plan, int32_t gram_precision, int32_t ev_chunk);
+
 /* Change the iteration cap and stopping tolerance of an existing plan
  * (same meaning as selr_desc.max_iter / tol).  SELR_ERR_INVALID_ARG if
  * max_iter < 1. */

@@ -145,6 +145,11 @@ class Plan:
         names = {v: k for k, v in GRAM.items()}
         return {"gram": names.get(g.value, g.value), "ev_chunk": c.value, "jacobi_max_sweeps": w.value}
 
+    def set_tuning(self, gram, ev_chunk=0):
+        """selr_plan_set_tuning: Gram mode (name as in Desc) and eigenvectors per pass (0, 8, 16)."""
+        check(self.lib.selr_plan_set_tuning(self.handle, GRAM[gram], int(ev_chunk)), "selr_plan_set_tuning")
+        self.desc.gram = gram
+
     STAGES = ("adjoint", "dc", "hybrid_fft", "lift", "gram", "svd", "apply")
 
     def profile(self, on=True):

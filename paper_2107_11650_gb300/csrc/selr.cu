@@ -1507,6 +1507,18 @@ extern "C" selr_status selr_plan_tuning(const selr_plan *p, int32_t *gram_precis
     return SELR_OK;
 }
 
+extern "C" selr_status selr_plan_set_tuning(selr_plan *p, int32_t gram_precision, int32_t ev_chunk) {
+    if (!p) return SELR_ERR_INVALID_ARG;
+    if (gram_precision != SELR_GRAM_FP32 && gram_precision != SELR_GRAM_TF32 && gram_precision != SELR_GRAM_3XTF32 &&
+        gram_precision != SELR_GRAM_BF16X3 && gram_precision != SELR_GRAM_BF16X6)
+        return SELR_ERR_INVALID_ARG;
+    if (ev_chunk != 0 && ev_chunk != 8 && ev_chunk != 16) return SELR_ERR_INVALID_ARG;
+    p->d.gram_precision = gram_precision;
+    p->ev_chunk = ev_chunk;
+    drop_graphs(p);
+    return SELR_OK;
+}
+
 extern "C" selr_status selr_set_iterations(selr_plan *p, int32_t max_iter, float tol) {
     if (!p || max_iter < 1 || !isfinite(tol)) return SELR_ERR_INVALID_ARG;
     p->d.max_iter = max_iter;

@@ -128,3 +128,4 @@ def test_null_arguments(lib):
     assert lib.selr_max(None, 1, None, None) == 1
     te = (ctypes.c_float * 1)(1.0)
     assert lib.selr_t2_fit(None, te, 1, 1, 1.0, 10.0, None, None, None) == 1
+    assert lib.selr_plan_set_tuning(None, 0, 16) == 1
