@@ -266,6 +266,8 @@ def run_gpu(args, rank, world):
     for mode in modes:
         plan = api.Plan(api.Desc.from_workload(wl, exec=mode, max_iter=max(args.warmup, 1), svd=args.svd,
                                                gram=gram_for(args, model2d)))
+        if args.reduction:
+            plan.set_reduction(args.reduction)
         nmat = sum(plan.lift_shape(a)[0] for a in (("row", "col") if model2d else ("pe", "param")))
         with torch.cuda.stream(stream):
             api.selr_solve(plan, Y, mask, X, stream=stream)           # W warm-up iterations
@@ -907,6 +909,8 @@ def main():
                     help="Gram precision before autotuning (default: 3xtf32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--reduction", type=int, default=0, choices=[0, 1, 2],
+                    help="Householder reduction: 0 by order, 1 one-stage, 2 two-stage where the order allows")
     ap.add_argument("--ev-chunk", type=int, default=0, choices=[0, 8, 16],
                     help="eigenvectors per k_eigvec pass (replaces the autotuner; 0: autotune)")
     ap.add_argument("--allow-tf32", action="store_true")

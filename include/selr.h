@@ -387,6 +387,14 @@ selr_status selr_plan_tuning(const selr_plan *plan, int32_t *gram_precision, int
  * are dropped.  SELR_ERR_INVALID_ARG for other values. */
 selr_status selr_plan_set_tuning(selr_plan *plan, int32_t gram_precision, int32_t ev_chunk);
 
+/* Householder reduction of the Gram matrices (SELR_SVD_EIG): 0 = chosen by order, 1 = the
+ * one-stage reduction to tridiagonal form for every order, 2 = the two-stage reduction
+ * (Hermitian band of half-bandwidth 16 by blocked reflectors, then bulge chasing to
+ * tridiagonal form) wherever the order is within 48 .. 192.  Both compute the same
+ * eigenpairs to FP32 accuracy; the reverse-mode SVT derivative always uses the one-stage
+ * reduction.  Cached CUDA graphs are dropped.  SELR_ERR_INVALID_ARG for other modes. */
+selr_status selr_plan_set_reduction(selr_plan *plan, int32_t mode);
+
 /* Change the iteration cap and stopping tolerance of an existing plan
  * (same meaning as selr_desc.max_iter / tol).  SELR_ERR_INVALID_ARG if
  * max_iter < 1. */

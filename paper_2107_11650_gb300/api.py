@@ -150,6 +150,10 @@ class Plan:
         check(self.lib.selr_plan_set_tuning(self.handle, GRAM[gram], int(ev_chunk)), "selr_plan_set_tuning")
         self.desc.gram = gram
 
+    def set_reduction(self, mode):
+        """selr_plan_set_reduction: 0 by order, 1 one-stage, 2 two-stage (orders 48 .. 192)."""
+        check(self.lib.selr_plan_set_reduction(self.handle, int(mode)), "selr_plan_set_reduction")
+
     STAGES = ("adjoint", "dc", "hybrid_fft", "lift", "gram", "svd", "apply")
 
     def profile(self, on=True):

@@ -46,6 +46,10 @@ struct selr_plan {
     double *sp_part;
     double2 *sp_C, *sp_work;
     unsigned *gready, *ready, *vready;   // kernel hand-off flags, one per matrix (see EigArgs)
+    unsigned *bready;                    // k_sb1 -> k_sb2 hand-off flags (two-stage reduction)
+    cf *sb;                              // two-stage reduction scratch (gs.sb_total elements)
+    long long sb_elems;
+    int reduction;                       // 0 by order, 1 one-stage, 2 two-stage (EigArgs)
     unsigned long long *rank_acc;        // per-matrix sum of eigensolver ranks over the last solve
     void *f64work;                       // FP64 re-solve slots (SELR_FP64_SLOTS x f64slot double2)
     long long f64slot;
@@ -180,7 +184,7 @@ static Group make_group(int kind, int nmat, int nv, int p, int J, int vc, int M,
 }
 
 static void finish_set(GroupSet *gs) {
-    long long off = 0, soff = 0, poff = 0;
+    long long off = 0, soff = 0, poff = 0, sboff = 0;
     int moff = 0;
     gs->start[0] = 0;
     for (int k = 0; k < gs->n; ++k) {
@@ -188,6 +192,11 @@ static void finish_set(GroupSet *gs) {
         gs->g[k].soff = soff;
         gs->g[k].poff = poff;
         gs->g[k].moff = moff;
+        gs->g[k].sboff = -1;
+        if (sb_eligible(gs->g[k].s)) {
+            gs->g[k].sboff = sboff;
+            sboff += (long long)gs->g[k].nmat * sb_stride(gs->g[k].s);
+        }
         poff += (long long)gs->g[k].nmat * gs->g[k].s * (gs->g[k].s + 1) / 2;
         off += (long long)gs->g[k].nmat * gs->g[k].rows * gs->g[k].cols;
         soff += (long long)gs->g[k].nmat * gs->g[k].s;
@@ -195,6 +204,7 @@ static void finish_set(GroupSet *gs) {
         gs->start[k + 1] = moff;
     }
     gs->total = moff;
+    gs->sb_total = sboff;
 }
 
 static selr_status validate(const selr_desc *d) {
@@ -298,7 +308,7 @@ extern "C" selr_status selr_plan_destroy(selr_plan *p) {
     for (void *b : gbufs)
         if (b) cudaFree(b);
     void *bufs[] = {p->K, p->hybA, p->hybB, p->adjA, p->adjB, p->D, p->E, p->W, p->B0, p->Gp, p->V, p->lam, p->tri,
-                    p->rank, p->gready, p->ready, p->vready, p->rank_acc, p->f64work, p->sp_Gm, p->sp_g,
+                    p->rank, p->gready, p->ready, p->vready, p->bready, p->sb, p->rank_acc, p->f64work, p->sp_Gm, p->sp_g,
                     p->sp_vec, p->sp_Hm, p->sp_cj, p->sp_diag, p->sp_part, p->sp_C, p->sp_work, p->sigma,
                     p->mat_status, p->partial, p->rel, p->active, p->active_next, p->status};
     for (void *b : bufs)
@@ -451,6 +461,11 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
         AL(p->gready, sizeof(unsigned) * (size_t)gs.total);
         AL(p->ready, sizeof(unsigned) * (size_t)gs.total);
         AL(p->vready, sizeof(unsigned) * (size_t)gs.total);
+        if (gs.sb_total > 0) {
+            AL(p->bready, sizeof(unsigned) * (size_t)gs.total);
+            AL(p->sb, sizeof(cf) * (size_t)gs.sb_total);
+            p->sb_elems = gs.sb_total;
+        }
         AL(p->rank_acc, sizeof(unsigned long long) * (size_t)gs.total);
         if (d->fp64_fallback) {
             long long mx = 0;
@@ -490,7 +505,8 @@ static selr_status create_plan(const selr_desc *ds, int n_inst, selr_plan **out)
     if (cudaMemset(p->status, 0, sizeof(unsigned)) != cudaSuccess ||
         (p->ready && (cudaMemset(p->gready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess ||
                       cudaMemset(p->ready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess ||
-                      cudaMemset(p->vready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess))) {
+                      cudaMemset(p->vready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess ||
+                      (p->bready && cudaMemset(p->bready, 0, sizeof(unsigned) * (size_t)gs.total) != cudaSuccess)))) {
         selr_plan_destroy(p);
         return SELR_ERR_CUDA;
     }
@@ -667,6 +683,9 @@ static EigArgs eig_args(selr_plan *p, const int *active) {
     e.ev_chunk = p->ev_chunk;
     e.ready = p->ready;
     e.vready = p->vready;
+    e.bready = p->bready;
+    e.sb = p->sb;
+    e.reduction = p->reduction;
     return e;
 }
 
@@ -708,6 +727,7 @@ static cudaError_t svd_apply(selr_plan *p, const GroupSet &gs, int m0, int mc, c
                 ea.gready = tc ? p->gready : nullptr;
                 ea.rank_acc = a.mode == 1 ? p->rank_acc : nullptr;    // ADMM iterations only
                 ea.fp64_fallback = p->f64work != nullptr;
+                if (gs.sb_total > p->sb_elems) ea.sb = nullptr;         // scratch too small: one-stage
                 if (part & 1)
                     e = tc ? launch_gram_tc(v, lb, lc, p->B0, p->Gp, a.active, (int)p->d.gram_precision, p->status,
                                             p->gready, st)
@@ -1515,6 +1535,13 @@ extern "C" selr_status selr_plan_set_tuning(selr_plan *p, int32_t gram_precision
     if (ev_chunk != 0 && ev_chunk != 8 && ev_chunk != 16) return SELR_ERR_INVALID_ARG;
     p->d.gram_precision = gram_precision;
     p->ev_chunk = ev_chunk;
+    drop_graphs(p);
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_plan_set_reduction(selr_plan *p, int32_t mode) {
+    if (!p || mode < 0 || mode > 2) return SELR_ERR_INVALID_ARG;
+    p->reduction = mode;
     drop_graphs(p);
     return SELR_OK;
 }

@@ -56,6 +56,8 @@ struct Group {
     long long soff;        // offset of matrix 0 in per-vector arrays (sigma)
     long long poff;        // offset of matrix 0 in packed Gram storage (s (s+1) / 2 per matrix)
     int moff;              // index of matrix 0 among all matrices (status words)
+    long long sboff;       // offset of matrix 0 in the two-stage reduction scratch, -1: no
+                           // scratch (order outside [SB_NMIN, SB_NMAX])
     int inst;              // instance of a batched plan the family belongs to
     int aoff;              // offset of the instance's FE positions in the activity flags
     const cf *w;           // weights (length nv) or nullptr (identity)
@@ -66,6 +68,7 @@ struct Group {
 struct GroupSet {
     int n;
     int total;                       // total matrices
+    long long sb_total;              // elements of two-stage reduction scratch the set needs
     int start[SELR_MAX_GROUPS + 1];  // prefix sums of nmat
     Group g[SELR_MAX_GROUPS];
 };
@@ -272,6 +275,30 @@ bool svt_small_fits(const Group &g);
 cudaError_t launch_svt_small(const GroupSet &gs, int mat_begin, int mat_count, const SvtArgs &a, cudaStream_t st);
 
 // svt_eig.cu
+// Two-stage Householder reduction (svt_eig.cu): G -> Hermitian band of half-bandwidth SB_B
+// (blocked panels, k_sb1) -> tridiagonal (bulge chasing, k_sb2), for orders in
+// [SB_NMIN, SB_NMAX].  Per matrix the scratch holds the band ([n][SB_B + 1]) and the
+// bulge-chasing reflectors, sweep-major: sweep j (j = 0 .. n-3) has sb_nsteps(n, j)
+// reflectors, each stored as SB_B + 1 complex values (tau and its first row, then v).
+#define SB_B 16
+#define SB_NMIN 48
+#define SB_NMAX 192
+__host__ __device__ inline int sb_nsteps(int n, int j) { return (n - 3 - j) / SB_B + 1; }
+// sum of floor(u / SB_B) over u = 0 .. U (0 for U < 0)
+__host__ __device__ inline long long sb_fsum(long long U) {
+    if (U < 0) return 0;
+    const long long q = (U + 1) / SB_B, r = (U + 1) % SB_B;
+    return (long long)SB_B * q * (q - 1) / 2 + q * r;
+}
+// reflectors of the sweeps before sweep j: sum of sb_nsteps(n, j') over j' < j
+__host__ __device__ inline long long sb_sweep_off(int n, int j) {
+    return j + sb_fsum(n - 3) - sb_fsum(n - 3 - j);
+}
+__host__ __device__ inline long long sb_stride(int n) {
+    return (long long)n * (SB_B + 1) + sb_sweep_off(n, n - 2) * (SB_B + 1);
+}
+__host__ __device__ inline bool sb_eligible(int n) { return n >= SB_NMIN && n <= SB_NMAX; }
+
 struct EigArgs {
     const cf *B0;
     cf *Gp;              // packed G in, Householder vectors out (offset g.poff per group)
@@ -291,6 +318,12 @@ struct EigArgs {
     unsigned *vready;    // k_eigvec -> k_apply_stream / k_apply_eig
     unsigned long long *rank_acc;   // [mat] running sum of ranks over a solve, or null
     int fp64_fallback;   // flag near-degenerate matrices (rank -1) for the FP64 re-solve
+    // two-stage reduction: scratch of GroupSet::sb_total elements (Group::sboff), or null;
+    // reduction 0 = by order, 1 = one-stage only, 2 = two-stage wherever the order allows
+    cf *sb;
+    int reduction;
+    unsigned *bready;    // k_sb1 -> k_sb2 (with gready / ready; null with plain launches)
+    int band;            // set by launch_heig: k_eigvec back-transforms through the two stages
 };
 cudaError_t eig_init_attributes();
 cudaError_t launch_gram(const GroupSet &gs, int mat_begin, int mat_count, const cf *B0, cf *Gp,

@@ -747,6 +747,574 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
     publish_flag(flag_of(a.ready, g, mat));
 }
 
+// ------------------------------------------- two-stage reduction (orders SB_NMIN .. SB_NMAX)
+// The one-stage reduction above is a chain of n - 2 dependent Householder steps, each with
+// block-wide reductions and a pass over the whole trailing matrix.  The two-stage form
+// reduces G first to a Hermitian band of half-bandwidth b = SB_B with blocked reflectors
+// (about n / b dependent panel steps; the trailing updates are rank-2b products with b-fold
+// reuse of every loaded element), then the band to tridiagonal by bulge chasing.
+//
+// Stage 1, k_sb1 (one CTA per matrix, packed G in shared memory).  For the panel of columns
+// c0 .. c0 + b - 1 and rows r0 = c0 + b .. n - 1 (m = n - r0 rows):
+//   QR of the panel: nr = min(b, m - 1) reflectors H_t = I - tau_t v_t v_t^H, one warp per
+//     panel column, one barrier per reflector (Q = H_0 ... H_{nr-1} = I - V T V^H);
+//   T by the forward recurrence T_tt = tau_t, T[0:t, t] = -tau_t T[0:t, 0:t] (V^H v_t)[0:t];
+//   trailing update A <- Q^H A Q on rows / columns r0 .. n - 1 as
+//     Y = V T,  X = A Y,  M = Y^H X,  W = X - V M / 2,  A <- A - W V^H - V W^H.
+// The band (diagonals 0 .. b) goes to the scratch, the reflectors to the packed buffer (column c
+// holds v of the panel reflector of that column on rows c + b .. n - 1) and tau_c to the tau
+// slots of the tridiagonal data.
+//
+// Stage 2, k_sb2 (one CTA of four warps per matrix, the band with room for the bulge in
+// shared memory).  Sweep j (j = 0 .. n - 3) has steps k = 1 .. sb_nsteps(n, j): step 1
+// annihilates column j below its first sub-diagonal with a reflector on rows j + 1 .. j + b;
+// step k > 1 annihilates the first column of the bulge the previous step left below the band
+// (column j + 1 + (k - 2) b) on rows j + 1 + (k - 1) b .. j + k b.  Each reflector is applied
+// from the left to the columns between that column and its window, from both sides to the
+// window's diagonal block and from the right to the b rows below the window.  Step k of sweep
+// j runs at time 3 j + k: the steps that share a time touch disjoint entries, and every entry
+// a step reads was last written by a step of an earlier time, so one warp per step with a
+// barrier per time gives the same matrix as the sweeps run one after the other.  The
+// reflectors are stored sweep-major; the tridiagonal d, e goes to the tridiagonal data.
+//
+// Back-transformation (k_eigvec with EigArgs::band): y = Q1 Q2 P z; Q2 = S_0 S_1 ... S_{n-3}
+// with S_j the product of the (commuting: disjoint windows) reflectors of sweep j, applied for
+// j = n - 3 .. 0; then the panel reflectors, as the one-stage reflectors with their first row
+// b - 1 rows further down.
+
+#define SB_AUTO_MIN (1 << 30)     // by order: the two-stage reduction from this order up
+#define SB1_THREADS 512
+#define SB1_RPL 6                  // panel rows per lane: n - SB_B <= 32 SB1_RPL for n <= SB_NMAX
+
+struct Sb1Layout {
+    size_t gs, vd, xs, ys, sm, tm, mm, total;
+};
+__host__ __device__ inline Sb1Layout sb1_layout(int n) {
+    Sb1Layout L;
+    const size_t mm = (size_t)(n > SB_B ? n - SB_B : 1);
+    size_t o = 0;
+    L.gs = o; o += al16((size_t)n * (n + 1) / 2 * 8);
+    L.vd = o; o += al16(mm * SB_B * 8);
+    L.xs = o; o += al16(mm * SB_B * 8);
+    L.ys = o; o += al16(mm * SB_B * 8);
+    L.sm = o; o += SB_B * SB_B * 8;
+    L.tm = o; o += SB_B * SB_B * 8;
+    L.mm = o; o += SB_B * SB_B * 8;
+    L.total = o;
+    return L;
+}
+
+// Householder reflector of x (this warp's entries xs[q] at local rows lane + 32 q, rows < t0
+// excluded, x0 on local row t0 < 32, in lane t0 slot 0): (I - tau v v^H) x = alpha e1 with
+// v0 = phs (|x0| + ||x||) and v = x below; tau = 0 when the column is already reduced.
+__device__ __forceinline__ void sb_reflector(float xn2, cf x0, float floor2, float *tau, cf *alpha, cf *v0) {
+    const float ax0 = sqrtf(cabs2(x0));
+    const float rest = xn2 - ax0 * ax0;
+    *tau = 0.f;
+    *alpha = x0;
+    *v0 = mk(0.f, 0.f);
+    if (rest > 1e-30f * xn2 && xn2 > floor2) {
+        const float xnorm = sqrtf(xn2);
+        const cf phs = ax0 > 0.f ? mk(x0.x / ax0, x0.y / ax0) : mk(1.f, 0.f);
+        *alpha = mk(-phs.x * xnorm, -phs.y * xnorm);
+        *tau = 1.f / (xn2 + xnorm * ax0);
+        *v0 = mk(phs.x * (ax0 + xnorm), phs.y * (ax0 + xnorm));
+    }
+}
+
+__global__ void __launch_bounds__(SB1_THREADS, 1) k_sb1(GroupSet gs, int mat_begin, EigArgs a) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    __shared__ float red[EIG_WARPS];
+    __shared__ float s_pt[SB_B];
+    int mat;
+    const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    clear_flag_before_release(flag_of(a.vready, g, mat));
+    pdl_release_dependents();
+    if (is_frozen(g, mat, a.active)) return;
+    wait_flag(flag_of(a.gready, g, mat), a.status, true);
+    const int n = g.s;
+    const long long pk = (long long)n * (n + 1) / 2;
+    cf *Gglob = a.Gp + g.poff + (long long)mat * pk;
+    cf *band = a.sb + g.sboff + (long long)mat * sb_stride(n);
+    float *ttau = tri_d(a, g, mat) + n;
+    const Sb1Layout LY = sb1_layout(n);
+    cf *Gs = (cf *)(tsm + LY.gs), *Vd = (cf *)(tsm + LY.vd), *Xs = (cf *)(tsm + LY.xs), *Ys = (cf *)(tsm + LY.ys);
+    cf *Sm = (cf *)(tsm + LY.sm), *Tm = (cf *)(tsm + LY.tm), *Mm = (cf *)(tsm + LY.mm);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (long long i = tid; i < pk; i += SB1_THREADS) Gs[i] = Gglob[i];
+    for (int j = tid; j < n; j += SB1_THREADS) ttau[j] = 0.f;
+    __syncthreads();
+    float gmax = 0.f;
+    for (int j = tid; j < n; j += SB1_THREADS) gmax = fmaxf(gmax, Gs[colstart(j, n)].x);
+    const float floor2 = reflector_floor(bmax(gmax, red));
+    int c0 = 0;
+    for (; c0 + SB_B < n - 1; c0 += SB_B) {
+        const int r0 = c0 + SB_B, m = n - r0, nr = min(SB_B, m - 1);
+        // ---- QR of the panel: warp w holds column cw = c0 + w, local rows lane + 32 q
+        const int cw = c0 + warp;
+        const cf *colw = Gs + colstart(cw, n) - cw;       // colw[i] = G(i, cw), i >= cw
+        cf x[SB1_RPL];
+#pragma unroll
+        for (int q = 0; q < SB1_RPL; ++q) {
+            const int i = lane + 32 * q;
+            x[q] = i < m ? colw[r0 + i] : mk(0.f, 0.f);
+        }
+        for (int t = 0; t < nr; ++t) {
+            cf *vs = Ys + (t & 1) * m;                     // reflector broadcast (double buffer)
+            if (warp == t) {
+                float xn2 = 0.f;
+#pragma unroll
+                for (int q = 0; q < SB1_RPL; ++q) {
+                    const int i = lane + 32 * q;
+                    if (i >= t && i < m) xn2 += cabs2(x[q]);
+                }
+                xn2 = wsum(xn2);
+                const cf x0 = shfl_cf(x[0], t);
+                float tau;
+                cf alpha, v0;
+                sb_reflector(xn2, x0, floor2, &tau, &alpha, &v0);
+#pragma unroll
+                for (int q = 0; q < SB1_RPL; ++q) {
+                    const int i = lane + 32 * q;
+                    cf v = mk(0.f, 0.f);
+                    if (tau != 0.f && i >= t && i < m) v = i == t ? v0 : x[q];
+                    if (i < m) {
+                        vs[i] = v;
+                        Vd[i * SB_B + t] = v;
+                    }
+                    if (tau != 0.f && i >= t) x[q] = i == t ? alpha : mk(0.f, 0.f);
+                }
+                if (lane == 0) {
+                    s_pt[t] = tau;
+                    ttau[cw] = tau;
+                }
+            }
+            __syncthreads();
+            if (warp > t) {
+                const float tau = s_pt[t];
+                if (tau != 0.f) {
+                    float dr = 0.f, di = 0.f;
+#pragma unroll
+                    for (int q = 0; q < SB1_RPL; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i >= t && i < m) {
+                            const cf v = vs[i];
+                            dr += v.x * x[q].x + v.y * x[q].y;
+                            di += v.x * x[q].y - v.y * x[q].x;
+                        }
+                    }
+                    dr = tau * wsum(dr);
+                    di = tau * wsum(di);
+#pragma unroll
+                    for (int q = 0; q < SB1_RPL; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i >= t && i < m) {
+                            const cf v = vs[i];
+                            x[q].x -= v.x * dr - v.y * di;
+                            x[q].y -= v.x * di + v.y * dr;
+                        }
+                    }
+                }
+            }
+        }
+        // ---- band of the panel's column: rows cw .. r0 - 1 from G, rows r0 .. r0 + w from R;
+        // the reflector to the packed buffer (rows cw + b ..); columns without one get V = 0
+        {
+            const int dr0 = SB_B - warp;                   // first diagonal taken from R
+            const cf xv = shfl_cf(x[0], (lane - dr0) & 31);
+            if (lane <= SB_B) {
+                cf val = mk(0.f, 0.f);
+                if (cw + lane < n) val = lane < dr0 ? colw[cw + lane] : xv;
+                band[(long long)cw * (SB_B + 1) + lane] = val;
+            }
+            if (warp >= nr)
+                for (int i = lane; i < m; i += 32) Vd[i * SB_B + warp] = mk(0.f, 0.f);
+            __syncwarp();
+            if (warp < nr)
+                for (int i = warp + lane; i < m; i += 32) Gglob[colstart(cw, n) + (r0 + i - cw)] = Vd[i * SB_B + warp];
+        }
+        __syncthreads();
+        // ---- S = V^H V (strict upper part; warp t: column t)
+        if (warp > 0 && warp < nr) {
+            const int t = warp;
+            float acc[2 * SB_B];
+#pragma unroll
+            for (int p = 0; p < 2 * SB_B; ++p) acc[p] = 0.f;
+            for (int i = t + lane; i < m; i += 32) {
+                const cf vt = Vd[i * SB_B + t];
+#pragma unroll
+                for (int p = 0; p < SB_B; ++p) {
+                    if (p < t) {
+                        const cf vp = Vd[i * SB_B + p];
+                        acc[2 * p] += vp.x * vt.x + vp.y * vt.y;
+                        acc[2 * p + 1] += vp.x * vt.y - vp.y * vt.x;
+                    }
+                }
+            }
+            float lo[16], hi[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                lo[u] = acc[u];
+                hi[u] = acc[16 + u];
+            }
+            const float s0 = treduce16(lo, lane), s1 = treduce16(hi, lane);   // lane L: value (L >> 1) & 15
+            if ((lane & 1) == 0) {
+                const int v = (lane >> 1) & 15;
+                ((float *)Sm)[2 * ((v >> 1) * SB_B + t) + (v & 1)] = s0;
+                ((float *)Sm)[2 * ((8 + (v >> 1)) * SB_B + t) + (v & 1)] = s1;
+            }
+        }
+        __syncthreads();
+        // ---- T (warp 0, lane q holds row q)
+        if (warp == 0) {
+            cf trow[SB_B];
+#pragma unroll
+            for (int t = 0; t < SB_B; ++t) {
+                cf tv = mk(0.f, 0.f);
+                if (t < nr) {
+                    const float taut = s_pt[t];
+                    if (lane == t) tv = mk(taut, 0.f);
+                    else if (lane < t) {
+                        float ar = 0.f, ai = 0.f;
+#pragma unroll
+                        for (int p = 0; p < t; ++p) {
+                            if (p >= lane) {
+                                const cf sv = Sm[p * SB_B + t];
+                                ar += trow[p].x * sv.x - trow[p].y * sv.y;
+                                ai += trow[p].x * sv.y + trow[p].y * sv.x;
+                            }
+                        }
+                        tv = mk(-taut * ar, -taut * ai);
+                    }
+                }
+                trow[t] = tv;
+            }
+            if (lane < SB_B) {
+#pragma unroll
+                for (int t = 0; t < SB_B; ++t) Tm[lane * SB_B + t] = trow[t];
+            }
+        }
+        __syncthreads();
+        // ---- Y = V T
+        for (int idx = tid; idx < m * SB_B; idx += SB1_THREADS) {
+            const int i = idx >> 4, t = idx & 15;
+            float ar = 0.f, ai = 0.f;
+            for (int p = 0; p <= t; ++p) {
+                const cf v = Vd[i * SB_B + p], tt = Tm[p * SB_B + t];
+                ar += v.x * tt.x - v.y * tt.y;
+                ai += v.x * tt.y + v.y * tt.x;
+            }
+            Ys[idx] = mk(ar, ai);
+        }
+        __syncthreads();
+        // ---- X = A Y over rows / columns r0 .. n - 1 (warp item: 32 rows x 8 columns of X)
+        const int nrb = (m + 31) >> 5;
+        for (int item = warp; item < 2 * nrb; item += EIG_WARPS) {
+            const int rb = item >> 1, h = item & 1;
+            const int il = 32 * rb + lane, i = r0 + il;
+            const bool valid = il < m;
+            float acc[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+            const long long csi = valid ? colstart(i, n) : 0;
+            long long csj = colstart(r0, n);
+            for (int jl = 0; jl < m; ++jl) {
+                const int j = r0 + jl;
+                cf av = mk(0.f, 0.f);
+                if (valid) {
+                    const long long ix = j <= i ? csj + (i - j) : csi + (j - i);
+                    av = Gs[ix];
+                    if (j > i) av.y = -av.y;
+                }
+                const float4 *yr = (const float4 *)(Ys + jl * SB_B + 8 * h);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 y4 = yr[q];
+                    acc[4 * q + 0] = fmaf(av.x, y4.x, acc[4 * q + 0]);
+                    acc[4 * q + 0] = fmaf(-av.y, y4.y, acc[4 * q + 0]);
+                    acc[4 * q + 1] = fmaf(av.x, y4.y, acc[4 * q + 1]);
+                    acc[4 * q + 1] = fmaf(av.y, y4.x, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(av.x, y4.z, acc[4 * q + 2]);
+                    acc[4 * q + 2] = fmaf(-av.y, y4.w, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(av.x, y4.w, acc[4 * q + 3]);
+                    acc[4 * q + 3] = fmaf(av.y, y4.z, acc[4 * q + 3]);
+                }
+                csj += n - j;
+            }
+            if (valid) {
+                float4 *xr = (float4 *)(Xs + il * SB_B + 8 * h);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) xr[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+            }
+        }
+        __syncthreads();
+        // ---- M = Y^H X (warp p: row p)
+        {
+            const int p = warp;
+            float acc[2 * SB_B];
+#pragma unroll
+            for (int u = 0; u < 2 * SB_B; ++u) acc[u] = 0.f;
+            for (int i = lane; i < m; i += 32) {
+                const cf yp = Ys[i * SB_B + p];
+#pragma unroll
+                for (int q = 0; q < SB_B; ++q) {
+                    const cf xq = Xs[i * SB_B + q];
+                    acc[2 * q] += yp.x * xq.x + yp.y * xq.y;
+                    acc[2 * q + 1] += yp.x * xq.y - yp.y * xq.x;
+                }
+            }
+            float lo[16], hi[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                lo[u] = acc[u];
+                hi[u] = acc[16 + u];
+            }
+            const float s0 = treduce16(lo, lane), s1 = treduce16(hi, lane);
+            if ((lane & 1) == 0) {
+                const int v = (lane >> 1) & 15;
+                ((float *)Mm)[2 * (p * SB_B + (v >> 1)) + (v & 1)] = s0;
+                ((float *)Mm)[2 * (p * SB_B + 8 + (v >> 1)) + (v & 1)] = s1;
+            }
+        }
+        __syncthreads();
+        // ---- W = X - V M / 2, in place
+        for (int idx = tid; idx < m * SB_B; idx += SB1_THREADS) {
+            const int i = idx >> 4, q = idx & 15;
+            float ar = 0.f, ai = 0.f;
+#pragma unroll
+            for (int p = 0; p < SB_B; ++p) {
+                const cf v = Vd[i * SB_B + p], mv = Mm[p * SB_B + q];
+                ar += v.x * mv.x - v.y * mv.y;
+                ai += v.x * mv.y + v.y * mv.x;
+            }
+            const cf xv = Xs[idx];
+            Xs[idx] = mk(xv.x - 0.5f * ar, xv.y - 0.5f * ai);
+        }
+        __syncthreads();
+        // ---- A <- A - W V^H - V W^H on the lower triangle (warp item: a 32 x 32 tile)
+        const int ntiles = nrb * (nrb + 1) / 2;
+        for (int tile = warp; tile < ntiles; tile += EIG_WARPS) {
+            int rb = 0, cb = tile;
+            while (cb > rb) {
+                cb -= rb + 1;
+                ++rb;
+            }
+            const int il = 32 * rb + lane;
+            const bool valid = il < m;
+            cf wi[SB_B], vi[SB_B];
+#pragma unroll
+            for (int p = 0; p < SB_B; ++p) {
+                wi[p] = valid ? Xs[il * SB_B + p] : mk(0.f, 0.f);
+                vi[p] = valid ? Vd[il * SB_B + p] : mk(0.f, 0.f);
+            }
+            const int jl1 = min(32 * cb + 32, m);
+            for (int jl = 32 * cb; jl < jl1; ++jl) {
+                if (valid && jl <= il) {
+                    cf *ap = Gs + colstart(r0 + jl, n) + (il - jl);
+                    float ar = ap->x, ai = ap->y;
+                    const float4 *vr = (const float4 *)(Vd + jl * SB_B), *wr = (const float4 *)(Xs + jl * SB_B);
+#pragma unroll
+                    for (int q = 0; q < SB_B / 2; ++q) {
+                        const float4 v4 = vr[q], w4 = wr[q];
+                        // a -= w_i conj(v_j) + v_i conj(w_j), two columns per float4
+                        ar = fmaf(-wi[2 * q].x, v4.x, ar); ar = fmaf(-wi[2 * q].y, v4.y, ar);
+                        ai = fmaf(wi[2 * q].x, v4.y, ai);  ai = fmaf(-wi[2 * q].y, v4.x, ai);
+                        ar = fmaf(-vi[2 * q].x, w4.x, ar); ar = fmaf(-vi[2 * q].y, w4.y, ar);
+                        ai = fmaf(vi[2 * q].x, w4.y, ai);  ai = fmaf(-vi[2 * q].y, w4.x, ai);
+                        ar = fmaf(-wi[2 * q + 1].x, v4.z, ar); ar = fmaf(-wi[2 * q + 1].y, v4.w, ar);
+                        ai = fmaf(wi[2 * q + 1].x, v4.w, ai);  ai = fmaf(-wi[2 * q + 1].y, v4.z, ai);
+                        ar = fmaf(-vi[2 * q + 1].x, w4.z, ar); ar = fmaf(-vi[2 * q + 1].y, w4.w, ar);
+                        ai = fmaf(vi[2 * q + 1].x, w4.w, ai);  ai = fmaf(-vi[2 * q + 1].y, w4.z, ai);
+                    }
+                    *ap = mk(ar, ai);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ---- band of the remaining columns (already within the band)
+    for (int idx = tid; idx < (n - c0) * (SB_B + 1); idx += SB1_THREADS) {
+        const int c = c0 + idx / (SB_B + 1), d = idx - (c - c0) * (SB_B + 1);
+        band[(long long)c * (SB_B + 1) + d] = c + d < n ? Gs[colstart(c, n) + d] : mk(0.f, 0.f);
+    }
+    publish_flag(flag_of(a.bready, g, mat));
+}
+
+#define SB2_THREADS 128
+#define SB2_WARPS (SB2_THREADS / 32)
+#define SB2_LD (2 * SB_B)          // stored diagonals 0 .. 2 b - 1 (band and bulge)
+
+__host__ __device__ inline size_t sb2_smem(int n) { return (size_t)n * SB2_LD * 8; }
+
+// One bulge-chasing step (sweep j, step k) by one warp on the band Ls (Ls[c LD + d] = A(c + d, c)).
+__device__ void sb2_step(cf *Ls, int n, int j, int k, float floor2, cf *rec, cf *sv, cf *sw, int lane) {
+    int c, r0, r1;
+    if (k == 1) {
+        c = j;
+        r0 = j + 1;
+        r1 = min(j + SB_B, n - 1);
+    } else {
+        c = j + 1 + (k - 2) * SB_B;
+        r0 = j + 1 + (k - 1) * SB_B;
+        r1 = min(j + k * SB_B, n - 1);
+    }
+    const int L = r1 - r0 + 1;                 // 2 .. SB_B
+    const bool lo = lane < SB_B;
+    const int l = lane & (SB_B - 1);
+    // 1. reflector of A[r0 .. r1, c]
+    cf x = mk(0.f, 0.f);
+    if (lo && l < L) x = Ls[c * SB2_LD + (r0 - c) + l];
+    const float xn2 = wsum(cabs2(x));
+    const cf x0 = shfl_cf(x, 0);
+    float tau;
+    cf alpha, v0;
+    sb_reflector(xn2, x0, floor2, &tau, &alpha, &v0);
+    cf v = mk(0.f, 0.f);
+    if (tau != 0.f && lo && l < L) v = l == 0 ? v0 : x;
+    if (lane == 0) rec[0] = mk(tau, __int_as_float(r0));
+    if (lo) rec[1 + l] = v;
+    if (tau == 0.f) return;
+    if (lo && l < L) Ls[c * SB2_LD + (r0 - c) + l] = l == 0 ? alpha : mk(0.f, 0.f);
+    if (lo) sv[l] = v;
+    __syncwarp();
+    // 2. from the left on the columns between c and the window
+    if (k >= 2 && lane < r0 - c - 1) {
+        const int cc = c + 1 + lane;
+        cf *col = Ls + cc * SB2_LD + (r0 - cc);
+        float dr = 0.f, di = 0.f;
+#pragma unroll
+        for (int i = 0; i < SB_B; ++i) {
+            if (i < L) {
+                const cf vv = sv[i], a = col[i];
+                dr += vv.x * a.x + vv.y * a.y;
+                di += vv.x * a.y - vv.y * a.x;
+            }
+        }
+        dr *= tau;
+        di *= tau;
+#pragma unroll
+        for (int i = 0; i < SB_B; ++i) {
+            if (i < L) {
+                const cf vv = sv[i];
+                col[i] = mk(col[i].x - (vv.x * dr - vv.y * di), col[i].y - (vv.x * di + vv.y * dr));
+            }
+        }
+    }
+    // 3. from both sides on the diagonal block (lane l: row r0 + l)
+    cf p = mk(0.f, 0.f);
+    if (lo && l < L) {
+        float pr = 0.f, pi = 0.f;
+#pragma unroll
+        for (int i2 = 0; i2 < SB_B; ++i2) {
+            if (i2 < L) {
+                const int ix = i2 <= l ? (r0 + i2) * SB2_LD + (l - i2) : (r0 + l) * SB2_LD + (i2 - l);
+                cf dv = Ls[ix];
+                if (i2 > l) dv.y = -dv.y;
+                if (i2 == l) dv.y = 0.f;
+                const cf vv = sv[i2];
+                pr += dv.x * vv.x - dv.y * vv.y;
+                pi += dv.x * vv.y + dv.y * vv.x;
+            }
+        }
+        p = mk(tau * pr, tau * pi);
+    }
+    const float kv = wsum(v.x * p.x + v.y * p.y);
+    const float K = 0.5f * tau * kv;
+    const cf w = mk(p.x - K * v.x, p.y - K * v.y);
+    if (lo) sw[l] = w;
+    __syncwarp();
+    if (lo && l < L) {
+#pragma unroll
+        for (int i2 = 0; i2 < SB_B; ++i2) {
+            if (i2 <= l && i2 < L) {
+                cf *dp = Ls + (r0 + i2) * SB2_LD + (l - i2);
+                const cf vj = sv[i2], wj = sw[i2];
+                float ur = dp->x, ui = dp->y;
+                ur -= v.x * wj.x + v.y * wj.y + w.x * vj.x + w.y * vj.y;
+                ui -= v.y * wj.x - v.x * wj.y + w.y * vj.x - w.x * vj.y;
+                if (i2 == l) ui = 0.f;
+                *dp = mk(ur, ui);
+            }
+        }
+    }
+    // 4. from the right on the rows below the window
+    const int nbelow = min(SB_B, n - 1 - r1);
+    if (lane < nbelow) {
+        const int row = r1 + 1 + lane;
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int i = 0; i < SB_B; ++i) {
+            if (i < L) {
+                const cf e = Ls[(r0 + i) * SB2_LD + (row - r0 - i)], vv = sv[i];
+                sr += e.x * vv.x - e.y * vv.y;
+                si += e.x * vv.y + e.y * vv.x;
+            }
+        }
+        sr *= tau;
+        si *= tau;
+#pragma unroll
+        for (int i = 0; i < SB_B; ++i) {
+            if (i < L) {
+                cf *ep = Ls + (r0 + i) * SB2_LD + (row - r0 - i);
+                const cf vv = sv[i];
+                // E -= s conj(v)
+                *ep = mk(ep->x - (sr * vv.x + si * vv.y), ep->y - (si * vv.x - sr * vv.y));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SB2_THREADS) k_sb2(GroupSet gs, int mat_begin, EigArgs a) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    __shared__ cf s_v[SB2_WARPS][SB_B], s_w[SB2_WARPS][SB_B];
+    __shared__ float red[SB2_WARPS];
+    int mat;
+    const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
+    const Group &g = gs.g[gi];
+    pdl_release_dependents();
+    if (is_frozen(g, mat, a.active)) return;
+    wait_flag(flag_of(a.bready, g, mat), a.status, true);
+    const int n = g.s;
+    const cf *band = a.sb + g.sboff + (long long)mat * sb_stride(n);
+    cf *rec = a.sb + g.sboff + (long long)mat * sb_stride(n) + (long long)n * (SB_B + 1);
+    float *td = tri_d(a, g, mat);
+    cf *te = (cf *)(td + 2 * n);
+    cf *Ls = (cf *)bsm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float gm = 0.f;
+    for (int idx = tid; idx < n * SB2_LD; idx += SB2_THREADS) {
+        const int c = idx / SB2_LD, d = idx - c * SB2_LD;
+        const cf v = d <= SB_B ? band[(long long)c * (SB_B + 1) + d] : mk(0.f, 0.f);
+        Ls[idx] = v;
+        if (d == 0) gm = fmaxf(gm, fabsf(v.x));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if (lane == 0) red[warp] = gm;
+    __syncthreads();
+    for (int w = 0; w < SB2_WARPS; ++w) gm = fmaxf(gm, red[w]);
+    const float floor2 = reflector_floor(gm);
+    if (n >= 3) {
+        const int kmax = sb_nsteps(n, 0);
+        const int tlast = 3 * (n - 3) + sb_nsteps(n, n - 3);
+        for (int tt = 1; tt <= tlast; ++tt) {
+            for (int k = (tt - 1) % 3 + 1 + 3 * warp; k <= kmax; k += 3 * SB2_WARPS) {
+                const int j = (tt - k) / 3;               // tt - k is a multiple of 3
+                if (tt - k < 0 || j > n - 3 || k > sb_nsteps(n, j)) continue;
+                sb2_step(Ls, n, j, k, floor2, rec + (sb_sweep_off(n, j) + k - 1) * (SB_B + 1), s_v[warp], s_w[warp],
+                         lane);
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n; i += SB2_THREADS) {
+        td[i] = Ls[i * SB2_LD].x;
+        te[i] = i + 1 < n ? Ls[i * SB2_LD + 1] : mk(0.f, 0.f);
+    }
+    publish_flag(flag_of(a.ready, g, mat));
+}
+
 // ------------------------------------------------ real tridiagonal setup
 // T = P T_r P^H with T_r real symmetric: f_k = |e_k| and phases ph_0 = 1,
 // ph_{k+1} = ph_k e_k / |e_k| (warp 0 runs a product scan).  The caller
@@ -1006,9 +1574,47 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
             Yc[idx] = cscale(ph[i], zv[i * IV_ST + w]);
         }
         __syncthreads();
+        if (a.band) {
+            // two-stage reduction: y <- Q2 y = S_0 (S_1 (... S_{n-3} y)), the reflectors of one
+            // sweep (disjoint windows of at most SB_B rows) two at a time, one per half-warp
+            const cf *rec = a.sb + g.sboff + (long long)mat * sb_stride(n) + (long long)n * (SB_B + 1);
+            const int hw = lane >> 4, l = lane & (SB_B - 1);
+            for (int w = warp; w < qc; w += NW) {
+                cf *y = Yc + (long long)w * n;
+                for (int j = n - 3; j >= 0; --j) {
+                    const int K = sb_nsteps(n, j);
+                    const cf *rj = rec + sb_sweep_off(n, j) * (SB_B + 1);
+                    for (int k0 = 0; k0 < K; k0 += 2) {
+                        const int k = k0 + hw;
+                        float tau = 0.f;
+                        int row = n;
+                        cf v = mk(0.f, 0.f);
+                        if (k < K) {
+                            const cf hd = rj[k * (SB_B + 1)];
+                            tau = hd.x;
+                            row = __float_as_int(hd.y) + l;
+                            v = rj[k * (SB_B + 1) + 1 + l];
+                        }
+                        const bool on = tau != 0.f && row < n;
+                        const cf yy = on ? y[row] : mk(0.f, 0.f);
+                        float dr = v.x * yy.x + v.y * yy.y, di = v.x * yy.y - v.y * yy.x;
+#pragma unroll
+                        for (int o = SB_B / 2; o > 0; o >>= 1) {
+                            dr += __shfl_xor_sync(0xffffffffu, dr, o);
+                            di += __shfl_xor_sync(0xffffffffu, di, o);
+                        }
+                        dr *= tau;
+                        di *= tau;
+                        if (on) y[row] = mk(yy.x - (v.x * dr - v.y * di), yy.y - (v.x * di + v.y * dr));
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
         // Reflectors are applied in batches of EV_HB, u_j = v_{kb-j} (j = 0 .. EV_HB-1, in the order
-        // of application), staged in shared memory by absolute row (zero on rows <= kb - j, and
-        // wholly zero past reflector 0).  With d_j = u_j^H y and C_ji = u_j^H u_i, applying them
+        // of application), staged in shared memory by absolute row (zero above the reflector's
+        // first row, and wholly zero past reflector 0).  With d_j = u_j^H y and C_ji = u_j^H u_i, applying them
         // one after the other is
         //   s_j = d_j - sum_{i<j} tau_i C_ji s_i,   y <- y - sum_j tau_j u_j s_j,
         // so each vector needs one round of reductions per batch instead of one per reflector:
@@ -1022,15 +1628,19 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
         const size_t hb_elems = (size_t)EV_HB * n;
         const int nbuf = 3 * hb_elems * 8 <= LY.yc - LY.zv ? 3 : 2;
         cf *hbuf0 = (cf *)(vsm + LY.zv);
-        const int nbatch = n >= 3 ? (n - 3) / EV_HB + 1 : 0;   // batch b: kb = n - 3 - b EV_HB
+        // reflector of column k: rows >= k + hoff (1; SB_B for the panel reflectors of the
+        // two-stage reduction, the last of which belongs to column n - 2 - SB_B)
+        const int hoff = a.band ? SB_B : 1;
+        const int kfirst = n - 2 - hoff;
+        const int nbatch = kfirst >= 0 ? kfirst / EV_HB + 1 : 0;   // batch b: kb = kfirst - b EV_HB
         auto issue_batch = [&](int b) {
             if (b < nbatch) {
-                const int kb = n - 3 - b * EV_HB;
+                const int kb = kfirst - b * EV_HB;
                 cf *buf = hbuf0 + (long long)(b % nbuf) * hb_elems;
                 for (int j = 0; j < EV_HB; ++j) {
                     const int k = kb - j;
                     for (int row = tid; row < n; row += NT) {
-                        const bool ok = k >= 0 && row > k;
+                        const bool ok = k >= 0 && row >= k + hoff;
                         cp_async8(buf + (long long)j * n + row, ok ? Gglob + colstart(k, n) + (row - k) : Gglob,
                                   ok ? 8 : 0);
                     }
@@ -1040,9 +1650,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
         };
         for (int b = 0; b + 1 < nbuf; ++b) issue_batch(b);
         for (int b = 0; b < nbatch; ++b) {
-            const int kb = n - 3 - b * EV_HB;
+            const int kb = kfirst - b * EV_HB;
             const int nbat = min(EV_HB, kb + 1);
-            const int r0 = kb - nbat + 2;                    // first row any u_j of the batch touches
+            const int r0 = kb - nbat + 1 + hoff;             // first row any u_j of the batch touches
             const cf *hb = hbuf0 + (long long)(b % nbuf) * hb_elems;
             if (nbuf == 3) cp_async_wait_1();                // every group but the newest (batch b + 1)
             else cp_async_wait_all();
@@ -1061,7 +1671,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
                     float cr = 0.f, ci = 0.f;
                     if (pq0 + e < EV_HB * (EV_HB - 1) / 2) {
                         const cf *uj = hb + (long long)j * n, *ui = hb + (long long)i * n;
-                        for (int row = kb - i + 1 + lane; row < n; row += 32) {
+                        for (int row = kb - i + hoff + lane; row < n; row += 32) {
                             const cf x = uj[row], z = ui[row];
                             cr += x.x * z.x + x.y * z.y;
                             ci += x.x * z.y - x.y * z.x;
@@ -1642,6 +2252,9 @@ cudaError_t eig_init_attributes() {
     TRI_ATTR(1, false) TRI_ATTR(2, false) TRI_ATTR(4, false) TRI_ATTR(6, false) TRI_ATTR(7, false) TRI_ATTR(8, true)
 #undef TRI_ATTR
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tridiag_g, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sb1, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sb2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb2_smem(SB_NMAX));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<16, 17, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eigvec<8, 9, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resolvent<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -1698,9 +2311,28 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
     size_t ev_smem = 0;
     for (int k = 0; k < gs.n; ++k) ev_smem = max(ev_smem, ev_layout(gs.g[k].s, chunk, chunk + 1).total);
     if (ev_smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
-    // 1. tridiagonalisation (a programmatic dependent of k_gram_tc when ea.gready is set)
+    // 1. tridiagonalisation (a programmatic dependent of k_gram_tc when ea.gready is set):
+    // two-stage where every order allows it, scratch is given, the eigenpairs above t^2 are
+    // all that is wanted (the reverse mode's resolvent solves use the one-stage reflectors)
+    // and the flags of the launch chain are complete
+    bool two = ea.sb != nullptr && ea.reduction != 1 && ea.zsave == nullptr && !ea.allp &&
+               (ea.ready == nullptr || ea.bready != nullptr) && sb1_layout(nmax).total <= (size_t)g_eig_smem_max;
+    int nmin = nmax;
+    for (int k = 0; k < gs.n; ++k) {
+        two = two && sb_eligible(gs.g[k].s) && gs.g[k].sboff >= 0;
+        nmin = min(nmin, gs.g[k].s);
+    }
+    if (ea.reduction == 0) two = two && nmin >= SB_AUTO_MIN;
+    EigArgs eb = ea;
+    eb.band = two ? SB_B : 0;
     cudaError_t e;
-    if (nmax <= EIG_SMEM_MAX_N) {
+    if (two) {
+        e = launch_ex(ea.gready != nullptr, k_sb1, dim3(mat_count), dim3(SB1_THREADS), sb1_layout(nmax).total, st, gs,
+                      mat_begin, eb);
+        if (e == cudaSuccess)
+            e = launch_ex(ea.ready != nullptr, k_sb2, dim3(mat_count), dim3(SB2_THREADS), sb2_smem(nmax), st, gs,
+                          mat_begin, eb);
+    } else if (nmax <= EIG_SMEM_MAX_N) {
         const size_t smem = tridiag_smem(nmax);
         if (smem > (size_t)g_eig_smem_max) return cudaErrorInvalidValue;
         if (nmax <= 32) e = tridiag_launch<1, false>(gs, mat_begin, mat_count, ea, smem, st);
@@ -1721,8 +2353,8 @@ cudaError_t launch_heig(const GroupSet &gs, int mat_begin, int mat_count, const 
     // a programmatic dependent of the reduction.
     const bool pdl = ea.ready != nullptr;
     if (chunk == 16)
-        return launch_ex(pdl, k_eigvec<16, 17, 512>, dim3(mat_count), dim3(512), ev_smem, st, gs, mat_begin, ea);
-    return launch_ex(pdl, k_eigvec<8, 9, 256>, dim3(mat_count), dim3(256), ev_smem, st, gs, mat_begin, ea);
+        return launch_ex(pdl, k_eigvec<16, 17, 512>, dim3(mat_count), dim3(512), ev_smem, st, gs, mat_begin, eb);
+    return launch_ex(pdl, k_eigvec<8, 9, 256>, dim3(mat_count), dim3(256), ev_smem, st, gs, mat_begin, eb);
 }
 
 cudaError_t launch_apply_eig(const GroupSet &gs, int mat_begin, int mat_count, const EigArgs &ea, const SvtArgs &a,

@@ -129,3 +129,4 @@ def test_null_arguments(lib):
     te = (ctypes.c_float * 1)(1.0)
     assert lib.selr_t2_fit(None, te, 1, 1, 1.0, 10.0, None, None, None) == 1
     assert lib.selr_plan_set_tuning(None, 0, 16) == 1
+    assert lib.selr_plan_set_reduction(None, 2) == 1
