@@ -758,14 +758,15 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
 // c0 .. c0 + b - 1 and rows r0 = c0 + b .. n - 1 (m = n - r0 rows):
 //   QR of the panel: nr = min(b, m - 1) reflectors H_t = I - tau_t v_t v_t^H, one warp per
 //     panel column, one barrier per reflector (Q = H_0 ... H_{nr-1} = I - V T V^H);
-//   T by the forward recurrence T_tt = tau_t, T[0:t, t] = -tau_t T[0:t, 0:t] (V^H v_t)[0:t];
+//   S = V^H V and Y = V T, with T^-1 = diag(1 / tau) + (strict upper part of S), by a
+//     triangular solve per row of V;
 //   trailing update A <- Q^H A Q on rows / columns r0 .. n - 1 as
-//     Y = V T,  X = A Y,  M = Y^H X,  W = X - V M / 2,  A <- A - W V^H - V W^H.
+//     X = A Y,  M = Y^H X,  W = X - V M / 2,  A <- A - W V^H - V W^H.
 // The band (diagonals 0 .. b) goes to the scratch, the reflectors to the packed buffer (column c
 // holds v of the panel reflector of that column on rows c + b .. n - 1) and tau_c to the tau
 // slots of the tridiagonal data.
 //
-// Stage 2, k_sb2 (one CTA of four warps per matrix, the band with room for the bulge in
+// Stage 2, k_sb2 (one CTA of eight warps per matrix, the band with room for the bulge in
 // shared memory).  Sweep j (j = 0 .. n - 3) has steps k = 1 .. sb_nsteps(n, j): step 1
 // annihilates column j below its first sub-diagonal with a reflector on rows j + 1 .. j + b;
 // step k > 1 annihilates the first column of the bulge the previous step left below the band
@@ -773,8 +774,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
 // from the left to the columns between that column and its window, from both sides to the
 // window's diagonal block and from the right to the b rows below the window.  Step k of sweep
 // j runs at time 3 j + k: the steps that share a time touch disjoint entries, and every entry
-// a step reads was last written by a step of an earlier time, so one warp per step with a
-// barrier per time gives the same matrix as the sweeps run one after the other.  The
+// a step reads was last written by a step of an earlier time, so a pair of warps per step
+// with a barrier per time gives the same matrix as the sweeps run one after the other.  The
 // reflectors are stored sweep-major; the tridiagonal d, e goes to the tridiagonal data.
 //
 // Back-transformation (k_eigvec with EigArgs::band): y = Q1 Q2 P z; Q2 = S_0 S_1 ... S_{n-3}
@@ -787,7 +788,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
 #define SB1_RPL 6                  // panel rows per lane: n - SB_B <= 32 SB1_RPL for n <= SB_NMAX
 
 struct Sb1Layout {
-    size_t gs, vd, xs, ys, sm, tm, mm, total;
+    size_t gs, vd, xs, ys, sm, mm, total;
 };
 __host__ __device__ inline Sb1Layout sb1_layout(int n) {
     Sb1Layout L;
@@ -795,10 +796,9 @@ __host__ __device__ inline Sb1Layout sb1_layout(int n) {
     size_t o = 0;
     L.gs = o; o += al16((size_t)n * (n + 1) / 2 * 8);
     L.vd = o; o += al16(mm * SB_B * 8);
-    L.xs = o; o += al16(mm * SB_B * 8);
+    L.xs = o; o += al16((mm * SB_B + SB_B) * 8);    // also the column-major reflectors of the QR
     L.ys = o; o += al16(mm * SB_B * 8);
     L.sm = o; o += SB_B * SB_B * 8;
-    L.tm = o; o += SB_B * SB_B * 8;
     L.mm = o; o += SB_B * SB_B * 8;
     L.total = o;
     return L;
@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(SB1_THREADS, 1) k_sb1(GroupSet gs, int mat_beg
     float *ttau = tri_d(a, g, mat) + n;
     const Sb1Layout LY = sb1_layout(n);
     cf *Gs = (cf *)(tsm + LY.gs), *Vd = (cf *)(tsm + LY.vd), *Xs = (cf *)(tsm + LY.xs), *Ys = (cf *)(tsm + LY.ys);
-    cf *Sm = (cf *)(tsm + LY.sm), *Tm = (cf *)(tsm + LY.tm), *Mm = (cf *)(tsm + LY.mm);
+    cf *Sm = (cf *)(tsm + LY.sm), *Mm = (cf *)(tsm + LY.mm);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (long long i = tid; i < pk; i += SB1_THREADS) Gs[i] = Gglob[i];
     for (int j = tid; j < n; j += SB1_THREADS) ttau[j] = 0.f;
@@ -860,8 +860,12 @@ __global__ void __launch_bounds__(SB1_THREADS, 1) k_sb1(GroupSet gs, int mat_beg
             const int i = lane + 32 * q;
             x[q] = i < m ? colw[r0 + i] : mk(0.f, 0.f);
         }
+        // reflectors column-major in the X buffer (odd column stride: the transposition below reads
+        // a row across the columns without bank conflicts)
+        cf *Vc = Xs;
+        const int vst = (m & 1) ? m : m + 1;
         for (int t = 0; t < nr; ++t) {
-            cf *vs = Ys + (t & 1) * m;                     // reflector broadcast (double buffer)
+            const cf *vs = Vc + t * vst;
             if (warp == t) {
                 float xn2 = 0.f;
 #pragma unroll
@@ -879,10 +883,7 @@ __global__ void __launch_bounds__(SB1_THREADS, 1) k_sb1(GroupSet gs, int mat_beg
                     const int i = lane + 32 * q;
                     cf v = mk(0.f, 0.f);
                     if (tau != 0.f && i >= t && i < m) v = i == t ? v0 : x[q];
-                    if (i < m) {
-                        vs[i] = v;
-                        Vd[i * SB_B + t] = v;
-                    }
+                    if (i < m) Vc[t * vst + i] = v;
                     if (tau != 0.f && i >= t) x[q] = i == t ? alpha : mk(0.f, 0.f);
                 }
                 if (lane == 0) {
@@ -928,84 +929,66 @@ __global__ void __launch_bounds__(SB1_THREADS, 1) k_sb1(GroupSet gs, int mat_beg
                 if (cw + lane < n) val = lane < dr0 ? colw[cw + lane] : xv;
                 band[(long long)cw * (SB_B + 1) + lane] = val;
             }
-            if (warp >= nr)
-                for (int i = lane; i < m; i += 32) Vd[i * SB_B + warp] = mk(0.f, 0.f);
-            __syncwarp();
             if (warp < nr)
-                for (int i = warp + lane; i < m; i += 32) Gglob[colstart(cw, n) + (r0 + i - cw)] = Vd[i * SB_B + warp];
+                for (int i = warp + lane; i < m; i += 32) Gglob[colstart(cw, n) + (r0 + i - cw)] = Vc[warp * vst + i];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < m * SB_B; idx += SB1_THREADS) {
+            const int i = idx >> 4, t = idx & 15;
+            Vd[idx] = t < nr ? Vc[t * vst + i] : mk(0.f, 0.f);
         }
         __syncthreads();
         // ---- S = V^H V (strict upper part; warp t: column t)
-        if (warp > 0 && warp < nr) {
-            const int t = warp;
-            float acc[2 * SB_B];
-#pragma unroll
-            for (int p = 0; p < 2 * SB_B; ++p) acc[p] = 0.f;
-            for (int i = t + lane; i < m; i += 32) {
-                const cf vt = Vd[i * SB_B + t];
-#pragma unroll
-                for (int p = 0; p < SB_B; ++p) {
-                    if (p < t) {
-                        const cf vp = Vd[i * SB_B + p];
-                        acc[2 * p] += vp.x * vt.x + vp.y * vt.y;
-                        acc[2 * p + 1] += vp.x * vt.y - vp.y * vt.x;
-                    }
-                }
+        if (warp > 0 && warp < nr) {                       // lanes (row parity r, column p)
+            const int t = warp, r = lane >> 4, pc = lane & 15;
+            float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
+            int i = t + r;
+            for (; i + 2 < m; i += 4) {
+                const cf vp = Vd[i * SB_B + pc], vt = Vd[i * SB_B + t];
+                const cf wp = Vd[(i + 2) * SB_B + pc], wt = Vd[(i + 2) * SB_B + t];
+                sr0 += vp.x * vt.x + vp.y * vt.y;
+                si0 += vp.x * vt.y - vp.y * vt.x;
+                sr1 += wp.x * wt.x + wp.y * wt.y;
+                si1 += wp.x * wt.y - wp.y * wt.x;
             }
-            float lo[16], hi[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                lo[u] = acc[u];
-                hi[u] = acc[16 + u];
+            if (i < m) {
+                const cf vp = Vd[i * SB_B + pc], vt = Vd[i * SB_B + t];
+                sr0 += vp.x * vt.x + vp.y * vt.y;
+                si0 += vp.x * vt.y - vp.y * vt.x;
             }
-            const float s0 = treduce16(lo, lane), s1 = treduce16(hi, lane);   // lane L: value (L >> 1) & 15
-            if ((lane & 1) == 0) {
-                const int v = (lane >> 1) & 15;
-                ((float *)Sm)[2 * ((v >> 1) * SB_B + t) + (v & 1)] = s0;
-                ((float *)Sm)[2 * ((8 + (v >> 1)) * SB_B + t) + (v & 1)] = s1;
-            }
+            float sr = sr0 + sr1, si = si0 + si1;
+            sr += __shfl_xor_sync(0xffffffffu, sr, 16);
+            si += __shfl_xor_sync(0xffffffffu, si, 16);
+            if (r == 0 && pc < t) Sm[pc * SB_B + t] = mk(sr, si);
         }
         __syncthreads();
-        // ---- T (warp 0, lane q holds row q)
-        if (warp == 0) {
-            cf trow[SB_B];
+        // ---- Y = V T without forming T: T^-1 = U = diag(1 / tau) + (strict upper part of S) (the
+        // inverse of the forward recurrence for T), so each row of Y solves y U = v:
+        //   y_t = tau_t (v_t - sum_{p < t} y_p S_pt)
+        for (int i = tid; i < m; i += SB1_THREADS) {
+            cf y[SB_B];
+            const float4 *vr = (const float4 *)(Vd + i * SB_B);
+#pragma unroll
+            for (int q = 0; q < SB_B / 2; ++q) {
+                const float4 v4 = vr[q];
+                y[2 * q] = mk(v4.x, v4.y);
+                y[2 * q + 1] = mk(v4.z, v4.w);
+            }
 #pragma unroll
             for (int t = 0; t < SB_B; ++t) {
-                cf tv = mk(0.f, 0.f);
-                if (t < nr) {
-                    const float taut = s_pt[t];
-                    if (lane == t) tv = mk(taut, 0.f);
-                    else if (lane < t) {
-                        float ar = 0.f, ai = 0.f;
+                float ar = y[t].x, ai = y[t].y;
 #pragma unroll
-                        for (int p = 0; p < t; ++p) {
-                            if (p >= lane) {
-                                const cf sv = Sm[p * SB_B + t];
-                                ar += trow[p].x * sv.x - trow[p].y * sv.y;
-                                ai += trow[p].x * sv.y + trow[p].y * sv.x;
-                            }
-                        }
-                        tv = mk(-taut * ar, -taut * ai);
-                    }
+                for (int p = 0; p < t; ++p) {
+                    const cf sv = Sm[p * SB_B + t];
+                    ar -= y[p].x * sv.x - y[p].y * sv.y;
+                    ai -= y[p].x * sv.y + y[p].y * sv.x;
                 }
-                trow[t] = tv;
+                const float tt = t < nr ? s_pt[t] : 0.f;
+                y[t] = mk(tt * ar, tt * ai);
             }
-            if (lane < SB_B) {
+            float4 *yw = (float4 *)(Ys + i * SB_B);
 #pragma unroll
-                for (int t = 0; t < SB_B; ++t) Tm[lane * SB_B + t] = trow[t];
-            }
-        }
-        __syncthreads();
-        // ---- Y = V T
-        for (int idx = tid; idx < m * SB_B; idx += SB1_THREADS) {
-            const int i = idx >> 4, t = idx & 15;
-            float ar = 0.f, ai = 0.f;
-            for (int p = 0; p <= t; ++p) {
-                const cf v = Vd[i * SB_B + p], tt = Tm[p * SB_B + t];
-                ar += v.x * tt.x - v.y * tt.y;
-                ai += v.x * tt.y + v.y * tt.x;
-            }
-            Ys[idx] = mk(ar, ai);
+            for (int q = 0; q < SB_B / 2; ++q) yw[q] = make_float4(y[2 * q].x, y[2 * q].y, y[2 * q + 1].x, y[2 * q + 1].y);
         }
         __syncthreads();
         // ---- X = A Y over rows / columns r0 .. n - 1 (warp item: 32 rows x 8 columns of X)
@@ -1050,32 +1033,27 @@ __global__ void __launch_bounds__(SB1_THREADS, 1) k_sb1(GroupSet gs, int mat_beg
         }
         __syncthreads();
         // ---- M = Y^H X (warp p: row p)
-        {
-            const int p = warp;
-            float acc[2 * SB_B];
-#pragma unroll
-            for (int u = 0; u < 2 * SB_B; ++u) acc[u] = 0.f;
-            for (int i = lane; i < m; i += 32) {
-                const cf yp = Ys[i * SB_B + p];
-#pragma unroll
-                for (int q = 0; q < SB_B; ++q) {
-                    const cf xq = Xs[i * SB_B + q];
-                    acc[2 * q] += yp.x * xq.x + yp.y * xq.y;
-                    acc[2 * q + 1] += yp.x * xq.y - yp.y * xq.x;
-                }
+        {                                                  // lanes (row parity r, column q)
+            const int p = warp, r = lane >> 4, q = lane & 15;
+            float mr0 = 0.f, mi0 = 0.f, mr1 = 0.f, mi1 = 0.f;
+            int i = r;
+            for (; i + 2 < m; i += 4) {
+                const cf yp = Ys[i * SB_B + p], xq = Xs[i * SB_B + q];
+                const cf zp = Ys[(i + 2) * SB_B + p], wq = Xs[(i + 2) * SB_B + q];
+                mr0 += yp.x * xq.x + yp.y * xq.y;
+                mi0 += yp.x * xq.y - yp.y * xq.x;
+                mr1 += zp.x * wq.x + zp.y * wq.y;
+                mi1 += zp.x * wq.y - zp.y * wq.x;
             }
-            float lo[16], hi[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                lo[u] = acc[u];
-                hi[u] = acc[16 + u];
+            if (i < m) {
+                const cf yp = Ys[i * SB_B + p], xq = Xs[i * SB_B + q];
+                mr0 += yp.x * xq.x + yp.y * xq.y;
+                mi0 += yp.x * xq.y - yp.y * xq.x;
             }
-            const float s0 = treduce16(lo, lane), s1 = treduce16(hi, lane);
-            if ((lane & 1) == 0) {
-                const int v = (lane >> 1) & 15;
-                ((float *)Mm)[2 * (p * SB_B + (v >> 1)) + (v & 1)] = s0;
-                ((float *)Mm)[2 * (p * SB_B + 8 + (v >> 1)) + (v & 1)] = s1;
-            }
+            float mr = mr0 + mr1, mi = mi0 + mi1;
+            mr += __shfl_xor_sync(0xffffffffu, mr, 16);
+            mi += __shfl_xor_sync(0xffffffffu, mi, 16);
+            if (r == 0) Mm[p * SB_B + q] = mk(mr, mi);
         }
         __syncthreads();
         // ---- W = X - V M / 2, in place
@@ -1109,9 +1087,10 @@ __global__ void __launch_bounds__(SB1_THREADS, 1) k_sb1(GroupSet gs, int mat_beg
                 vi[p] = valid ? Vd[il * SB_B + p] : mk(0.f, 0.f);
             }
             const int jl1 = min(32 * cb + 32, m);
-            for (int jl = 32 * cb; jl < jl1; ++jl) {
+            long long csj = colstart(r0 + 32 * cb, n);
+            for (int jl = 32 * cb; jl < jl1; csj += n - (r0 + jl), ++jl) {
                 if (valid && jl <= il) {
-                    cf *ap = Gs + colstart(r0 + jl, n) + (il - jl);
+                    cf *ap = Gs + csj + (il - jl);
                     float ar = ap->x, ai = ap->y;
                     const float4 *vr = (const float4 *)(Vd + jl * SB_B), *wr = (const float4 *)(Xs + jl * SB_B);
 #pragma unroll
@@ -1141,14 +1120,22 @@ __global__ void __launch_bounds__(SB1_THREADS, 1) k_sb1(GroupSet gs, int mat_beg
     publish_flag(flag_of(a.bready, g, mat));
 }
 
-#define SB2_THREADS 128
+#define SB2_THREADS 256
 #define SB2_WARPS (SB2_THREADS / 32)
 #define SB2_LD (2 * SB_B)          // stored diagonals 0 .. 2 b - 1 (band and bulge)
 
 __host__ __device__ inline size_t sb2_smem(int n) { return (size_t)n * SB2_LD * 8; }
 
-// One bulge-chasing step (sweep j, step k) by one warp on the band Ls (Ls[c LD + d] = A(c + d, c)).
-__device__ void sb2_step(cf *Ls, int n, int j, int k, float floor2, cf *rec, cf *sv, cf *sw, int lane) {
+// One bulge-chasing step (sweep j, step k) by a pair of warps on the band Ls
+// (Ls[c LD + d] = A(c + d, c)).  Both warps form the reflector (the same arithmetic, so the
+// same v and tau) from A[r0 .. r1, c]; after a pair barrier (both have read the column) warp 0
+// writes the annihilated column and the reflector and applies it from both sides to the
+// window's diagonal block (lane l: row l), while warp 1 applies it from the left to the
+// columns between c and the window (lanes 0 .. 14) and from the right to the rows below the
+// window (lanes 16 ..).  Every lane first loads the entries it updates, then computes, then
+// stores.
+__device__ __forceinline__ void sb2_step(cf *Ls, int n, int j, int k, float floor2, cf *rec, cf *sv, cf *sw,
+                                         int role, int pair, int lane) {
     int c, r0, r1;
     if (k == 1) {
         c = j;
@@ -1162,52 +1149,40 @@ __device__ void sb2_step(cf *Ls, int n, int j, int k, float floor2, cf *rec, cf 
     const int L = r1 - r0 + 1;                 // 2 .. SB_B
     const bool lo = lane < SB_B;
     const int l = lane & (SB_B - 1);
-    // 1. reflector of A[r0 .. r1, c]
     cf x = mk(0.f, 0.f);
     if (lo && l < L) x = Ls[c * SB2_LD + (r0 - c) + l];
-    const float xn2 = wsum(cabs2(x));
+    float xn2 = cabs2(x);
+#pragma unroll
+    for (int o = SB_B / 2; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
+    xn2 = __shfl_sync(0xffffffffu, xn2, 0);
     const cf x0 = shfl_cf(x, 0);
     float tau;
     cf alpha, v0;
     sb_reflector(xn2, x0, floor2, &tau, &alpha, &v0);
     cf v = mk(0.f, 0.f);
     if (tau != 0.f && lo && l < L) v = l == 0 ? v0 : x;
-    if (lane == 0) rec[0] = mk(tau, __int_as_float(r0));
-    if (lo) rec[1 + l] = v;
-    if (tau == 0.f) return;
-    if (lo && l < L) Ls[c * SB2_LD + (r0 - c) + l] = l == 0 ? alpha : mk(0.f, 0.f);
-    if (lo) sv[l] = v;
-    __syncwarp();
-    // 2. from the left on the columns between c and the window
-    if (k >= 2 && lane < r0 - c - 1) {
-        const int cc = c + 1 + lane;
-        cf *col = Ls + cc * SB2_LD + (r0 - cc);
-        float dr = 0.f, di = 0.f;
-#pragma unroll
-        for (int i = 0; i < SB_B; ++i) {
-            if (i < L) {
-                const cf vv = sv[i], a = col[i];
-                dr += vv.x * a.x + vv.y * a.y;
-                di += vv.x * a.y - vv.y * a.x;
-            }
-        }
-        dr *= tau;
-        di *= tau;
-#pragma unroll
-        for (int i = 0; i < SB_B; ++i) {
-            if (i < L) {
-                const cf vv = sv[i];
-                col[i] = mk(col[i].x - (vv.x * dr - vv.y * di), col[i].y - (vv.x * di + vv.y * dr));
-            }
-        }
+    if (role == 0 && lo) sv[l] = v;
+    // pair barrier (ids 1 .. 4, compile-time so that only five barriers are reserved): column c
+    // read by both warps, v in sv
+    switch (pair) {
+    case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
     }
-    // 3. from both sides on the diagonal block (lane l: row r0 + l)
-    cf p = mk(0.f, 0.f);
-    if (lo && l < L) {
+    if (role == 0) {
+        if (lane == 0) rec[0] = mk(tau, __int_as_float(r0));
+        if (lo) rec[1 + l] = v;
+    }
+    if (tau == 0.f) return;
+    if (role == 0) {
+        if (lo && l < L) Ls[c * SB2_LD + (r0 - c) + l] = l == 0 ? alpha : mk(0.f, 0.f);
+        // diagonal block D = A[r0 .. r1, r0 .. r1]: p = tau D v, K = tau / 2 v^H p, w = p - K v,
+        // D <- D - v w^H - w v^H (lower part, lane l: row l)
         float pr = 0.f, pi = 0.f;
 #pragma unroll
         for (int i2 = 0; i2 < SB_B; ++i2) {
-            if (i2 < L) {
+            if (lo && l < L && i2 < L) {
                 const int ix = i2 <= l ? (r0 + i2) * SB2_LD + (l - i2) : (r0 + l) * SB2_LD + (i2 - l);
                 cf dv = Ls[ix];
                 if (i2 > l) dv.y = -dv.y;
@@ -1217,58 +1192,84 @@ __device__ void sb2_step(cf *Ls, int n, int j, int k, float floor2, cf *rec, cf 
                 pi += dv.x * vv.y + dv.y * vv.x;
             }
         }
-        p = mk(tau * pr, tau * pi);
-    }
-    const float kv = wsum(v.x * p.x + v.y * p.y);
-    const float K = 0.5f * tau * kv;
-    const cf w = mk(p.x - K * v.x, p.y - K * v.y);
-    if (lo) sw[l] = w;
-    __syncwarp();
-    if (lo && l < L) {
+        const cf p = mk(tau * pr, tau * pi);
+        float kv = (lo && l < L) ? v.x * p.x + v.y * p.y : 0.f;
 #pragma unroll
-        for (int i2 = 0; i2 < SB_B; ++i2) {
-            if (i2 <= l && i2 < L) {
-                cf *dp = Ls + (r0 + i2) * SB2_LD + (l - i2);
-                const cf vj = sv[i2], wj = sw[i2];
-                float ur = dp->x, ui = dp->y;
-                ur -= v.x * wj.x + v.y * wj.y + w.x * vj.x + w.y * vj.y;
-                ui -= v.y * wj.x - v.x * wj.y + w.y * vj.x - w.x * vj.y;
-                if (i2 == l) ui = 0.f;
-                *dp = mk(ur, ui);
+        for (int o = SB_B / 2; o > 0; o >>= 1) kv += __shfl_xor_sync(0xffffffffu, kv, o);
+        kv = __shfl_sync(0xffffffffu, kv, 0);
+        const float K = 0.5f * tau * kv;
+        const cf w = mk(p.x - K * v.x, p.y - K * v.y);
+        if (lo) sw[l] = w;
+        __syncwarp();
+        if (lo && l < L) {
+#pragma unroll
+            for (int i2 = 0; i2 < SB_B; ++i2) {
+                if (i2 <= l) {
+                    cf *dp = Ls + (r0 + i2) * SB2_LD + (l - i2);
+                    const cf d0 = *dp, vj = sv[i2], wj = sw[i2];
+                    float ur = d0.x, ui = d0.y;
+                    ur -= v.x * wj.x + v.y * wj.y + w.x * vj.x + w.y * vj.y;
+                    ui -= v.y * wj.x - v.x * wj.y + w.y * vj.x - w.x * vj.y;
+                    if (i2 == l) ui = 0.f;
+                    *dp = mk(ur, ui);
+                }
             }
         }
-    }
-    // 4. from the right on the rows below the window
-    const int nbelow = min(SB_B, n - 1 - r1);
-    if (lane < nbelow) {
-        const int row = r1 + 1 + lane;
+    } else {
+        cf *ep = nullptr;                      // lane's column (left of the window) or row (below)
+        int stride = 0;
+        bool act = false;
+        if (lo) {
+            if (k >= 2 && lane < r0 - c - 1) {
+                const int cc = c + 1 + lane;
+                ep = Ls + cc * SB2_LD + (r0 - cc);           // A[r0 + i, cc] = ep[i]
+                stride = 1;
+                act = true;
+            }
+        } else {
+            const int row = r1 + 1 + (lane - SB_B);
+            if (row < n && lane - SB_B < SB_B) {
+                ep = Ls + r0 * SB2_LD + (row - r0);           // A[row, r0 + i] = ep[i (LD - 1)]
+                stride = SB2_LD - 1;
+                act = true;
+            }
+        }
+        // conj(v) for a column (s = v^H col), v for a row (s = row v): one code path with
+        // cs = -1 / +1 on the imaginary part of v
+        const float cs = lo ? -1.f : 1.f;
+        cf e[SB_B];
         float sr = 0.f, si = 0.f;
 #pragma unroll
         for (int i = 0; i < SB_B; ++i) {
-            if (i < L) {
-                const cf e = Ls[(r0 + i) * SB2_LD + (row - r0 - i)], vv = sv[i];
-                sr += e.x * vv.x - e.y * vv.y;
-                si += e.x * vv.y + e.y * vv.x;
-            }
+            e[i] = (act && i < L) ? ep[i * stride] : mk(0.f, 0.f);
+            const cf vv = sv[i];
+            const float vy = cs * vv.y;
+            sr += e[i].x * vv.x - e[i].y * vy;
+            si += e[i].x * vy + e[i].y * vv.x;
         }
         sr *= tau;
         si *= tau;
+        if (act) {
 #pragma unroll
-        for (int i = 0; i < SB_B; ++i) {
-            if (i < L) {
-                cf *ep = Ls + (r0 + i) * SB2_LD + (row - r0 - i);
-                const cf vv = sv[i];
-                // E -= s conj(v)
-                *ep = mk(ep->x - (sr * vv.x + si * vv.y), ep->y - (si * vv.x - sr * vv.y));
+            for (int i = 0; i < SB_B; ++i) {
+                if (i < L) {
+                    // column: col -= v s;  row: row -= s conj(v)
+                    const cf vv = sv[i];
+                    const float vy = -cs * vv.y;
+                    cf u = e[i];
+                    u.x -= vv.x * sr - vy * si;
+                    u.y -= vv.x * si + vy * sr;
+                    ep[i * stride] = u;
+                }
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(SB2_THREADS) k_sb2(GroupSet gs, int mat_begin, EigArgs a) {
+__global__ void __launch_bounds__(SB2_THREADS, 4) k_sb2(GroupSet gs, int mat_begin, EigArgs a) {
     extern __shared__ __align__(16) unsigned char bsm[];
-    __shared__ cf s_v[SB2_WARPS][SB_B], s_w[SB2_WARPS][SB_B];
     __shared__ float red[SB2_WARPS];
+    __shared__ cf s_v[SB2_WARPS / 2][SB_B], s_w[SB2_WARPS / 2][SB_B];
     int mat;
     const int gi = find_group(gs, mat_begin + blockIdx.x, &mat);
     const Group &g = gs.g[gi];
@@ -1295,15 +1296,17 @@ __global__ void __launch_bounds__(SB2_THREADS) k_sb2(GroupSet gs, int mat_begin,
     __syncthreads();
     for (int w = 0; w < SB2_WARPS; ++w) gm = fmaxf(gm, red[w]);
     const float floor2 = reflector_floor(gm);
+    const int pair = warp >> 1, role = warp & 1;
     if (n >= 3) {
         const int kmax = sb_nsteps(n, 0);
         const int tlast = 3 * (n - 3) + sb_nsteps(n, n - 3);
         for (int tt = 1; tt <= tlast; ++tt) {
-            for (int k = (tt - 1) % 3 + 1 + 3 * warp; k <= kmax; k += 3 * SB2_WARPS) {
+            // the steps of this time: k = tt mod 3 (1 .. 3), + 3, ...; pair q takes the q-th, the q+4-th, ...
+            for (int k = (tt - 1) % 3 + 1 + 3 * pair; k <= kmax; k += 3 * (SB2_WARPS / 2)) {
                 const int j = (tt - k) / 3;               // tt - k is a multiple of 3
                 if (tt - k < 0 || j > n - 3 || k > sb_nsteps(n, j)) continue;
-                sb2_step(Ls, n, j, k, floor2, rec + (sb_sweep_off(n, j) + k - 1) * (SB_B + 1), s_v[warp], s_w[warp],
-                         lane);
+                sb2_step(Ls, n, j, k, floor2, rec + (sb_sweep_off(n, j) + k - 1) * (SB_B + 1), s_v[pair], s_w[pair],
+                         role, pair, lane);
             }
             __syncthreads();
         }
@@ -1576,46 +1579,77 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3)) k_eigvec(GroupSet gs,
         __syncthreads();
         if (a.band) {
             // two-stage reduction: y <- Q2 y = S_0 (S_1 (... S_{n-3} y)), the reflectors of one
-            // sweep (disjoint windows of at most SB_B rows) two at a time, one per half-warp
+            // sweep (disjoint windows of at most SB_B rows) two at a time, one per half-warp.  The
+            // reflectors are staged by groups of sweeps (from the last) into two buffers in the
+            // inverse-iteration arrays (free from here on), the next group while one is applied.
             const cf *rec = a.sb + g.sboff + (long long)mat * sb_stride(n) + (long long)n * (SB_B + 1);
+            cf *qb = (cf *)(vsm + LY.zv);
+            const long long cap = (long long)((LY.yc - LY.zv) / 8) / 2 / (SB_B + 1);   // reflectors per buffer
+            auto group_lo = [&](int jh) {
+                int jl = jh;
+                while (jl > 0 && sb_sweep_off(n, jh + 1) - sb_sweep_off(n, jl - 1) <= cap) --jl;
+                return jl;
+            };
+            auto stage = [&](int jh, int jl, int bi) {
+                const long long o0 = sb_sweep_off(n, jl) * (SB_B + 1), o1 = sb_sweep_off(n, jh + 1) * (SB_B + 1);
+                cf *dst = qb + (long long)bi * cap * (SB_B + 1);
+                for (long long e = tid; e < o1 - o0; e += NT) cp_async8(dst + e, rec + o0 + e, 8);
+                cp_async_commit();
+            };
             const int hw = lane >> 4, l = lane & (SB_B - 1);
-            for (int w = warp; w < qc; w += NW) {
-                cf *y = Yc + (long long)w * n;
-                for (int j = n - 3; j >= 0; --j) {
-                    const int K = sb_nsteps(n, j);
-                    const cf *rj = rec + sb_sweep_off(n, j) * (SB_B + 1);
-                    for (int k0 = 0; k0 < K; k0 += 2) {
-                        const int k = k0 + hw;
-                        float tau = 0.f;
-                        int row = n;
-                        cf v = mk(0.f, 0.f);
-                        if (k < K) {
-                            const cf hd = rj[k * (SB_B + 1)];
-                            tau = hd.x;
-                            row = __float_as_int(hd.y) + l;
-                            v = rj[k * (SB_B + 1) + 1 + l];
-                        }
-                        const bool on = tau != 0.f && row < n;
-                        const cf yy = on ? y[row] : mk(0.f, 0.f);
-                        float dr = v.x * yy.x + v.y * yy.y, di = v.x * yy.y - v.y * yy.x;
+            int jhi = n - 3, jlo = group_lo(jhi), buf = 0;
+            stage(jhi, jlo, 0);
+            while (jhi >= 0) {
+                const int nh = jlo - 1, nl = nh >= 0 ? group_lo(nh) : 0;
+                if (nh >= 0) stage(nh, nl, buf ^ 1);
+                else cp_async_commit();
+                cp_async_wait_1();
+                __syncthreads();
+                const cf *gb = qb + (long long)buf * cap * (SB_B + 1);
+                const long long ob = sb_sweep_off(n, jlo);
+                for (int w = warp; w < qc; w += NW) {
+                    cf *y = Yc + (long long)w * n;
+                    for (int j = jhi; j >= jlo; --j) {
+                        const int K = sb_nsteps(n, j);
+                        const cf *rj = gb + (sb_sweep_off(n, j) - ob) * (SB_B + 1);
+                        for (int k0 = 0; k0 < K; k0 += 2) {
+                            const int k = k0 + hw;
+                            float tau = 0.f;
+                            int row = n;
+                            cf v = mk(0.f, 0.f);
+                            if (k < K) {
+                                const cf hd = rj[k * (SB_B + 1)];
+                                tau = hd.x;
+                                row = __float_as_int(hd.y) + l;
+                                v = rj[k * (SB_B + 1) + 1 + l];
+                            }
+                            const bool on = tau != 0.f && row < n;
+                            const cf yy = on ? y[row] : mk(0.f, 0.f);
+                            float dr = v.x * yy.x + v.y * yy.y, di = v.x * yy.y - v.y * yy.x;
 #pragma unroll
-                        for (int o = SB_B / 2; o > 0; o >>= 1) {
-                            dr += __shfl_xor_sync(0xffffffffu, dr, o);
-                            di += __shfl_xor_sync(0xffffffffu, di, o);
+                            for (int o = SB_B / 2; o > 0; o >>= 1) {
+                                dr += __shfl_xor_sync(0xffffffffu, dr, o);
+                                di += __shfl_xor_sync(0xffffffffu, di, o);
+                            }
+                            dr *= tau;
+                            di *= tau;
+                            if (on) y[row] = mk(yy.x - (v.x * dr - v.y * di), yy.y - (v.x * di + v.y * dr));
                         }
-                        dr *= tau;
-                        di *= tau;
-                        if (on) y[row] = mk(yy.x - (v.x * dr - v.y * di), yy.y - (v.x * di + v.y * dr));
+                        __syncwarp();
                     }
-                    __syncwarp();
                 }
+                __syncthreads();                             // this buffer is staged into next-but-one
+                jhi = nh;
+                jlo = nl;
+                buf ^= 1;
             }
+            cp_async_wait_all();
             __syncthreads();
         }
         // Reflectors are applied in batches of EV_HB, u_j = v_{kb-j} (j = 0 .. EV_HB-1, in the order
         // of application), staged in shared memory by absolute row (zero above the reflector's
-        // first row, and wholly zero past reflector 0).  With d_j = u_j^H y and C_ji = u_j^H u_i, applying them
-        // one after the other is
+        // first row, and wholly zero past reflector 0).  With d_j = u_j^H y and C_ji = u_j^H u_i,
+        // applying them one after the other is
         //   s_j = d_j - sum_{i<j} tau_i C_ji s_i,   y <- y - sum_j tau_j u_j s_j,
         // so each vector needs one round of reductions per batch instead of one per reflector:
         // its 2 EV_HB dot-product sums are reduced over the lanes by one transpose-reduce and
