@@ -14,6 +14,7 @@
 
 #define LIFT_THREADS 256
 #define LIFT_PER_BLOCK 1024
+#define ADJ_SLICES 4
 
 __global__ void __launch_bounds__(LIFT_THREADS)
 k_lift(GroupSet gs, int mat_begin, const cf *D, int d_natural, float inv_beta, cf *out, cf *out2,
@@ -63,7 +64,8 @@ k_adjoint(GroupSet gs, int mat_begin, const cf *E, int e_natural) {
     const Group &g = gs.g[gi];
     const long long mbase = g.off + (long long)mat * g.rows * g.cols;
     const int total = g.J * g.nv;
-    for (int idx = threadIdx.x; idx < total; idx += LIFT_THREADS) {
+    // blockIdx.y: slice of the J nv outputs (ADJ_SLICES CTAs per matrix, for more loads in flight)
+    for (int idx = blockIdx.y * LIFT_THREADS + threadIdx.x; idx < total; idx += LIFT_THREADS * gridDim.y) {
         const int j = idx / g.nv, k = idx - j * g.nv;
         // plain channel j
         cf s = mk(0.f, 0.f);
@@ -96,7 +98,10 @@ cudaError_t launch_adjoint(const GroupSet &gs, int gfirst, int mat_begin, int ma
                            const cf *E, int e_natural, cudaStream_t st) {
     (void)gfirst;
     if (mat_count <= 0) return cudaSuccess;
-    k_adjoint<<<mat_count, LIFT_THREADS, 0, st>>>(gs, mat_begin, E, e_natural);
+    int maxout = 0;
+    for (int k = 0; k < gs.n; ++k) maxout = max(maxout, gs.g[k].J * gs.g[k].nv);
+    const int slices = max(1, min(ADJ_SLICES, (maxout + LIFT_THREADS - 1) / LIFT_THREADS));
+    k_adjoint<<<dim3(mat_count, slices), LIFT_THREADS, 0, st>>>(gs, mat_begin, E, e_natural);
     return cudaGetLastError();
 }
 
