@@ -98,7 +98,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- GPU arm
-def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
+def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig", reduction=0):
     """Kernels libselr launches per ADMM iteration (mirrors admm_stage and svd_apply in
     selr.cu): adjoint, FFTs of the adjoints, DC + reduction, hybrid FFTs, lift, and the
     SVT kernels: either the warp-per-matrix SVT (s <= 8, len <= 64) or Gram, tridiagonal
@@ -106,7 +106,9 @@ def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
     32 < r <= 64 pairs, general above) and the FP64 re-solve of flagged matrices (eig),
     Jacobi and apply (jacobi).  Batched, one
     SVT launch sequence covers each run of consecutive lift families of the same SVT
-    size class (svt_class in selr.cu); plain, one per matrix."""
+    size class (svt_class in selr.cu); plain, one per matrix.  With the two-stage reduction in
+    force (reduction 2) a sequence whose orders all lie in 48 .. 192 launches both of its
+    kernels in place of the one-stage reduction."""
     fams = [plan.lift_shape(a) for a in (("row", "col") if model2d else ("pe", "param"))]
     fft_a = 2 if model2d else 1
 
@@ -121,13 +123,22 @@ def kernel_launches_per_iteration(plan, model2d, exec_mode, svd="eig"):
                 return i
         return 7
 
+    def two_stage(shapes):
+        return svd == "eig" and reduction == 2 and all(48 <= min(r, c) <= 192 for r, c in shapes)
+
     def svt_kernels(r, c):
-        return 1 if svt_class(r, c) == 0 else (7 if svd == "eig" else 2)
+        return 1 if svt_class(r, c) == 0 else ((8 if two_stage([(r, c)]) else 7) if svd == "eig" else 2)
 
     if exec_mode == "batched":
-        classes = [svt_class(r, c) for _, r, c in fams]
-        runs = [k for i, k in enumerate(classes) if i == 0 or k != classes[i - 1]]
-        per = 1 + fft_a + 2 + fft_a + 1 + sum(1 if k == 0 else (7 if svd == "eig" else 2) for k in runs)
+        runs = []                                   # (class, shapes) of consecutive families
+        for _, r, c in fams:
+            k = svt_class(r, c)
+            if runs and runs[-1][0] == k:
+                runs[-1][1].append((r, c))
+            else:
+                runs.append((k, [(r, c)]))
+        per = 1 + fft_a + 2 + fft_a + 1 + sum(
+            1 if k == 0 else ((8 if two_stage(sh) else 7) if svd == "eig" else 2) for k, sh in runs)
     else:
         nmat = sum(nm for nm, _, _ in fams)
         per = nmat + fft_a + 2 + fft_a + sum(nm * (1 + svt_kernels(r, c)) for nm, r, c in fams)
@@ -313,7 +324,8 @@ def run_gpu(args, rank, world):
         plan.profile(False)
         st3 = api.selr_sync_status(plan, stream)
         results[mode] = dict(ms=ms, steps=steps, status=max(st, st2, st3), nmat=nmat, clocks=clocks, stages=prof,
-                             launches=steps * kernel_launches_per_iteration(plan, model2d, mode, args.svd) + 6
+                             launches=steps * kernel_launches_per_iteration(plan, model2d, mode, args.svd,
+                                                                            plan.tuning()["reduction"]) + 6
                              + calibration_launches(plan))
         if mode == "batched":
             results["plan"] = plan
@@ -974,6 +986,7 @@ def main():
                         + (fk["tridiag"] + fk["eigvec"] + fk["apply"] + fk["small_svt"]) / (fp32_peak * 1e12)
                         + jac["bytes"] / (hbm * 1e9))
     t_meas = b["ms"] / b["steps"]
+    two_stage = results["plan"].tuning()["reduction"] == 2 if args.svd == "eig" else False
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": b["steps"],
         "warmup": args.warmup, "ms_per_step": b["ms"] / b["steps"], "higher_is_better": True,
@@ -988,10 +1001,12 @@ def main():
                    "steps": results["plain"]["steps"]} if "plain" in results else None),
         "roofline": {"bound": "alu",
                      "kernel": ("k_jacobi (one-sided Jacobi SVD)" if args.svd == "jacobi" else
+                                "k_sb1 + k_sb2 + k_eigvec (two-stage Householder reduction, multisection, "
+                                "inverse iteration and back-transformation of the pairs above t^2)" if two_stage else
                                 "k_tridiag + k_eigvec (Householder tridiagonalisation, multisection, inverse "
                                 "iteration and back-transformation of the pairs above t^2)"),
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": svd_traffic(jac.get("eig_shapes")) if args.svd == "eig" else None,
+                     "traffic": svd_traffic(jac.get("eig_shapes")) if args.svd == "eig" and not two_stage else None,
                      "traffic_unit": "bytes per launch (ncu capture of the same kernels, scaled per matrix)",
                      "peak_source": fp32_src,
                      "flops_per_launch": jac["flops"], "launch_ms": jac["ms"],

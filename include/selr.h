@@ -368,7 +368,9 @@ selr_status selr_plan_rank_sums(selr_plan *plan, int64_t *out, int32_t n, int32_
  * plan: with SELR_SVD_EIG the Gram precision among the modes of FP32-level
  * accuracy (SELR_GRAM_FP32, SELR_GRAM_3XTF32, SELR_GRAM_BF16X6; also SELR_GRAM_TF32 and
  * SELR_GRAM_BF16X3 when flags & 1) and the number of eigenvectors refined per inverse-iteration
- * pass (8 or 16); with SELR_SVD_JACOBI the sweep cap (twice the largest
+ * pass (8 or 16), then, on a plan whose reduction mode is 0 and that has two-stage scratch
+ * (orders 48 .. 192), whether the two-stage reduction is faster (mode 2 if so); with
+ * SELR_SVD_JACOBI the sweep cap (twice the largest
  * number of sweeps a matrix needed, + 2, if below the current cap and no
  * matrix reached it).
  * max_iter, tol and profiling are restored afterwards; cached CUDA graphs are
@@ -394,6 +396,10 @@ selr_status selr_plan_set_tuning(selr_plan *plan, int32_t gram_precision, int32_
  * eigenpairs to FP32 accuracy; the reverse-mode SVT derivative always uses the one-stage
  * reduction.  Cached CUDA graphs are dropped.  SELR_ERR_INVALID_ARG for other modes. */
 selr_status selr_plan_set_reduction(selr_plan *plan, int32_t mode);
+
+/* The reduction mode in force (as set above, or 2 when selr_plan_autotune found the two-stage
+ * reduction faster on a plan left at 0). */
+selr_status selr_plan_get_reduction(const selr_plan *plan, int32_t *mode);
 
 /* Change the iteration cap and stopping tolerance of an existing plan
  * (same meaning as selr_desc.max_iter / tol).  SELR_ERR_INVALID_ARG if

@@ -83,6 +83,7 @@ SIGNATURES = {
     "selr_plan_autotune": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "selr_plan_set_tuning": (c_int32, [c_void_p, c_int32, c_int32]),
     "selr_plan_set_reduction": (c_int32, [c_void_p, c_int32]),
+    "selr_plan_get_reduction": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
     "selr_plan_tuning": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
                                    ctypes.POINTER(c_int32)]),
     "selr_svt_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p,

@@ -143,7 +143,10 @@ class Plan:
         check(self.lib.selr_plan_tuning(self.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(w)),
               "selr_plan_tuning")
         names = {v: k for k, v in GRAM.items()}
-        return {"gram": names.get(g.value, g.value), "ev_chunk": c.value, "jacobi_max_sweeps": w.value}
+        red = ctypes.c_int32()
+        check(self.lib.selr_plan_get_reduction(self.handle, ctypes.byref(red)), "selr_plan_get_reduction")
+        return {"gram": names.get(g.value, g.value), "ev_chunk": c.value, "jacobi_max_sweeps": w.value,
+                "reduction": red.value}
 
     def set_tuning(self, gram, ev_chunk=0):
         """selr_plan_set_tuning: Gram mode (name as in Desc) and eigenvectors per pass (0, 8, 16)."""

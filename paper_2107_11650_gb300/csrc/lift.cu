@@ -100,7 +100,9 @@ cudaError_t launch_adjoint(const GroupSet &gs, int gfirst, int mat_begin, int ma
     if (mat_count <= 0) return cudaSuccess;
     int maxout = 0;
     for (int k = 0; k < gs.n; ++k) maxout = max(maxout, gs.g[k].J * gs.g[k].nv);
-    const int slices = max(1, min(ADJ_SLICES, (maxout + LIFT_THREADS - 1) / LIFT_THREADS));
+    // a few large matrices (the 2D lifts): several CTAs per matrix; many small ones (the
+    // parameter lifts): one CTA each already fills the GPU
+    const int slices = mat_count >= 1024 ? 1 : max(1, min(ADJ_SLICES, (maxout + LIFT_THREADS - 1) / LIFT_THREADS));
     k_adjoint<<<dim3(mat_count, slices), LIFT_THREADS, 0, st>>>(gs, mat_begin, E, e_natural);
     return cudaGetLastError();
 }

@@ -1509,6 +1509,14 @@ extern "C" selr_status selr_plan_autotune(selr_plan *p, const void *Y, const uin
         }
         p->d.gram_precision = bg;
         p->ev_chunk = bc;
+        // the two-stage reduction where the plan has its scratch and the choice is left open
+        if (s == SELR_OK && p->sb && p->reduction == 0) {
+            p->reduction = 2;
+            drop_graphs(p);
+            float ms = 0.f;
+            s = time_solve(p, Y, mask, X_scratch, st, &ms);
+            if (s != SELR_OK || ms >= best) p->reduction = 0;
+        }
     }
     drop_graphs(p);
     p->d.max_iter = max_iter;
@@ -1536,6 +1544,12 @@ extern "C" selr_status selr_plan_set_tuning(selr_plan *p, int32_t gram_precision
     p->d.gram_precision = gram_precision;
     p->ev_chunk = ev_chunk;
     drop_graphs(p);
+    return SELR_OK;
+}
+
+extern "C" selr_status selr_plan_get_reduction(const selr_plan *p, int32_t *mode) {
+    if (!p || !mode) return SELR_ERR_INVALID_ARG;
+    *mode = p->reduction;
     return SELR_OK;
 }
 

@@ -1988,10 +1988,12 @@ __global__ void __launch_bounds__(EIG_THREADS) k_resolvent(GroupSet gs, EigArgs 
 #define AS_SMALL 8        // up to this many pairs phase 1 splits the rows of B over the warps
 #define AS_THREADS 256
 #define AS_P1B 8          // rows of B loaded together in phase 1
+// CH = 32: four CTAs per SM (at most 64 registers), more loads in flight per SM than the three
+// that 80 registers allow (0.437 against 0.464 ms per apply stage on the 12-coil 256x256
+// workload); CH = 64 keeps its registers (its eight accumulators per thread would spill)
 template <int CH>
-// four CTAs per SM (at most 64 registers): more loads in flight per SM than the three that 80
-// registers allow, 0.437 against 0.464 ms per apply stage on the 12-coil 256x256 workload
-__global__ void __launch_bounds__(AS_THREADS, 4) k_apply_stream(GroupSet gs, int mat_begin, EigArgs ea, SvtArgs a) {
+__global__ void __launch_bounds__(AS_THREADS, CH <= 32 ? 4 : 3)
+    k_apply_stream(GroupSet gs, int mat_begin, EigArgs ea, SvtArgs a) {
     extern __shared__ cf ssm[];
     __shared__ float gcoef[CH];
     int mat;

@@ -130,3 +130,4 @@ def test_null_arguments(lib):
     assert lib.selr_t2_fit(None, te, 1, 1, 1.0, 10.0, None, None, None) == 1
     assert lib.selr_plan_set_tuning(None, 0, 16) == 1
     assert lib.selr_plan_set_reduction(None, 2) == 1
+    assert lib.selr_plan_get_reduction(None, None) == 1
