@@ -374,10 +374,10 @@ def work_model(plan, model2d, svd, rank_sums, stages):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per matrix of k_tridiag + k_eigvec,
 # by order s, from one full-size ncu capture of each kernel on the 12-coil 256x256 workload
-# (k_tridiag 75.9 + 19.4 MB, k_eigvec 77.6 + 1.8 MB per launch of 512 matrices): the packed
+# (k_tridiag 75.94 + 18.22 MB, k_eigvec 77.59 + 0.06 MB per launch of 512 matrices): the packed
 # Gram read once, the Householder vectors written once and read once.  Orders without a
 # capture report no traffic.
-NCU_SVD_BYTES_PER_MATRIX = {192: (75.9e6 + 19.4e6 + 77.6e6 + 1.8e6) / 512}
+NCU_SVD_BYTES_PER_MATRIX = {192: (75.94e6 + 18.22e6 + 77.59e6 + 0.06e6) / 512}
 
 
 def svd_traffic(eig_shapes):
