@@ -15,6 +15,9 @@
 //               step's matrix-vector product (one pass over the matrix per
 //               step); k_tridiag_g is the same reduction on global memory for
 //               orders that do not fit in shared memory.
+//   k_sb1, k_sb2  the two-stage alternative to k_tridiag (orders 48 .. 192, opt-in): G to a
+//               Hermitian band of half-bandwidth 16 by blocked panels, then the band to
+//               tridiagonal by bulge chasing (see the section before k_eigvec).
 //   k_eigvec    diagonal phase scaling to a real symmetric tridiagonal T,
 //               Sturm count of the eigenvalues above t^2, 32-way multisection
 //               of each of them (one warp per eigenvalue), inverse iteration
@@ -783,7 +786,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
 // j = n - 3 .. 0; then the panel reflectors, as the one-stage reflectors with their first row
 // b - 1 rows further down.
 
-#define SB_AUTO_MIN (1 << 30)     // by order: the two-stage reduction from this order up
+// Reduction mode 0 ("by order") takes the two-stage reduction from this order up: never, since
+// the one-stage reduction is faster at every order measured (the autotuner still tries it).
+#define SB_AUTO_MIN (1 << 30)
 #define SB1_THREADS 512
 #define SB1_RPL 6                  // panel rows per lane: n - SB_B <= 32 SB1_RPL for n <= SB_NMAX
 
