@@ -787,8 +787,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_tridiag_g(GroupSet gs, int m
 // b - 1 rows further down.
 
 // Reduction mode 0 ("by order") takes the two-stage reduction from this order up: never, since
-// the one-stage reduction was faster at the orders measured, 48 and 192 (the autotuner still
-// tries it).
+// the one-stage reduction was faster at order 192, the order measured (the autotuner still
+// tries the two-stage reduction on each plan).
 #define SB_AUTO_MIN (1 << 30)
 #define SB1_THREADS 512
 #define SB1_RPL 6                  // panel rows per lane: n - SB_B <= 32 SB1_RPL for n <= SB_NMAX
