@@ -34,6 +34,20 @@ def test_bench_workload_counts_fifteen_per_iteration():
     assert bench.kernel_launches_per_iteration(p, True, "batched", svd="jacobi") == 10
 
 
+def test_two_stage_reduction_adds_one_launch_per_eligible_sequence():
+    # k_sb1 + k_sb2 replace k_tridiag where every order of the sequence lies in 48 .. 192
+    p = _Plan({"row": (256, 241, 192), "col": (256, 241, 192)})
+    assert bench.kernel_launches_per_iteration(p, True, "batched", reduction=2) == 16
+    assert bench.kernel_launches_per_iteration(p, True, "batched", reduction=1) == 15
+    # order 384 (outside the range) keeps the one-stage sequence; order 192 gets two-stage
+    p = _Plan({"row": (256, 241, 384), "col": (256, 241, 192)})
+    assert bench.kernel_launches_per_iteration(p, True, "batched", reduction=2) == 8 + 15
+    # plain: one more kernel per eligible matrix (orders 32 stay one-stage)
+    p = _Plan({"row": (4, 57, 48), "col": (4, 57, 32)})
+    assert (bench.kernel_launches_per_iteration(p, True, "plain", reduction=2)
+            == bench.kernel_launches_per_iteration(p, True, "plain") + 4)
+
+
 def test_families_in_different_classes_get_their_own_sequence():
     # SHLR-V-like rows (s = 241) and a family of s = 192: two eigensolver sequences
     p = _Plan({"row": (256, 241, 384), "col": (256, 241, 192)})

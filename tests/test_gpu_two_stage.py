@@ -163,3 +163,26 @@ def test_two_stage_outputs_stay_in_bounds(rows, cols):
     torch.cuda.synchronize()
     for buf, gw in ((raw, 2 * GUARD), (rawr, GUARD)):
         assert bool((buf[:gw] == CANARY).all() and (buf[-gw:] == CANARY).all())
+
+
+def test_autotune_tries_two_stage_and_keeps_a_set_mode():
+    """The autotuner times the two-stage reduction on a plan left at mode 0 (order 48 here) and
+    reports the mode in force; a plan set to one-stage stays one-stage.  The two tuned plans
+    (possibly different Gram modes and reductions) agree within the metric's tolerance."""
+    from paper_2107_11650_gb300 import api
+    wl = synth.get_config("shlr_12c_256").with_(J=4, M=96, N=80, window=12, n_iter=4)
+    inp = synth.make_inputs(wl)
+    Y = torch.from_numpy(inp["Y"].astype(np.complex64)).cuda()
+    m = torch.from_numpy(inp["mask"].astype(np.uint8)).cuda()
+    plan = api.Plan(api.Desc.from_workload(wl))
+    assert plan.autotune(Y, m)["reduction"] in (0, 2)
+    fixed = api.Plan(api.Desc.from_workload(wl))
+    fixed.set_reduction(1)
+    assert fixed.autotune(Y, m)["reduction"] == 1
+    out = []
+    for p in (plan, fixed):
+        X = torch.empty_like(Y)
+        api.selr_solve(p, Y, m, X)
+        assert api.selr_sync_status(p) == 0
+        out.append(X.cpu().numpy().astype(np.complex128))
+    assert rel_l2(out[0], out[1]) < TOL
